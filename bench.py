@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Benchmark of the coupled LB-DPS step on GB300.
+
+Default workload: the periodic riser section, D2Q9 256 x 2048 cells, 200,000
+particles of 54 um at mean 2D solid fraction 0.05, FP32 deviation storage
+(the riser configuration in the shape of the paper's Table 2).  A "step" is
+one coupled time step: deposition + modified-LBE collide-stream, interpolated
+EMMS drag with the third-law rescale and integration, cell sort, hard-sphere
+collision detection and resolution.
+
+Prints one JSON line (rank 0).  Metric: coupled-step MLUPS (cell updates per
+second / 1e6), whole job over all ranks.  Multi-GPU runs are independent
+replicas of the bed (weak scaling, no data-path collective).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled-step MLUPS"
+UNIT = "MLUPS"
+L2_FLUSH_BYTES = 512 * 1024 * 1024      # > 129 MB L2
+KERNELS_PER_STEP = 10                   # collide_stream, drag_pre, drag_integrate,
+                                        # scan x3, scatter, gather, detect, resolve
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(storage):
+    from paper_1303_2653_gb300 import workloads as W
+    st = {"f32": W.STORE_F32, "f16": W.STORE_F16, "bf16": W.STORE_BF16, "f64": W.STORE_F64}[storage]
+    return W.riser2d(storage=st)
+
+
+def config_dict(w, n_gpus, storage):
+    return {"workload": f"riser2d D2Q9 {w.n[0]}x{w.n[1]}, {w.n_particles} particles, "
+                        f"{storage} population storage",
+            "cells": w.ncell, "particles": w.n_particles, "lattice": "D2Q9",
+            "storage": storage, "l2": "flushed between timed steps (512 MB write)",
+            "parallelism": f"replicas x{n_gpus}"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ roofline
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def collide_stream_bytes(w, storage):
+    """Algorithmic bytes of one collide_stream launch: populations read and
+    written once, the cell_start offset, the node outputs (rho, u, F_p->g,
+    beta) written once, and each particle velocity read once."""
+    q = 9 if w.dim == 2 else 19
+    s_f = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}[storage]
+    s_r = 8 if storage == "f64" else 4
+    per_cell = 2 * q * s_f + 4 + (1 + w.dim + w.dim + 1) * s_r
+    per_particle = w.dim * s_r
+    return w.ncell * per_cell + w.n_particles * per_particle, per_cell, per_particle
+
+
+def profiled_traffic():
+    """DRAM bytes per collide_stream launch from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "collide_stream_riser2d_256x2048.md")
+    src = os.path.join(ROOT, "paper_1303_2653_gb300", "csrc", "lbm_kernels.cu")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"source sha256:\s*([0-9a-f]{16})", text)
+    t = re.search(r"dram bytes per launch:\s*([0-9.eE+]+)", text)
+    if not m or not t:
+        return None
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return float(t.group(1)) if cur == m.group(1) else None
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_rate(w, budget_s):
+    """Time the FP64 oracle (single thread) on the workload for about
+    budget_s seconds; returns (MLUPS, steps, seconds)."""
+    from oracle import oracle as O
+    bed = O.OracleBed(w)
+    t0 = time.perf_counter()
+    bed.step(1)
+    t1 = time.perf_counter()
+    per = t1 - t0
+    steps = max(1, int(budget_s / max(per, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    bed.step(steps)
+    dt = time.perf_counter() - t0
+    return w.ncell * steps / dt / 1e6, steps, dt
+
+
+def reference_main(args, rank, world):
+    """The oracle as the reference arm: K timed steps, each a bounded sample
+    (a slab of the riser at the same solid fraction) so the run stays short."""
+    from paper_1303_2653_gb300 import workloads as W
+    from oracle import oracle as O
+    if rank != 0:
+        return
+    full = workload(args.storage)
+    total = args.steps + args.warmup
+    per_step_budget = 120.0 / max(total, 1)
+    # oracle cost is close to 1.0 us per cell plus particles at this density
+    ny = int(max(8, min(full.n[1], per_step_budget / 1.2e-6 / full.n[0])))
+    sample = W.scaled_riser2d(nx=full.n[0], ny=ny, n_particles=int(round(
+        full.n_particles * ny / full.n[1])), storage=W.STORE_F64)
+    bed = O.OracleBed(sample)
+    bed.step(args.warmup)
+    t0 = time.perf_counter()
+    bed.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = sample.ncell * args.steps / dt / 1e6
+    desc = (f"{args.steps} oracle steps of a {sample.n[0]}x{sample.n[1]} slab of the riser "
+            f"({sample.n_particles} particles, same solid fraction)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / max(args.steps, 1) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(full, args.gpus, args.storage),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ main
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_main(args, rank, world)
+        return
+
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1303_2653_gb300 import lbdps as L
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = workload(args.storage)
+    bed = L.Bed(w)
+    st = bed.stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    bed.step(args.warmup)
+    bed.sync()
+
+    # ---- timed region: K steps, L2 flushed (untimed) before each ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    with torch.cuda.stream(st):
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(st)
+            bed.step(1)
+            ev[k][1].record(st)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    health = bed.health()
+    value = world * w.ncell * args.steps / (total_ms / 1e3) / 1e6
+
+    # ---- dominant-kernel roofline from per-kernel events (L2 flushed) ----
+    prof_steps = min(args.steps, 200)
+    acc = {}
+    with torch.cuda.stream(st):
+        for _ in range(prof_steps):
+            flush.zero_()
+            torch.cuda._sleep(2_000_000)
+            for k, v in bed.step_profiled(1).items():
+                acc[k] = acc.get(k, 0.0) + v
+    per_kernel_ms = {k: v / prof_steps for k, v in acc.items()}
+    alg_bytes, per_cell, per_particle = collide_stream_bytes(w, args.storage)
+    peak, peak_kind = measured_peaks()
+    cs_ms = per_kernel_ms["collide_stream"]
+    achieved = alg_bytes / (cs_ms / 1e3) / 1e9
+    traffic = profiled_traffic()
+    roofline = {"bound": "hbm", "kernel": "collide_stream", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": traffic, "algorithmic_bytes": alg_bytes,
+                "bytes_per_cell": per_cell, "bytes_per_particle": per_particle,
+                "per_kernel_ms": per_kernel_ms}
+
+    # ---- end to end through the C ABI from host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b2 = L.Bed(w)                      # H2D of the particle state from host arrays
+        for _ in range(args.steps):
+            b2.step(1)
+            b2.stats()                     # D2H of the FP64 reductions, every step
+        P, V = b2.particles()              # D2H of the final particle state
+        b2.sync()
+        t_e2e = time.perf_counter() - t0
+        b2.close()
+        real = 8 if args.storage == "f64" else 4
+        h2d = w.n_particles * (w.dim * 8 + w.dim * real + 4)
+        d2h_step = 7 * 8 + 4
+        d2h_final = w.n_particles * (w.dim * 8 + w.dim * real + 4)
+        e2e = {"value": world * w.ncell * args.steps / t_e2e / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps,
+               "d2h_bytes_per_step": d2h_step + d2h_final / args.steps,
+               "includes": "create from host arrays, K x (step + stats readback), final "
+                           "particle readback"}
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n_st, secs = oracle_rate(w.with_(storage=0), 15.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n_st} FP64 oracle steps of the full bed ({secs:.1f} s, one thread)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.storage == "f64" else "f32",
+                "data": "synthetic", "config": config_dict(w, world, args.storage),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": KERNELS_PER_STEP * args.steps * world,
+                "clocks": clock_info, "health": health,
+                "particle_updates_per_s": world * w.n_particles * args.steps / (total_ms / 1e3)}
+        print(json.dumps(line), flush=True)
+    bed.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * lbdps.h — C ABI of the GB300 (sm_103a) library for the coupled time step of
+ * the lattice-Boltzmann based discrete particle simulation of Wang, Zhang,
+ * Wang, Ge and Li, "Lattice Boltzmann based discrete simulation for gas-solid
+ * fluidization" (arXiv 1303.2653).
+ *
+ * One step (the paper's Fig. 4, steps 2-6) advances:
+ *   - deposition of solid velocity and voidage on the lattice (Eq. 8, 10, 11),
+ *   - the modified LBE collide-and-stream with partially saturated cells,
+ *     EMMS correction and optional Smagorinsky LES (Eq. 2-7, 9, 12-15, 20,
+ *     23-25),
+ *   - the interpolated EMMS/Ergun drag rescaled by Newton's third law and the
+ *     particle integration (Eq. 16, 19-22, 26-28),
+ *   - the time-driven hard-sphere step: cell binning, contact detection and
+ *     binary collisions (section 2.2, Eq. 17-18).
+ *
+ * Conventions
+ *   - Every function returning int returns LBDPS_OK (0) or a negative
+ *     LBDPS_ERR_* code; nothing else crosses the ABI.  lbdps_last_error()
+ *     returns a message for the most recent failure on the calling thread.
+ *   - All pointer arguments are plain host pointers unless stated otherwise.
+ *     Inputs are copied; the caller keeps ownership of its arrays.
+ *   - Device memory is owned by the handle.  It is obtained from params.alloc
+ *     (for example a framework's caching allocator) or, when that is NULL,
+ *     from cudaMalloc, and released at lbdps_destroy.
+ *   - Work is issued on params.stream (a cudaStream_t, NULL = a stream the
+ *     handle creates).  lbdps_step is asynchronous; functions that return
+ *     host data synchronise that stream first.
+ *   - A handle is not thread safe: use one handle per thread.
+ *   - Lattice units: cell size h = 1, time step dt = 1, reference gas
+ *     density 1.  SI inputs are converted at create (the paper's Tables 1-2
+ *     list both forms).
+ *   - Axes: x, y (and z in 3D); the last axis is vertical.  Cells are stored
+ *     x-fastest; a cell index is x + nx*(y + ny*z).
+ */
+#ifndef LBDPS_H
+#define LBDPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define LBDPS_OK            0
+#define LBDPS_ERR_INVALID  (-1)  /* bad argument or description           */
+#define LBDPS_ERR_OOM      (-2)  /* allocation failed                      */
+#define LBDPS_ERR_CAPACITY (-3)  /* a caller buffer or table is too small  */
+#define LBDPS_ERR_DIVERGED (-4)  /* NaN/Inf, rho <= 0 or |u| > 0.3 seen    */
+#define LBDPS_ERR_DOMAIN   (-5)  /* a particle left the domain             */
+#define LBDPS_ERR_TIMEOUT  (-6)  /* a bounded device wait gave up          */
+#define LBDPS_ERR_CUDA     (-7)  /* a CUDA runtime call failed             */
+
+/* ---- face types (lbdps_lattice_desc.bc) ------------------------------ */
+#define LBDPS_WALL      0  /* half-way bounce-back for the gas, specular wall for particles */
+#define LBDPS_PERIODIC  1
+#define LBDPS_INLET     2  /* velocity inlet, vertical axis only; particles reflect          */
+#define LBDPS_OUTLET    3  /* pressure outlet (rho = 1), vertical axis only; particles reflect */
+
+/* ---- population storage (lbdps_params.storage) ---------------------- */
+#define LBDPS_STORE_F64   0  /* FP64 deviations f_i - w_i, FP64 arithmetic          */
+#define LBDPS_STORE_F32   1  /* FP32 deviations f_i - w_i, FP32 arithmetic          */
+#define LBDPS_STORE_F16   2  /* FP16 of (f_i - w_i) * 2^10, FP32 arithmetic         */
+#define LBDPS_STORE_BF16  3  /* BF16 of (f_i - w_i), FP32 arithmetic                */
+
+/* ---- units of exported data ----------------------------------------- */
+#define LBDPS_UNITS_LATTICE 0
+#define LBDPS_UNITS_SI      1
+
+/* ---- node fields of the last step (lbdps_fields mask bits) ---------- */
+#define LBDPS_FIELD_RHO    (1 << 0)  /* gas density, Eq. 5                          (1)   */
+#define LBDPS_FIELD_U      (1 << 1)  /* superficial gas velocity, Eq. 24            (dim) */
+#define LBDPS_FIELD_FPG    (1 << 2)  /* force on the gas from particles, Eq. 25     (dim) */
+#define LBDPS_FIELD_BETA   (1 << 3)  /* inter-phase coefficient, Eq. 19             (1)   */
+/* the following need params.diagnostics = 1 */
+#define LBDPS_FIELD_VS     (1 << 4)  /* mean solid velocity, Eq. 8                  (dim) */
+#define LBDPS_FIELD_NTOT   (1 << 5)  /* particles per cell, Fig. 1                  (1)   */
+#define LBDPS_FIELD_TAU_T  (1 << 6)  /* LES relaxation time, Eq. 15                 (1)   */
+#define LBDPS_FIELD_UACT   (1 << 7)  /* actual (interstitial) gas velocity          (dim) */
+#define LBDPS_FIELD_EPS_G  (1 << 8)  /* gas voidage used by the drag, Eq. 11        (1)   */
+
+/* ---- per-particle diagnostics (lbdps_particle_diag) ----------------- */
+#define LBDPS_PDIAG_FPRE   0  /* pre-estimated drag, Eq. 26 (dim, needs diagnostics) */
+#define LBDPS_PDIAG_FD     1  /* rescaled drag, Eq. 28 (dim, needs diagnostics)      */
+#define LBDPS_PDIAG_BEST   2  /* chosen collision partner id, or -1 (1)             */
+#define LBDPS_PDIAG_WALL   3  /* wall contacts: bit 2a low face, 2a+1 high face (1) */
+#define LBDPS_PDIAG_CELL   4  /* cell index of the particle (1)                     */
+#define LBDPS_PDIAG_ORDER  5  /* ids in cell-sorted order: entry k is the id held
+                                 in sorted slot k (1)                               */
+
+typedef struct lbdps lbdps_t;
+
+/* Lattice and boundaries: the paper's step 1 "size and geometry of the
+ * simulation domain ... boundary conditions" (Fig. 4). */
+typedef struct {
+    int dim;              /* 2 (D2Q9) or 3 (D3Q19)                                 */
+    int n[3];             /* cells per axis; n[2] ignored in 2D                     */
+    int bc[6];            /* face types x-, x+, y-, y+, z-, z+ (LBDPS_WALL ...)     */
+    double h;             /* cell size, m                                          */
+    double dt;            /* time step, s                                          */
+    const double *inlet_u;   /* inlet-face velocities, m/s, (cells of the inlet face) x dim,
+                                face cells x-fastest; NULL = zero; copied          */
+    double wall_u[6][3];  /* wall velocity per face, m/s (moving-wall bounce-back) */
+} lbdps_lattice_desc;
+
+/* Particles: "mass, radius, position and velocity" of section 2.2; one
+ * diameter and density for all (monodisperse).  Particle k has id k. */
+typedef struct {
+    int64_t n;            /* number of particles                                  */
+    double d_p;           /* diameter, m (must not exceed h)                      */
+    double rho_s;         /* solid density, kg/m^3                                */
+    double e;             /* restitution coefficient, Eq. 17-18                   */
+    const double *pos;    /* n x dim centres, m, inside the domain, non-overlapping; copied */
+    const double *vel;    /* n x dim velocities, m/s; copied                      */
+} lbdps_particle_desc;
+
+/* Gas and run parameters. */
+typedef struct {
+    double rho_g;         /* gas density, kg/m^3                                  */
+    double mu_g;          /* gas viscosity, Pa s (tau = 3 nu + 1/2, Eq. 3)         */
+    double g[3];          /* gravity, m/s^2 (particles feel (1 - rho_g/rho_s) g)  */
+    double body_accel[3]; /* gas body acceleration, m/s^2 (Guo forcing)            */
+    double u0[3];         /* initial gas velocity, m/s (equilibrium at rho = 1)    */
+    double cs_smag;       /* Smagorinsky constant C_s of Eq. 12-15; 0 = off        */
+    int superficial_mode; /* actual velocity = u / eps_2d (0), u / eps_g (1), u (2) */
+    int pressure_plus;    /* 1: +V_p grad p as printed in Eq. 16; 0: -V_p grad p   */
+    int storage;          /* LBDPS_STORE_*                                         */
+    int check_every;      /* read the health word every k steps in lbdps_step (0 = never) */
+    int diagnostics;      /* 1: keep the extra node and particle diagnostics       */
+    int use_graph;        /* 1: replay lbdps_step through a captured CUDA graph    */
+    void *stream;         /* cudaStream_t for all work; NULL = the handle's own    */
+    void *(*alloc)(size_t bytes, void *ctx);  /* device allocator, or NULL       */
+    void (*free)(void *ptr, void *ctx);       /* matching release, or NULL       */
+    void *alloc_ctx;
+} lbdps_params;
+
+typedef struct {
+    double mass;                 /* sum of gas populations                          */
+    double gas_momentum[3];      /* sum_i c_i f_i over the lattice                  */
+    double particle_momentum[3]; /* sum m_p v                                       */
+    double mean_eps_g;           /* lattice-mean gas voidage of the last step       */
+    double mean_slip;            /* particle-weighted mean |u_act - v_s| (diagnostics) */
+    int64_t steps;               /* steps taken so far                              */
+    int health;                  /* bitmask: 1 diverged, 2 domain, 4 capacity       */
+} lbdps_stats_t;
+
+/* Create a bed (the paper's step 1, Fig. 4).  Validates the description:
+ * tau > 1/2, |u| < 0.3 in lattice units, d_p <= h, periodic axes of at least
+ * 3 cells, inlet/outlet only on the vertical axis, particles inside the
+ * domain and pairwise at least d_p apart.  Returns LBDPS_ERR_INVALID, _OOM
+ * or _CUDA on failure and leaves *out NULL. */
+int lbdps_create(const lbdps_lattice_desc *lattice, const lbdps_particle_desc *particles,
+                 const lbdps_params *params, lbdps_t **out);
+
+/* Release the handle and all its device memory (waits for its stream). */
+void lbdps_destroy(lbdps_t *h);
+
+/* Advance nsteps coupled steps (Fig. 4 steps 2-6), asynchronously on the
+ * handle's stream.  With check_every > 0 the health word is read every
+ * check_every steps and LBDPS_ERR_DIVERGED / _DOMAIN is returned. */
+int lbdps_step(lbdps_t *h, int64_t nsteps);
+
+/* Advance nsteps steps launching each kernel separately with CUDA events
+ * around it; kernel_ms[k] receives the summed milliseconds of kernel class k
+ * (order: collide_stream, drag_pre, drag_integrate, sort, collide_particles),
+ * cap entries at most.  Returns the number of classes in *nclass. */
+int lbdps_step_profiled(lbdps_t *h, int64_t nsteps, double *kernel_ms, int cap, int *nclass);
+
+/* Wait for the handle's stream. */
+int lbdps_sync(lbdps_t *h);
+
+/* Copy node fields of the last step (collision-time values, Eq. 5, 24, 25,
+ * 19) into out: for each bit of mask in increasing order, ncell values (or
+ * ncell x dim, cell-major) as double.  cap is the capacity of out in doubles;
+ * LBDPS_ERR_CAPACITY if too small.  Bits LBDPS_FIELD_VS and above need
+ * params.diagnostics = 1.  units: LBDPS_UNITS_LATTICE or _SI. */
+int lbdps_fields(lbdps_t *h, int mask, int units, double *out, size_t cap);
+
+/* Copy the particle state (section 2.2: P, v) in id order, n x dim each.
+ * cap is the capacity of each array in particles. */
+int lbdps_particles(lbdps_t *h, int units, double *pos, double *vel, int64_t cap);
+
+/* Replace the particle state: n particles in id order, lattice units,
+ * n x dim each; sorts them into cells.  Same validation as create. */
+int lbdps_set_particles(lbdps_t *h, int64_t n, const double *pos, const double *vel);
+
+/* Copy the pre-collision populations f_i (full values, Eq. 2) as double,
+ * layout [q][cell]; cap in doubles (>= q * ncell). */
+int lbdps_populations(lbdps_t *h, double *f, size_t cap);
+
+/* Replace the populations (full values, [q][cell]); each value is rounded
+ * to the storage format as the deviation f_i - w_i. */
+int lbdps_set_populations(lbdps_t *h, const double *f, size_t count);
+
+/* Per-particle diagnostics of the last step in id order (LBDPS_PDIAG_*),
+ * as double; cap in doubles. */
+int lbdps_particle_diag(lbdps_t *h, int which, double *out, size_t cap);
+
+/* The particle half of step 6 alone on the current state: sort into cells,
+ * detect approaching contacts (section 2.2) and apply Eq. 17-18.  When pairs
+ * is not NULL the approaching contact pairs (id_i < id_j) are written as
+ * 2*count int64 in increasing (id_i, id_j) order, cap pairs at most;
+ * *npairs receives the total (LBDPS_ERR_CAPACITY if it exceeds cap). */
+int lbdps_collide_particles(lbdps_t *h, int64_t *pairs, int64_t cap, int64_t *npairs);
+
+/* Deterministic FP64 reductions of the current state. */
+int lbdps_stats(lbdps_t *h, lbdps_stats_t *out);
+
+/* Health bitmask (1 diverged, 2 domain, 4 capacity) accumulated so far. */
+int lbdps_health(lbdps_t *h, int *health);
+
+/* Lattice-unit constants derived at create, in this order: tau, nu, mu,
+ * rho_s/rho_g, d, r, V_p, m_p, e, g_eff[3], F_b[3], u0[3], C_s. */
+int lbdps_constants(lbdps_t *h, double *out, int cap);
+
+/* Shape queries. */
+int lbdps_shape(lbdps_t *h, int *dim, int *q, int64_t *ncell, int64_t *nparticles);
+
+/* Checkpoint: raw populations, particle arrays, cell list and step count.
+ * lbdps_save writes at most cap bytes into buf (NULL buf: only *used is
+ * set to the size needed).  lbdps_load restores a checkpoint made by a
+ * handle of the same shape and storage; the continuation is bit-identical. */
+int lbdps_save(lbdps_t *h, void *buf, size_t cap, size_t *used);
+int lbdps_load(lbdps_t *h, const void *buf, size_t size);
+
+/* Message text of a status code, and of the last failure on this thread. */
+const char *lbdps_strerror(int code);
+const char *lbdps_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBDPS_H */

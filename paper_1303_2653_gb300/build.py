@@ -33,3 +33,53 @@ def build_workloads(force: bool = False) -> str:
                        check=True)
         os.replace(tmp, out)
     return out
+
+
+CU_SOURCES = ["lbm_kernels.cu", "particle_kernels.cu", "stats_kernels.cu", "lbdps_api.cu"]
+HEADERS = ["lbdps_internal.cuh"]
+
+
+def nvcc_flags(extra=()):
+    return ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O2",
+            f"-I{INCLUDE}", f"-I{CSRC}", *extra]
+
+
+def build_lbdps(force: bool = False, verbose_ptxas: bool = False, jobs: int = 4) -> str:
+    """Compile the CUDA library into ``liblbdps.so`` next to this file."""
+    out = os.path.join(HERE, "liblbdps.so")
+    srcs = [os.path.join(CSRC, s) for s in CU_SOURCES]
+    deps = srcs + [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "lbdps.h")]
+    if not force and _newer(out, deps):
+        return out
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+
+    def compile_one(src):
+        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+        cmd = ["nvcc", *nvcc_flags(extra), "-c", src, "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        return obj, r.stderr
+
+    with _cf.ThreadPoolExecutor(max_workers=jobs) as ex:
+        results = list(ex.map(compile_one, srcs))
+    if verbose_ptxas:
+        for _, log in results:
+            print(log)
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["nvcc", *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def build_all(force: bool = False) -> None:
+    build_workloads(force)
+    build_lbdps(force)
+
+
+if __name__ == "__main__":
+    import sys
+    build_workloads(force=True)
+    print(build_lbdps(force=True, verbose_ptxas="-v" in sys.argv))

@@ -1,0 +1,1211 @@
+// Host side of the C ABI declared in include/lbdps.h: validation, unit
+// conversion, device memory, the step sequence (optionally replayed from a
+// captured CUDA graph), data transfer, reductions and checkpoints.
+#include "lbdps.h"
+#include "lbdps_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace lbdpsk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(LBDPS_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),  \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+#define CHECK_LAUNCH()                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = cudaGetLastError();                                              \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(LBDPS_ERR_CUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+// Lattice-unit constants (h = 1, dt = 1, reference gas density 1).
+struct Derived {
+    double nu, mu, tau, rho_s, d, r, vp, mp, e;
+    double geff[3], fb[3], u0[3], wall_u[6][3];
+    double cs;
+};
+
+constexpr double kPi = 3.141592653589793238462643383;
+
+Derived derive(const lbdps_lattice_desc &L, const lbdps_particle_desc &Pd, const lbdps_params &P)
+{
+    Derived k{};
+    const double nu_si = P.mu_g / P.rho_g;
+    k.nu = nu_si * L.dt / (L.h * L.h);
+    k.mu = k.nu;
+    k.tau = 3.0 * k.nu + 0.5;                          // Eq. 3
+    k.rho_s = Pd.rho_s / P.rho_g;
+    k.d = Pd.d_p / L.h;
+    k.r = 0.5 * k.d;
+    k.vp = kPi * k.d * k.d * k.d / 6.0;
+    k.mp = k.rho_s * k.vp;
+    k.e = Pd.e;
+    const double gscale = L.dt * L.dt / L.h, uscale = L.dt / L.h;
+    for (int a = 0; a < 3; ++a) {
+        k.geff[a] = (1.0 - P.rho_g / Pd.rho_s) * P.g[a] * gscale;   // effective gravity (section 3)
+        k.fb[a] = P.body_accel[a] * gscale;
+        k.u0[a] = P.u0[a] * uscale;
+    }
+    for (int f = 0; f < 6; ++f)
+        for (int a = 0; a < 3; ++a) k.wall_u[f][a] = L.wall_u[f][a] * uscale;
+    k.cs = P.cs_smag;
+    return k;
+}
+
+struct DeviceAlloc {
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*release)(void *, void *) = nullptr;
+    void *ctx = nullptr;
+    std::vector<void *> owned;
+
+    void *get(size_t bytes)
+    {
+        bytes = (bytes + 255) & ~size_t(255);
+        if (bytes == 0) bytes = 256;
+        void *p = nullptr;
+        if (alloc) {
+            p = alloc(bytes, ctx);
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (p) owned.push_back(p);
+        return p;
+    }
+    void release_all()
+    {
+        for (void *p : owned) {
+            if (release) release(p, ctx);
+            else cudaFree(p);
+        }
+        owned.clear();
+    }
+};
+
+// Interface of one (lattice, arithmetic, storage) instantiation.
+struct Engine {
+    virtual ~Engine() {}
+    virtual int allocate(DeviceAlloc &A) = 0;
+    virtual int upload_initial(const double *pos_lat, const double *vel_lat) = 0;
+    virtual int enqueue_step(int parity, cudaEvent_t *ev) = 0;
+    virtual int fields(int mask, int units, double *out, size_t cap) = 0;
+    virtual int particles(int units, double *pos, double *vel, int64_t cap) = 0;
+    virtual int set_particles(const double *pos, const double *vel) = 0;
+    virtual int populations(double *f, size_t cap) = 0;
+    virtual int set_populations(const double *f, size_t count) = 0;
+    virtual int particle_diag(int which, double *out, size_t cap) = 0;
+    virtual int collide_particles(int64_t *pairs, int64_t cap, int64_t *npairs) = 0;
+    virtual int stats(lbdps_stats_t *out) = 0;
+    virtual int health(unsigned *out) = 0;
+    virtual size_t checkpoint_bytes() const = 0;
+    virtual int save(char *buf) = 0;
+    virtual int load(const char *buf) = 0;
+};
+
+}  // namespace
+
+struct lbdps {
+    int dim = 0, q = 0;
+    int n[3] = {1, 1, 1};
+    int ncell = 0, np = 0;
+    int bc[6] = {0, 0, 0, 0, 0, 0};
+    double h = 1.0, dt = 1.0;
+    lbdps_params prm{};
+    Derived k{};
+    int ntab = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    DeviceAlloc mem;
+    std::unique_ptr<Engine> eng;
+    int parity = 0;
+    int64_t steps = 0;
+    int64_t since_check = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    unsigned *health_host = nullptr;   // pinned
+    std::vector<double> inlet_lat;     // face cells x dim
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Engine for one instantiation.
+// ---------------------------------------------------------------------------
+template <class L, class Real, class S> struct EngineT : Engine {
+    static constexpr int D = L::D, Q = L::Q;
+    lbdps *H;
+    S *f[2] = {nullptr, nullptr};
+    Fields<Real> fld{};
+    Particles<Real> part[2]{};
+    int *cell_start[2] = {nullptr, nullptr};
+    int *key = nullptr, *counts = nullptr, *tmp = nullptr, *block_sums = nullptr;
+    Real *fpre = nullptr, *gradp = nullptr, *diag_fpre = nullptr, *diag_fd = nullptr;
+    int *best = nullptr, *wall = nullptr;
+    Real *tabs[10] = {};
+    int *tab_branch = nullptr;
+    Real *inlet_dev = nullptr;
+    unsigned *health_dev = nullptr;
+    double *red_partials = nullptr, *red_out = nullptr;
+    unsigned long long *npairs_dev = nullptr;
+    StepParams<Real> sp{};
+
+    explicit EngineT(lbdps *h) : H(h) {}
+
+    int allocate(DeviceAlloc &A) override
+    {
+        const size_t nc = (size_t)H->ncell, np = (size_t)std::max(H->np, 1);
+        auto get = [&](size_t bytes) { return A.get(bytes); };
+        for (int b = 0; b < 2; ++b) {
+            f[b] = (S *)get(sizeof(S) * Q * nc);
+            cell_start[b] = (int *)get(sizeof(int) * (nc + 1));
+            for (int a = 0; a < D; ++a) {
+                part[b].P[a] = (double *)get(sizeof(double) * np);
+                part[b].v[a] = (Real *)get(sizeof(Real) * np);
+                part[b].off[a] = (Real *)get(sizeof(Real) * np);
+            }
+            part[b].id = (int *)get(sizeof(int) * np);
+            part[b].cell = (int *)get(sizeof(int) * np);
+        }
+        fld.rho = (Real *)get(sizeof(Real) * nc);
+        fld.beta = (Real *)get(sizeof(Real) * nc);
+        for (int a = 0; a < D; ++a) {
+            fld.u[a] = (Real *)get(sizeof(Real) * nc);
+            fld.fpg[a] = (Real *)get(sizeof(Real) * nc);
+        }
+        if (H->prm.diagnostics) {
+            fld.tau_t = (Real *)get(sizeof(Real) * nc);
+            fld.eps_g = (Real *)get(sizeof(Real) * nc);
+            fld.ntot = (int *)get(sizeof(int) * nc);
+            for (int a = 0; a < D; ++a) {
+                fld.vs[a] = (Real *)get(sizeof(Real) * nc);
+                fld.uact[a] = (Real *)get(sizeof(Real) * nc);
+            }
+            diag_fpre = (Real *)get(sizeof(Real) * D * np);
+            diag_fd = (Real *)get(sizeof(Real) * D * np);
+        }
+        key = (int *)get(sizeof(int) * np);
+        counts = (int *)get(sizeof(int) * nc);
+        tmp = (int *)get(sizeof(int) * np);
+        block_sums = (int *)get(sizeof(int) * (scan_block_count(H->ncell) + 1));
+        fpre = (Real *)get(sizeof(Real) * D * np);
+        gradp = (Real *)get(sizeof(Real) * D * np);
+        best = (int *)get(sizeof(int) * np);
+        wall = (int *)get(sizeof(int) * np);
+        for (int t = 0; t < 10; ++t) tabs[t] = (Real *)get(sizeof(Real) * H->ntab);
+        tab_branch = (int *)get(sizeof(int) * H->ntab);
+        const int nface = (int)(H->inlet_lat.size() / D);
+        inlet_dev = (Real *)get(sizeof(Real) * D * std::max(nface, 1));
+        health_dev = (unsigned *)get(sizeof(unsigned));
+        red_partials = (double *)get(sizeof(double) * 7 * 1024);
+        red_out = (double *)get(sizeof(double) * 8);
+        npairs_dev = (unsigned long long *)get(sizeof(unsigned long long));
+        void *must[] = {f[0], f[1], cell_start[0], cell_start[1], fld.rho, fld.beta, key, counts,
+                        tmp, block_sums, fpre, gradp, best, wall, tab_branch, inlet_dev, health_dev,
+                        red_partials, red_out, npairs_dev, part[0].id, part[1].id,
+                        part[0].cell, part[1].cell};
+        for (void *p : must)
+            if (!p) return fail(LBDPS_ERR_OOM, "device allocation failed");
+        for (int a = 0; a < D; ++a)
+            if (!fld.u[a] || !fld.fpg[a] || !part[0].P[a] || !part[1].P[a] || !part[0].v[a] ||
+                !part[1].v[a] || !part[0].off[a] || !part[1].off[a])
+                return fail(LBDPS_ERR_OOM, "device allocation failed");
+        for (int t = 0; t < 10; ++t)
+            if (!tabs[t]) return fail(LBDPS_ERR_OOM, "device allocation failed");
+        if (H->prm.diagnostics && (!fld.tau_t || !fld.eps_g || !fld.ntot || !diag_fpre || !diag_fd))
+            return fail(LBDPS_ERR_OOM, "device allocation failed");
+        fill_params();
+        return LBDPS_OK;
+    }
+
+    void fill_params()
+    {
+        const Derived &k = H->k;
+        StepParams<Real> &p = sp;
+        p.dim = D;
+        for (int a = 0; a < 3; ++a) p.n[a] = H->n[a];
+        p.ncell = H->ncell;
+        for (int f6 = 0; f6 < 6; ++f6) p.bc[f6] = H->bc[f6];
+        p.vert = D - 1;
+        p.tau = (Real)k.tau;
+        p.inv_tau = (Real)(1.0 / k.tau);
+        p.les_k = (Real)(18.0 * k.cs * k.cs);
+        p.has_fb = 0;
+        for (int a = 0; a < 3; ++a) {
+            p.fb[a] = (Real)k.fb[a];
+            if (k.fb[a] != 0.0) p.has_fb = 1;
+            p.geff[a] = (Real)k.geff[a];
+        }
+        for (int f6 = 0; f6 < 6; ++f6)
+            for (int a = 0; a < 3; ++a) p.wall_u[f6][a] = (Real)k.wall_u[f6][a];
+        p.mu = (Real)k.mu;
+        p.d = (Real)k.d;
+        p.r = (Real)k.r;
+        p.vp = (Real)k.vp;
+        p.mp = (Real)k.mp;
+        p.e = (Real)k.e;
+        p.psign = H->prm.pressure_plus ? Real(1) : Real(-1);
+        p.d2 = k.d * k.d;
+        p.r64 = k.r;
+        for (int a = 0; a < 3; ++a) {
+            p.len[a] = (double)H->n[a];
+            p.len_below[a] = std::nextafter((double)H->n[a], 0.0);
+        }
+        CountTables<Real> &t = p.tab;
+        t.eps_s = tabs[0];
+        t.eps_g = tabs[1];
+        t.inv_div = tabs[2];
+        t.og = tabs[3];
+        t.gam = tabs[4];
+        t.beta_a = tabs[5];
+        t.beta_b = tabs[6];
+        t.beta_c = tabs[7];
+        t.re_k = tabs[8];
+        t.sol_g = tabs[9];
+        t.branch = tab_branch;
+        t.ntab = H->ntab;
+        p.inlet_u = inlet_dev;
+        p.inlet_face = -1;
+        for (int f6 = 0; f6 < 6; ++f6)
+            if (H->bc[f6] == BC_INLET) p.inlet_face = f6;
+        p.health = health_dev;
+    }
+
+    int upload_initial(const double *pos_lat, const double *vel_lat) override
+    {
+        cudaStream_t st = H->stream;
+        const Derived &k = H->k;
+        launch_build_tables<Real>(D, k.tau, k.r, k.vp, k.d, k.mu, H->prm.superficial_mode, H->ntab,
+                                  nullptr, sp.tab, st);
+        CHECK_LAUNCH();
+        Real u0[3] = {(Real)k.u0[0], (Real)k.u0[1], (Real)k.u0[2]};
+        launch_init_equilibrium<L, Real, S>(H->ncell, u0, f[0], st);
+        CHECK_LAUNCH();
+        if (!H->inlet_lat.empty()) {
+            std::vector<Real> tmpu(H->inlet_lat.begin(), H->inlet_lat.end());
+            CU(cudaMemcpyAsync(inlet_dev, tmpu.data(), sizeof(Real) * tmpu.size(),
+                               cudaMemcpyHostToDevice, st));
+            CU(cudaStreamSynchronize(st));
+        }
+        CU(cudaMemsetAsync(health_dev, 0, sizeof(unsigned), st));
+        CU(cudaMemsetAsync(counts, 0, sizeof(int) * H->ncell, st));
+        if (H->np == 0) {
+            CU(cudaMemsetAsync(cell_start[0], 0, sizeof(int) * (H->ncell + 1), st));
+            CU(cudaMemsetAsync(cell_start[1], 0, sizeof(int) * (H->ncell + 1), st));
+            return LBDPS_OK;
+        }
+        return set_particles(pos_lat, vel_lat);
+    }
+
+    // Load particles (lattice units, id order) into the current buffers and sort them.
+    int set_particles(const double *pos, const double *vel) override
+    {
+        cudaStream_t st = H->stream;
+        const int np = H->np;
+        const int cur = H->parity, nxt = 1 - cur;
+        if (np == 0) return LBDPS_OK;
+        std::vector<double> Pa((size_t)np);
+        std::vector<Real> va((size_t)np);
+        std::vector<int> ids((size_t)np);
+        for (int i = 0; i < np; ++i) ids[i] = i;
+        // stage into the next buffers, then sort into the current ones
+        for (int a = 0; a < D; ++a) {
+            for (int i = 0; i < np; ++i) {
+                Pa[i] = pos[(size_t)i * D + a];
+                va[i] = (Real)vel[(size_t)i * D + a];
+            }
+            CU(cudaMemcpyAsync(part[nxt].P[a], Pa.data(), sizeof(double) * np,
+                               cudaMemcpyHostToDevice, st));
+            CU(cudaMemcpyAsync(part[nxt].v[a], va.data(), sizeof(Real) * np,
+                               cudaMemcpyHostToDevice, st));
+            CU(cudaStreamSynchronize(st));
+        }
+        CU(cudaMemcpyAsync(part[nxt].id, ids.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+        CU(cudaStreamSynchronize(st));
+        return sort_from(nxt, cur);
+    }
+
+    // Sort particles held in buffer `src` (any order) into buffer `dst` by (cell, id).
+    int sort_from(int src, int dst)
+    {
+        cudaStream_t st = H->stream;
+        CU(cudaMemsetAsync(counts, 0, sizeof(int) * H->ncell, st));
+        launch_cell_keys<D, Real>(H->n, part[src], key, counts, H->np, st);
+        CHECK_LAUNCH();
+        launch_scan(counts, cell_start[dst], block_sums, H->ncell, st);
+        CHECK_LAUNCH();
+        launch_scatter_gather<Real>(H->ncell, D, key, counts, cell_start[dst], tmp, part[src],
+                                    part[dst], H->np, st);
+        CHECK_LAUNCH();
+        return LBDPS_OK;
+    }
+
+    // One coupled step from buffers `parity` into buffers `1 - parity`.
+    // ev (optional, 6 events) brackets the kernel classes for profiling.
+    int enqueue_step(int parity, cudaEvent_t *ev) override
+    {
+        cudaStream_t st = H->stream;
+        const int a = parity, b = 1 - parity;
+        const int np = H->np;
+        if (ev) CU(cudaEventRecord(ev[0], st));
+        launch_collide_stream<L, Real, S>(sp, f[a], f[b], cell_start[a], part[a], fld, st);
+        CHECK_LAUNCH();
+        if (ev) CU(cudaEventRecord(ev[1], st));
+        launch_drag_pre<D, Real>(sp, part[a], cell_start[a], fld, fpre, gradp, np, st);
+        CHECK_LAUNCH();
+        if (ev) CU(cudaEventRecord(ev[2], st));
+        launch_drag_integrate<D, Real>(sp, part[a], cell_start[a], fld, fpre, gradp, key, counts,
+                                       diag_fpre, diag_fd, np, st);
+        CHECK_LAUNCH();
+        if (ev) CU(cudaEventRecord(ev[3], st));
+        if (np > 0) {
+            launch_scan(counts, cell_start[b], block_sums, H->ncell, st);
+            CHECK_LAUNCH();
+            launch_scatter_gather<Real>(H->ncell, D, key, counts, cell_start[b], tmp, part[a],
+                                        part[b], np, st);
+            CHECK_LAUNCH();
+        } else {
+            CU(cudaMemsetAsync(cell_start[b], 0, sizeof(int) * (H->ncell + 1), st));
+        }
+        if (ev) CU(cudaEventRecord(ev[4], st));
+        launch_detect<D, Real>(sp, part[b], cell_start[b], best, wall, nullptr, nullptr, 0, np, st);
+        CHECK_LAUNCH();
+        launch_resolve<D, Real>(sp, part[b], best, wall, np, st);
+        CHECK_LAUNCH();
+        if (ev) CU(cudaEventRecord(ev[5], st));
+        return LBDPS_OK;
+    }
+
+    int collide_particles(int64_t *pairs_out, int64_t cap, int64_t *npairs) override
+    {
+        cudaStream_t st = H->stream;
+        const int cur = H->parity, oth = 1 - cur;
+        const int np = H->np;
+        if (np == 0) {
+            if (npairs) *npairs = 0;
+            return LBDPS_OK;
+        }
+        // re-sort the current particles (positions may have been replaced)
+        int rc = copy_particles(cur, oth);
+        if (rc) return rc;
+        rc = sort_from(oth, cur);
+        if (rc) return rc;
+        long long *pairs_dev = nullptr;
+        long long pcap = 0;
+        std::vector<long long> hp;
+        if (pairs_out) {
+            pcap = std::max<int64_t>(cap, 1);
+            if (cudaMalloc(&pairs_dev, sizeof(long long) * 2 * pcap) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(LBDPS_ERR_OOM, "pair buffer allocation failed");
+            }
+        }
+        CU(cudaMemsetAsync(npairs_dev, 0, sizeof(unsigned long long), st));
+        launch_detect<D, Real>(sp, part[cur], cell_start[cur], best, wall, pairs_dev, npairs_dev,
+                               pcap, np, st);
+        CHECK_LAUNCH();
+        launch_resolve<D, Real>(sp, part[cur], best, wall, np, st);
+        CHECK_LAUNCH();
+        unsigned long long total = 0;
+        CU(cudaMemcpyAsync(&total, npairs_dev, sizeof(total), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        int result = LBDPS_OK;
+        if (pairs_out) {
+            const int64_t got = std::min<int64_t>((int64_t)total, cap);
+            hp.resize((size_t)std::max<int64_t>(got, 1) * 2);
+            if (got > 0) {
+                cudaError_t e = cudaMemcpy(hp.data(), pairs_dev, sizeof(long long) * 2 * got,
+                                           cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) result = fail(LBDPS_ERR_CUDA, "pair copy: %s", cudaGetErrorString(e));
+            }
+            std::vector<std::pair<long long, long long>> pr((size_t)got);
+            for (int64_t i = 0; i < got; ++i) pr[i] = {hp[2 * i], hp[2 * i + 1]};
+            std::sort(pr.begin(), pr.end());
+            for (int64_t i = 0; i < got; ++i) {
+                pairs_out[2 * i] = pr[i].first;
+                pairs_out[2 * i + 1] = pr[i].second;
+            }
+            cudaFree(pairs_dev);
+            if (result == LBDPS_OK && (int64_t)total > cap)
+                result = fail(LBDPS_ERR_CAPACITY, "%llu pairs exceed capacity %lld", total, (long long)cap);
+        }
+        if (npairs) *npairs = (int64_t)total;
+        return result;
+    }
+
+    int copy_particles(int from, int to)
+    {
+        cudaStream_t st = H->stream;
+        const size_t np = (size_t)H->np;
+        for (int a = 0; a < D; ++a) {
+            CU(cudaMemcpyAsync(part[to].P[a], part[from].P[a], sizeof(double) * np,
+                               cudaMemcpyDeviceToDevice, st));
+            CU(cudaMemcpyAsync(part[to].v[a], part[from].v[a], sizeof(Real) * np,
+                               cudaMemcpyDeviceToDevice, st));
+        }
+        CU(cudaMemcpyAsync(part[to].id, part[from].id, sizeof(int) * np, cudaMemcpyDeviceToDevice, st));
+        return LBDPS_OK;
+    }
+
+    template <class T> int d2h(std::vector<T> &dst, const T *src, size_t n)
+    {
+        dst.resize(std::max<size_t>(n, 1));
+        CU(cudaMemcpyAsync(dst.data(), src, sizeof(T) * n, cudaMemcpyDeviceToHost, H->stream));
+        CU(cudaStreamSynchronize(H->stream));
+        return LBDPS_OK;
+    }
+
+    int fields(int mask, int units, double *out, size_t cap) override
+    {
+        const size_t nc = (size_t)H->ncell;
+        size_t need = 0;
+        const int vec_bits = LBDPS_FIELD_U | LBDPS_FIELD_FPG | LBDPS_FIELD_VS | LBDPS_FIELD_UACT;
+        for (int bit = 0; bit < 9; ++bit)
+            if (mask & (1 << bit)) need += nc * (((1 << bit) & vec_bits) ? D : 1);
+        if (mask & ~((1 << 9) - 1)) return fail(LBDPS_ERR_INVALID, "unknown field bits");
+        if (need > cap) return fail(LBDPS_ERR_CAPACITY, "fields need %zu doubles", need);
+        if ((mask & ~0xF) && !H->prm.diagnostics)
+            return fail(LBDPS_ERR_INVALID, "diagnostic fields need params.diagnostics = 1");
+        const double us = units == LBDPS_UNITS_SI ? H->h / H->dt : 1.0;
+        const double rs = units == LBDPS_UNITS_SI ? H->prm.rho_g : 1.0;
+        // force per cell: rho h^3 (h/dt) / dt in SI
+        const double fs = units == LBDPS_UNITS_SI ? H->prm.rho_g * H->h * H->h * H->h * H->h / (H->dt * H->dt) : 1.0;
+        const double bs = units == LBDPS_UNITS_SI ? H->prm.rho_g / H->dt : 1.0;
+        const double ts = units == LBDPS_UNITS_SI ? H->dt : 1.0;
+        std::vector<Real> hb;
+        std::vector<int> hi;
+        size_t o = 0;
+        auto put_scalar = [&](const Real *src, double scale) -> int {
+            int rc = d2h(hb, src, nc);
+            if (rc) return rc;
+            for (size_t x = 0; x < nc; ++x) out[o + x] = (double)hb[x] * scale;
+            o += nc;
+            return LBDPS_OK;
+        };
+        auto put_vec = [&](Real *const *src, double scale) -> int {
+            for (int a = 0; a < D; ++a) {
+                int rc = d2h(hb, src[a], nc);
+                if (rc) return rc;
+                for (size_t x = 0; x < nc; ++x) out[o + x * D + a] = (double)hb[x] * scale;
+            }
+            o += nc * D;
+            return LBDPS_OK;
+        };
+        int rc = LBDPS_OK;
+        if (mask & LBDPS_FIELD_RHO) if ((rc = put_scalar(fld.rho, rs))) return rc;
+        if (mask & LBDPS_FIELD_U) if ((rc = put_vec(fld.u, us))) return rc;
+        if (mask & LBDPS_FIELD_FPG) if ((rc = put_vec(fld.fpg, fs))) return rc;
+        if (mask & LBDPS_FIELD_BETA) if ((rc = put_scalar(fld.beta, bs))) return rc;
+        if (mask & LBDPS_FIELD_VS) if ((rc = put_vec(fld.vs, us))) return rc;
+        if (mask & LBDPS_FIELD_NTOT) {
+            if ((rc = d2h(hi, fld.ntot, nc))) return rc;
+            for (size_t x = 0; x < nc; ++x) out[o + x] = (double)hi[x];
+            o += nc;
+        }
+        if (mask & LBDPS_FIELD_TAU_T) if ((rc = put_scalar(fld.tau_t, ts))) return rc;
+        if (mask & LBDPS_FIELD_UACT) if ((rc = put_vec(fld.uact, us))) return rc;
+        if (mask & LBDPS_FIELD_EPS_G) if ((rc = put_scalar(fld.eps_g, 1.0))) return rc;
+        return LBDPS_OK;
+    }
+
+    int particles(int units, double *pos, double *vel, int64_t cap) override
+    {
+        const int np = H->np, cur = H->parity;
+        if (cap < np) return fail(LBDPS_ERR_CAPACITY, "need room for %d particles", np);
+        if (np == 0) return LBDPS_OK;
+        std::vector<int> ids;
+        std::vector<double> Pd;
+        std::vector<Real> vd;
+        int rc = d2h(ids, part[cur].id, np);
+        if (rc) return rc;
+        const double ps = units == LBDPS_UNITS_SI ? H->h : 1.0;
+        const double vs = units == LBDPS_UNITS_SI ? H->h / H->dt : 1.0;
+        for (int a = 0; a < D; ++a) {
+            if ((rc = d2h(Pd, part[cur].P[a], np))) return rc;
+            if ((rc = d2h(vd, part[cur].v[a], np))) return rc;
+            for (int k = 0; k < np; ++k) {
+                const size_t o = (size_t)ids[k] * D + a;
+                if (pos) pos[o] = Pd[k] * ps;
+                if (vel) vel[o] = (double)vd[k] * vs;
+            }
+        }
+        return LBDPS_OK;
+    }
+
+    int populations(double *out, size_t cap) override
+    {
+        const size_t total = (size_t)Q * H->ncell;
+        if (cap < total) return fail(LBDPS_ERR_CAPACITY, "need %zu doubles", total);
+        double *dev = nullptr;
+        CU(cudaMalloc(&dev, sizeof(double) * total));
+        launch_export_populations<L, Real, S>(H->ncell, f[H->parity], dev, H->stream);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, dev, sizeof(double) * total, cudaMemcpyDeviceToHost, H->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(H->stream);
+        cudaFree(dev);
+        if (e != cudaSuccess) return fail(LBDPS_ERR_CUDA, "populations: %s", cudaGetErrorString(e));
+        return LBDPS_OK;
+    }
+
+    int set_populations(const double *in, size_t count) override
+    {
+        const size_t total = (size_t)Q * H->ncell;
+        if (count != total) return fail(LBDPS_ERR_INVALID, "expected %zu values", total);
+        double *dev = nullptr;
+        CU(cudaMalloc(&dev, sizeof(double) * total));
+        cudaError_t e = cudaMemcpyAsync(dev, in, sizeof(double) * total, cudaMemcpyHostToDevice, H->stream);
+        if (e == cudaSuccess) {
+            launch_import_populations<L, Real, S>(H->ncell, dev, f[H->parity], H->stream);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(H->stream);
+        cudaFree(dev);
+        if (e != cudaSuccess) return fail(LBDPS_ERR_CUDA, "set_populations: %s", cudaGetErrorString(e));
+        return LBDPS_OK;
+    }
+
+    int particle_diag(int which, double *out, size_t cap) override
+    {
+        const int np = H->np, cur = H->parity;
+        const bool vec = (which == LBDPS_PDIAG_FPRE || which == LBDPS_PDIAG_FD);
+        const size_t need = (size_t)np * (vec ? D : 1);
+        if (cap < need) return fail(LBDPS_ERR_CAPACITY, "need %zu doubles", need);
+        if (np == 0) return LBDPS_OK;
+        int rc;
+        if (vec) {
+            if (!H->prm.diagnostics) return fail(LBDPS_ERR_INVALID, "needs params.diagnostics = 1");
+            std::vector<Real> hb;
+            const Real *src = which == LBDPS_PDIAG_FPRE ? diag_fpre : diag_fd;
+            if ((rc = d2h(hb, src, (size_t)D * np))) return rc;
+            for (int a = 0; a < D; ++a)
+                for (int i = 0; i < np; ++i) out[(size_t)i * D + a] = (double)hb[(size_t)a * np + i];
+            return LBDPS_OK;
+        }
+        std::vector<int> ids, vals;
+        if ((rc = d2h(ids, part[cur].id, np))) return rc;
+        if (which == LBDPS_PDIAG_BEST) {
+            if ((rc = d2h(vals, best, np))) return rc;
+            for (int k = 0; k < np; ++k) out[ids[k]] = vals[k] >= 0 ? (double)ids[vals[k]] : -1.0;
+        } else if (which == LBDPS_PDIAG_WALL) {
+            if ((rc = d2h(vals, wall, np))) return rc;
+            for (int k = 0; k < np; ++k) out[ids[k]] = (double)vals[k];
+        } else if (which == LBDPS_PDIAG_ORDER) {
+            for (int k = 0; k < np; ++k) out[k] = (double)ids[k];
+        } else if (which == LBDPS_PDIAG_CELL) {
+            std::vector<int> cs;
+            if ((rc = d2h(cs, cell_start[cur], (size_t)H->ncell + 1))) return rc;
+            for (int c = 0; c < H->ncell; ++c)
+                for (int k = cs[c]; k < cs[c + 1]; ++k) out[ids[k]] = (double)c;
+        } else {
+            return fail(LBDPS_ERR_INVALID, "unknown diagnostic %d", which);
+        }
+        return LBDPS_OK;
+    }
+
+    int stats(lbdps_stats_t *out) override
+    {
+        double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const int cur = H->parity;
+        launch_reduce_state<L, Real, S>(H->ncell, f[cur], part[cur], H->k.mp, H->np, red_partials,
+                                        red_out, H->stream);
+        CHECK_LAUNCH();
+        CU(cudaMemcpyAsync(v, red_out, sizeof(double) * 7, cudaMemcpyDeviceToHost, H->stream));
+        CU(cudaStreamSynchronize(H->stream));
+        out->mass = v[0] + (double)H->ncell;
+        for (int a = 0; a < 3; ++a) {
+            out->gas_momentum[a] = a < D ? v[1 + a] : 0.0;
+            out->particle_momentum[a] = a < D ? v[4 + a] : 0.0;
+        }
+        out->mean_eps_g = NAN;
+        out->mean_slip = NAN;
+        if (H->prm.diagnostics && H->steps > 0) {
+            const Real *ua[3] = {fld.uact[0], fld.uact[1], D > 2 ? fld.uact[2] : nullptr};
+            const Real *va[3] = {fld.vs[0], fld.vs[1], D > 2 ? fld.vs[2] : nullptr};
+            launch_reduce_bed<Real>(H->ncell, D, fld.eps_g, fld.ntot, ua, va, red_partials, red_out,
+                                    H->stream);
+            CHECK_LAUNCH();
+            CU(cudaMemcpyAsync(v, red_out, sizeof(double) * 3, cudaMemcpyDeviceToHost, H->stream));
+            CU(cudaStreamSynchronize(H->stream));
+            out->mean_eps_g = v[0] / (double)H->ncell;
+            out->mean_slip = v[2] > 0 ? v[1] / v[2] : 0.0;
+        }
+        out->steps = H->steps;
+        unsigned hw = 0;
+        int rc = health(&hw);
+        if (rc) return rc;
+        out->health = (int)hw;
+        return LBDPS_OK;
+    }
+
+    int health(unsigned *out) override
+    {
+        CU(cudaMemcpyAsync(H->health_host, health_word(), sizeof(unsigned), cudaMemcpyDeviceToHost,
+                           H->stream));
+        CU(cudaStreamSynchronize(H->stream));
+        *out = *H->health_host;
+        return LBDPS_OK;
+    }
+    unsigned *health_word() { return this->health_dev; }
+
+    // checkpoint payload: populations, particles (P, v, id), cell list
+    size_t checkpoint_bytes() const override
+    {
+        const size_t nc = (size_t)H->ncell, np = (size_t)H->np;
+        return sizeof(S) * Q * nc + (sizeof(double) + 2 * sizeof(Real)) * D * np +
+               2 * sizeof(int) * np + sizeof(int) * (nc + 1);
+    }
+
+    int save(char *buf) override
+    {
+        cudaStream_t st = H->stream;
+        const size_t nc = (size_t)H->ncell, np = (size_t)H->np;
+        const int cur = H->parity;
+        size_t o = 0;
+        CU(cudaMemcpyAsync(buf + o, f[cur], sizeof(S) * Q * nc, cudaMemcpyDeviceToHost, st));
+        o += sizeof(S) * Q * nc;
+        for (int a = 0; a < D; ++a) {
+            CU(cudaMemcpyAsync(buf + o, part[cur].P[a], sizeof(double) * np, cudaMemcpyDeviceToHost, st));
+            o += sizeof(double) * np;
+            CU(cudaMemcpyAsync(buf + o, part[cur].v[a], sizeof(Real) * np, cudaMemcpyDeviceToHost, st));
+            o += sizeof(Real) * np;
+            CU(cudaMemcpyAsync(buf + o, part[cur].off[a], sizeof(Real) * np, cudaMemcpyDeviceToHost, st));
+            o += sizeof(Real) * np;
+        }
+        CU(cudaMemcpyAsync(buf + o, part[cur].id, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
+        o += sizeof(int) * np;
+        CU(cudaMemcpyAsync(buf + o, part[cur].cell, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
+        o += sizeof(int) * np;
+        CU(cudaMemcpyAsync(buf + o, cell_start[cur], sizeof(int) * (nc + 1), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        return LBDPS_OK;
+    }
+
+    int load(const char *buf) override
+    {
+        cudaStream_t st = H->stream;
+        const size_t nc = (size_t)H->ncell, np = (size_t)H->np;
+        const int cur = H->parity;
+        size_t o = 0;
+        CU(cudaMemcpyAsync(f[cur], buf + o, sizeof(S) * Q * nc, cudaMemcpyHostToDevice, st));
+        o += sizeof(S) * Q * nc;
+        for (int a = 0; a < D; ++a) {
+            CU(cudaMemcpyAsync(part[cur].P[a], buf + o, sizeof(double) * np, cudaMemcpyHostToDevice, st));
+            o += sizeof(double) * np;
+            CU(cudaMemcpyAsync(part[cur].v[a], buf + o, sizeof(Real) * np, cudaMemcpyHostToDevice, st));
+            o += sizeof(Real) * np;
+            CU(cudaMemcpyAsync(part[cur].off[a], buf + o, sizeof(Real) * np, cudaMemcpyHostToDevice, st));
+            o += sizeof(Real) * np;
+        }
+        CU(cudaMemcpyAsync(part[cur].id, buf + o, sizeof(int) * np, cudaMemcpyHostToDevice, st));
+        o += sizeof(int) * np;
+        CU(cudaMemcpyAsync(part[cur].cell, buf + o, sizeof(int) * np, cudaMemcpyHostToDevice, st));
+        o += sizeof(int) * np;
+        CU(cudaMemcpyAsync(cell_start[cur], buf + o, sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, st));
+        CU(cudaMemsetAsync(counts, 0, sizeof(int) * nc, st));
+        CU(cudaStreamSynchronize(st));
+        return LBDPS_OK;
+    }
+};
+
+template <class L>
+Engine *make_engine_l(lbdps *h)
+{
+    switch (h->prm.storage) {
+    case ST_F64: return new (std::nothrow) EngineT<L, double, double>(h);
+    case ST_F32: return new (std::nothrow) EngineT<L, float, float>(h);
+    case ST_F16: return new (std::nothrow) EngineT<L, float, __half>(h);
+    case ST_BF16: return new (std::nothrow) EngineT<L, float, __nv_bfloat16>(h);
+    }
+    return nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// Validation helpers.
+// ---------------------------------------------------------------------------
+int validate_positions(const lbdps *h, const double *pos, bool check_overlap)
+{
+    const int D = h->dim, np = h->np;
+    for (int i = 0; i < np; ++i)
+        for (int a = 0; a < D; ++a) {
+            const double p = pos[(size_t)i * D + a];
+            if (!(p >= 0.0 && p < (double)h->n[a]))
+                return fail(LBDPS_ERR_INVALID, "particle %d lies outside the domain on axis %d", i, a);
+        }
+    if (!check_overlap || np < 2) return LBDPS_OK;
+    // cell list on the lattice itself (cells are at least one diameter wide)
+    std::vector<int> head((size_t)h->ncell, -1), next((size_t)np, -1);
+    auto cell_of = [&](const double *p) {
+        int q[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) q[a] = std::min((int)std::floor(p[a]), h->n[a] - 1);
+        return q[0] + h->n[0] * (q[1] + h->n[1] * q[2]);
+    };
+    for (int i = 0; i < np; ++i) {
+        const int c = cell_of(pos + (size_t)i * D);
+        next[i] = head[c];
+        head[c] = i;
+    }
+    const double d2 = h->k.d * h->k.d;
+    for (int i = 0; i < np; ++i) {
+        const double *pi = pos + (size_t)i * D;
+        int idx[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) idx[a] = std::min((int)std::floor(pi[a]), h->n[a] - 1);
+        for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+            int q[3] = {idx[0] + ox, idx[1] + oy, idx[2] + oz};
+            bool skip = false;
+            for (int a = 0; a < D; ++a) {
+                if (q[a] < 0 || q[a] >= h->n[a]) {
+                    if (h->bc[2 * a] == BC_PERIODIC) q[a] = (q[a] + h->n[a]) % h->n[a];
+                    else skip = true;
+                }
+            }
+            if (skip) continue;
+            const int c = q[0] + h->n[0] * (q[1] + h->n[1] * q[2]);
+            for (int j = head[c]; j >= 0; j = next[j]) {
+                if (j <= i) continue;
+                double s = 0.0;
+                for (int a = 0; a < D; ++a) {
+                    double dd = pi[a] - pos[(size_t)j * D + a];
+                    if (h->bc[2 * a] == BC_PERIODIC) {
+                        const double L = (double)h->n[a];
+                        if (dd > 0.5 * L) dd -= L;
+                        else if (dd < -0.5 * L) dd += L;
+                    }
+                    s += dd * dd;
+                }
+                if (s < d2) return fail(LBDPS_ERR_INVALID, "particles %d and %d overlap", i, j);
+            }
+        }
+    }
+    return LBDPS_OK;
+}
+
+int run_steps(lbdps *h, int64_t nsteps)
+{
+    for (int64_t s = 0; s < nsteps; ++s) {
+        if (h->prm.use_graph) {
+            if (!h->graph[h->parity]) {
+                cudaGraph_t g = nullptr;
+                CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+                int rc = h->eng->enqueue_step(h->parity, nullptr);
+                cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+                if (rc) {
+                    if (g) cudaGraphDestroy(g);
+                    return rc;
+                }
+                if (e != cudaSuccess)
+                    return fail(LBDPS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+                e = cudaGraphInstantiate(&h->graph[h->parity], g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess)
+                    return fail(LBDPS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+            }
+            CU(cudaGraphLaunch(h->graph[h->parity], h->stream));
+        } else {
+            int rc = h->eng->enqueue_step(h->parity, nullptr);
+            if (rc) return rc;
+        }
+        h->parity ^= 1;
+        h->steps++;
+        if (h->prm.check_every > 0 && ++h->since_check >= h->prm.check_every) {
+            h->since_check = 0;
+            int hw = 0;
+            int rc = lbdps_health(h, &hw);
+            if (rc) return rc;
+            if (hw & HEALTH_DIVERGED) return fail(LBDPS_ERR_DIVERGED, "gas state diverged by step %lld", (long long)h->steps);
+            if (hw & HEALTH_DOMAIN) return fail(LBDPS_ERR_DOMAIN, "a particle left the domain by step %lld", (long long)h->steps);
+        }
+    }
+    return LBDPS_OK;
+}
+
+void free_graphs(lbdps *h)
+{
+    for (int p = 0; p < 2; ++p)
+        if (h->graph[p]) {
+            cudaGraphExecDestroy(h->graph[p]);
+            h->graph[p] = nullptr;
+        }
+}
+
+struct CkptHeader {
+    char magic[8];
+    int dim, q, storage, n[3], np, ncell;
+    long long steps;
+    unsigned long long payload;
+};
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
+                 const lbdps_params *prm, lbdps_t **out)
+{
+    if (!out) return fail(LBDPS_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!lat || !par || !prm) return fail(LBDPS_ERR_INVALID, "NULL description");
+    const int D = lat->dim;
+    if (D != 2 && D != 3) return fail(LBDPS_ERR_INVALID, "dim must be 2 or 3");
+    long long ncell = 1;
+    int n[3] = {1, 1, 1};
+    for (int a = 0; a < D; ++a) {
+        if (lat->n[a] < 1) return fail(LBDPS_ERR_INVALID, "n[%d] must be positive", a);
+        n[a] = lat->n[a];
+        ncell *= n[a];
+    }
+    const int Q = D == 2 ? 9 : 19;
+    if (ncell >= (1ll << 31) - 1 || ncell * Q >= (1ll << 40))
+        return fail(LBDPS_ERR_INVALID, "lattice too large");
+    int bc[6];
+    for (int f6 = 0; f6 < 6; ++f6) bc[f6] = lat->bc[f6];
+    if (D == 2) bc[4] = bc[5] = BC_PERIODIC;
+    for (int a = 0; a < D; ++a) {
+        for (int s = 0; s < 2; ++s)
+            if (bc[2 * a + s] < 0 || bc[2 * a + s] > 3)
+                return fail(LBDPS_ERR_INVALID, "unknown face type on face %d", 2 * a + s);
+        if ((bc[2 * a] == BC_PERIODIC) != (bc[2 * a + 1] == BC_PERIODIC))
+            return fail(LBDPS_ERR_INVALID, "axis %d: periodic faces must come in pairs", a);
+        if (bc[2 * a] == BC_PERIODIC && n[a] < 3)
+            return fail(LBDPS_ERR_INVALID, "axis %d: periodic axes need at least 3 cells", a);
+        const bool open = bc[2 * a] >= BC_INLET || bc[2 * a + 1] >= BC_INLET;
+        if (open && a != D - 1)
+            return fail(LBDPS_ERR_INVALID, "inlet/outlet faces only on the vertical axis");
+    }
+    if (bc[2 * (D - 1)] == BC_INLET && bc[2 * (D - 1) + 1] == BC_INLET)
+        return fail(LBDPS_ERR_INVALID, "at most one inlet face");
+    if (!(lat->h > 0) || !(lat->dt > 0)) return fail(LBDPS_ERR_INVALID, "h and dt must be positive");
+    if (par->n < 0 || par->n >= (1ll << 31) - 1) return fail(LBDPS_ERR_INVALID, "bad particle count");
+    if (par->n > 0 && (!par->pos || !par->vel)) return fail(LBDPS_ERR_INVALID, "NULL particle arrays");
+    if (!(par->d_p > 0) || !(par->rho_s > 0) || !(par->e >= 0 && par->e <= 1))
+        return fail(LBDPS_ERR_INVALID, "bad particle properties");
+    if (!(par->d_p <= lat->h)) return fail(LBDPS_ERR_INVALID, "d_p must not exceed h");
+    if (!(prm->rho_g > 0) || !(prm->mu_g > 0)) return fail(LBDPS_ERR_INVALID, "bad gas properties");
+    if (prm->storage < 0 || prm->storage > 3) return fail(LBDPS_ERR_INVALID, "bad storage");
+    if (!(prm->cs_smag >= 0)) return fail(LBDPS_ERR_INVALID, "bad Smagorinsky constant");
+    if (prm->superficial_mode < 0 || prm->superficial_mode > 2)
+        return fail(LBDPS_ERR_INVALID, "bad superficial_mode");
+
+    std::unique_ptr<lbdps> h(new (std::nothrow) lbdps());
+    if (!h) return fail(LBDPS_ERR_OOM, "host allocation failed");
+    h->dim = D;
+    h->q = Q;
+    for (int a = 0; a < 3; ++a) h->n[a] = n[a];
+    h->ncell = (int)ncell;
+    h->np = (int)par->n;
+    for (int f6 = 0; f6 < 6; ++f6) h->bc[f6] = bc[f6];
+    h->h = lat->h;
+    h->dt = lat->dt;
+    h->prm = *prm;
+    h->k = derive(*lat, *par, *prm);
+    const Derived &k = h->k;
+    if (!(k.tau > 0.5) || !std::isfinite(k.tau)) return fail(LBDPS_ERR_INVALID, "tau must exceed 1/2");
+    double u0s = 0;
+    for (int a = 0; a < D; ++a) u0s += k.u0[a] * k.u0[a];
+    if (!(u0s < 0.09)) return fail(LBDPS_ERR_INVALID, "|u0| must be below 0.3 in lattice units");
+    // count tables reach the close-packing cap
+    const double unit = D == 2 ? kPi * k.r * k.r : k.vp;
+    const double cap = D == 2 ? kPi / (2.0 * std::sqrt(3.0)) : kPi / (3.0 * std::sqrt(2.0));
+    const double ncap = std::ceil(cap / unit);
+    if (!(ncap < 4000)) return fail(LBDPS_ERR_INVALID, "particles too small for the cell (d_p/h)");
+    h->ntab = (int)ncap + 2;
+    // inlet velocities
+    int inlet_face = -1;
+    for (int f6 = 0; f6 < 6; ++f6)
+        if (bc[f6] == BC_INLET) inlet_face = f6;
+    if (inlet_face >= 0) {
+        const int nface = (int)(ncell / n[D - 1]);
+        h->inlet_lat.assign((size_t)nface * D, 0.0);
+        if (lat->inlet_u) {
+            const double us = lat->dt / lat->h;
+            for (int j = 0; j < nface; ++j) {
+                double s = 0;
+                for (int a = 0; a < D; ++a) {
+                    const double u = lat->inlet_u[(size_t)j * D + a] * us;
+                    h->inlet_lat[(size_t)j * D + a] = u;
+                    s += u * u;
+                }
+                if (!(s < 0.09)) return fail(LBDPS_ERR_INVALID, "inlet |u| must be below 0.3 in lattice units");
+            }
+        }
+    }
+    // particles in lattice units
+    std::vector<double> pos((size_t)h->np * D), vel((size_t)h->np * D);
+    const double vscale = lat->dt / lat->h;
+    for (size_t i = 0; i < pos.size(); ++i) {
+        pos[i] = par->pos[i] / lat->h;
+        vel[i] = par->vel[i] * vscale;
+    }
+    int rc = validate_positions(h.get(), pos.data(), true);
+    if (rc) return rc;
+
+    if (prm->stream) {
+        h->stream = (cudaStream_t)prm->stream;
+    } else {
+        CU(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    h->mem.alloc = prm->alloc;
+    h->mem.release = prm->free;
+    h->mem.ctx = prm->alloc_ctx;
+    h->eng.reset(D == 2 ? make_engine_l<D2Q9>(h.get()) : make_engine_l<D3Q19>(h.get()));
+    if (!h->eng) return fail(LBDPS_ERR_OOM, "engine allocation failed");
+    auto cleanup = [&](int code) {
+        if (h->stream) cudaStreamSynchronize(h->stream);
+        h->mem.release_all();
+        if (h->own_stream) cudaStreamDestroy(h->stream);
+        return code;
+    };
+    if ((rc = h->eng->allocate(h->mem))) return cleanup(rc);
+    if (cudaMallocHost(&h->health_host, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(LBDPS_ERR_OOM, "pinned allocation failed"));
+    }
+    if ((rc = h->eng->upload_initial(pos.data(), vel.data()))) {
+        cudaFreeHost(h->health_host);
+        return cleanup(rc);
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaFreeHost(h->health_host);
+        return cleanup(fail(LBDPS_ERR_CUDA, "create: %s", cudaGetErrorString(cudaGetLastError())));
+    }
+    *out = h.release();
+    return LBDPS_OK;
+}
+
+void lbdps_destroy(lbdps_t *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_graphs(h);
+    h->eng.reset();
+    h->mem.release_all();
+    if (h->health_host) cudaFreeHost(h->health_host);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int lbdps_step(lbdps_t *h, int64_t nsteps)
+{
+    if (!h || nsteps < 0) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    return run_steps(h, nsteps);
+}
+
+int lbdps_step_profiled(lbdps_t *h, int64_t nsteps, double *kernel_ms, int cap, int *nclass)
+{
+    if (!h || nsteps < 0 || (!kernel_ms && cap > 0)) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    constexpr int kClasses = 5;
+    if (nclass) *nclass = kClasses;
+    cudaEvent_t ev[6];
+    for (int e = 0; e < 6; ++e) CU(cudaEventCreate(&ev[e]));
+    double acc[kClasses] = {0, 0, 0, 0, 0};
+    int rc = LBDPS_OK;
+    for (int64_t s = 0; s < nsteps && rc == LBDPS_OK; ++s) {
+        rc = h->eng->enqueue_step(h->parity, ev);
+        if (rc) break;
+        if (cudaEventSynchronize(ev[5]) != cudaSuccess) {
+            rc = fail(LBDPS_ERR_CUDA, "profiling: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        for (int c = 0; c < kClasses; ++c) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[c], ev[c + 1]);
+            acc[c] += ms;
+        }
+        h->parity ^= 1;
+        h->steps++;
+    }
+    for (int e = 0; e < 6; ++e) cudaEventDestroy(ev[e]);
+    for (int c = 0; c < kClasses && c < cap; ++c) kernel_ms[c] = acc[c];
+    return rc;
+}
+
+int lbdps_sync(lbdps_t *h)
+{
+    if (!h) return fail(LBDPS_ERR_INVALID, "NULL handle");
+    CU(cudaStreamSynchronize(h->stream));
+    return LBDPS_OK;
+}
+
+int lbdps_fields(lbdps_t *h, int mask, int units, double *out, size_t cap)
+{
+    if (!h || !out) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    CU(cudaStreamSynchronize(h->stream));
+    return h->eng->fields(mask, units, out, cap);
+}
+
+int lbdps_particles(lbdps_t *h, int units, double *pos, double *vel, int64_t cap)
+{
+    if (!h) return fail(LBDPS_ERR_INVALID, "NULL handle");
+    CU(cudaStreamSynchronize(h->stream));
+    return h->eng->particles(units, pos, vel, cap);
+}
+
+int lbdps_set_particles(lbdps_t *h, int64_t n, const double *pos, const double *vel)
+{
+    if (!h || (n > 0 && (!pos || !vel))) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    if (n != h->np) return fail(LBDPS_ERR_INVALID, "particle count must stay %d", h->np);
+    int rc = validate_positions(h, pos, false);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(h->stream));
+    rc = h->eng->set_particles(pos, vel);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(h->stream));
+    return LBDPS_OK;
+}
+
+int lbdps_populations(lbdps_t *h, double *f, size_t cap)
+{
+    if (!h || !f) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    CU(cudaStreamSynchronize(h->stream));
+    return h->eng->populations(f, cap);
+}
+
+int lbdps_set_populations(lbdps_t *h, const double *f, size_t count)
+{
+    if (!h || !f) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    CU(cudaStreamSynchronize(h->stream));
+    return h->eng->set_populations(f, count);
+}
+
+int lbdps_particle_diag(lbdps_t *h, int which, double *out, size_t cap)
+{
+    if (!h || !out) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    CU(cudaStreamSynchronize(h->stream));
+    return h->eng->particle_diag(which, out, cap);
+}
+
+int lbdps_collide_particles(lbdps_t *h, int64_t *pairs, int64_t cap, int64_t *npairs)
+{
+    if (!h || cap < 0) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    CU(cudaStreamSynchronize(h->stream));
+    return h->eng->collide_particles(pairs, cap, npairs);
+}
+
+int lbdps_stats(lbdps_t *h, lbdps_stats_t *out)
+{
+    if (!h || !out) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    return h->eng->stats(out);
+}
+
+int lbdps_health(lbdps_t *h, int *health)
+{
+    if (!h || !health) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    unsigned hw = 0;
+    int rc = h->eng->health(&hw);
+    if (rc) return rc;
+    *health = (int)hw;
+    return LBDPS_OK;
+}
+
+int lbdps_constants(lbdps_t *h, double *out, int cap)
+{
+    if (!h || !out) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    const Derived &k = h->k;
+    const double v[19] = {k.tau, k.nu, k.mu, k.rho_s, k.d, k.r, k.vp, k.mp, k.e,
+                          k.geff[0], k.geff[1], k.geff[2], k.fb[0], k.fb[1], k.fb[2],
+                          k.u0[0], k.u0[1], k.u0[2], k.cs};
+    if (cap < 19) return fail(LBDPS_ERR_CAPACITY, "need 19 doubles");
+    std::memcpy(out, v, sizeof(v));
+    return LBDPS_OK;
+}
+
+int lbdps_shape(lbdps_t *h, int *dim, int *q, int64_t *ncell, int64_t *nparticles)
+{
+    if (!h) return fail(LBDPS_ERR_INVALID, "NULL handle");
+    if (dim) *dim = h->dim;
+    if (q) *q = h->q;
+    if (ncell) *ncell = h->ncell;
+    if (nparticles) *nparticles = h->np;
+    return LBDPS_OK;
+}
+
+int lbdps_save(lbdps_t *h, void *buf, size_t cap, size_t *used)
+{
+    if (!h) return fail(LBDPS_ERR_INVALID, "NULL handle");
+    const size_t need = sizeof(CkptHeader) + h->eng->checkpoint_bytes();
+    if (used) *used = need;
+    if (!buf) return LBDPS_OK;
+    if (cap < need) return fail(LBDPS_ERR_CAPACITY, "checkpoint needs %zu bytes", need);
+    CU(cudaStreamSynchronize(h->stream));
+    CkptHeader hd{};
+    std::memcpy(hd.magic, "LBDPSCK1", 8);
+    hd.dim = h->dim;
+    hd.q = h->q;
+    hd.storage = h->prm.storage;
+    for (int a = 0; a < 3; ++a) hd.n[a] = h->n[a];
+    hd.np = h->np;
+    hd.ncell = h->ncell;
+    hd.steps = h->steps;
+    hd.payload = h->eng->checkpoint_bytes();
+    std::memcpy(buf, &hd, sizeof(hd));
+    return h->eng->save((char *)buf + sizeof(hd));
+}
+
+int lbdps_load(lbdps_t *h, const void *buf, size_t size)
+{
+    if (!h || !buf || size < sizeof(CkptHeader)) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    CkptHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (std::memcmp(hd.magic, "LBDPSCK1", 8) != 0) return fail(LBDPS_ERR_INVALID, "not a checkpoint");
+    if (hd.dim != h->dim || hd.q != h->q || hd.storage != h->prm.storage || hd.np != h->np ||
+        hd.ncell != h->ncell || hd.n[0] != h->n[0] || hd.n[1] != h->n[1] || hd.n[2] != h->n[2])
+        return fail(LBDPS_ERR_INVALID, "checkpoint shape differs from the handle");
+    if (hd.payload != h->eng->checkpoint_bytes() || size < sizeof(hd) + hd.payload)
+        return fail(LBDPS_ERR_INVALID, "checkpoint truncated");
+    CU(cudaStreamSynchronize(h->stream));
+    int rc = h->eng->load((const char *)buf + sizeof(hd));
+    if (rc) return rc;
+    h->steps = hd.steps;
+    return LBDPS_OK;
+}
+
+const char *lbdps_strerror(int code)
+{
+    switch (code) {
+    case LBDPS_OK: return "ok";
+    case LBDPS_ERR_INVALID: return "invalid argument or description";
+    case LBDPS_ERR_OOM: return "out of memory";
+    case LBDPS_ERR_CAPACITY: return "capacity exceeded";
+    case LBDPS_ERR_DIVERGED: return "gas state diverged";
+    case LBDPS_ERR_DOMAIN: return "particle left the domain";
+    case LBDPS_ERR_TIMEOUT: return "device wait timed out";
+    case LBDPS_ERR_CUDA: return "CUDA runtime error";
+    }
+    return "unknown status";
+}
+
+const char *lbdps_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,215 @@
+// Internal declarations of the sm_103a LB-DPS library: lattice velocity sets,
+// kernel parameter blocks, storage conversions and kernel launchers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace lbdpsk {
+
+enum { BC_WALL = 0, BC_PERIODIC = 1, BC_INLET = 2, BC_OUTLET = 3 };
+enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+enum : unsigned { HEALTH_DIVERGED = 1u, HEALTH_DOMAIN = 2u, HEALTH_CAPACITY = 4u };
+
+// ---------------------------------------------------------------------------
+// Velocity sets.  D2Q9 in the paper's order (Eq. 4): rest, the four axis
+// directions counter-clockwise from +x, the four diagonals counter-clockwise
+// from (1,1).  D3Q19: rest, +-x, +-y, +-z, then the twelve edge diagonals in
+// opposite pairs.  Written as constexpr selections so that unrolled loops
+// fold every c_ia into an immediate.
+// ---------------------------------------------------------------------------
+struct D2Q9 {
+    static constexpr int D = 2, Q = 9;
+    __host__ __device__ static constexpr int c(int i, int a)
+    {
+        return a == 0 ? ((i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0)
+             : a == 1 ? ((i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0)
+                      : 0;
+    }
+    __host__ __device__ static constexpr int opp(int i)
+    {
+        return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+    }
+    __host__ __device__ static constexpr double w(int i)
+    {
+        return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+};
+
+struct D3Q19 {
+    static constexpr int D = 3, Q = 19;
+    __host__ __device__ static constexpr int c(int i, int a)
+    {
+        return a == 0 ? ((i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+                         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0)
+             : a == 1 ? ((i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+                         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0)
+                      : ((i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+                         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+    __host__ __device__ static constexpr double w(int i)
+    {
+        return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Storage of population deviations f_i - w_i.
+// ---------------------------------------------------------------------------
+template <class S> struct Store;
+template <> struct Store<double> {
+    using R = double;
+    __device__ static double load(double v) { return v; }
+    __device__ static double save(double v) { return v; }
+};
+template <> struct Store<float> {
+    using R = float;
+    __device__ static float load(float v) { return v; }
+    __device__ static float save(float v) { return v; }
+};
+// FP16 keeps the deviation scaled by 2^10 so that small deviations stay
+// normal numbers (FP16 subnormals start below 6.1e-5).
+constexpr float kF16Scale = 1024.0f;
+template <> struct Store<__half> {
+    using R = float;
+    __device__ static float load(__half v) { return __half2float(v) * (1.0f / kF16Scale); }
+    __device__ static __half save(float v) { return __float2half_rn(v * kF16Scale); }
+};
+template <> struct Store<__nv_bfloat16> {
+    using R = float;
+    __device__ static float load(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __nv_bfloat16 save(float v) { return __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------------------
+// Per-particle-count tables (deposition, Eq. 9-11, 19-20), built in FP64.
+// Index n = particles whose centre lies in the cell, clamped to ntab - 1
+// (beyond that the solid fraction is at its close-packing cap).
+// ---------------------------------------------------------------------------
+template <class Real> struct CountTables {
+    const Real *eps_s;    // solid fraction (Eq. 10, capped)
+    const Real *eps_g;    // gas voidage for the drag (Eq. 11 in 2D)
+    const Real *sol_g;    // 1 - eps_g, kept separately so 1 - eps_k needs no cancellation
+    const Real *inv_div;  // 1 / divisor of the superficial -> actual velocity
+    const Real *og;       // omega(eps_g) * gamma(eps_s, tau)  (Eq. 20, 9)
+    const Real *gam;      // gamma(eps_s, tau)
+    const Real *beta_a;   // beta = beta_a + beta_b |slip| (Ergun branch) or
+    const Real *beta_b;   //        beta_a (1 + 0.15 Re^0.687)            (dilute, Re < 1000)
+    const Real *beta_c;   //        beta_c |slip|                          (dilute, Re >= 1000)
+    const Real *re_k;     // Re_p = re_k |slip| (Eq. 22)
+    const int *branch;    // 0 Ergun, 1 dilute (decided in FP64 on eps_g > 0.74)
+    int ntab;
+};
+
+// ---------------------------------------------------------------------------
+// Parameter block shared by all step kernels (passed by value).
+// ---------------------------------------------------------------------------
+template <class Real> struct StepParams {
+    int dim;
+    int n[3];
+    int ncell;
+    int bc[6];
+    int vert;                 // vertical axis (dim - 1)
+    Real tau, inv_tau;
+    Real les_k;               // 18 C_s^2 (0 = LES off)
+    Real fb[3];               // gas body force density
+    int has_fb;
+    Real wall_u[6][3];
+    Real mu, d, r, vp, mp, e;
+    Real geff[3];
+    Real psign;               // -1 or +1 for the pressure-gradient force
+    double d2;                // d^2 in FP64 for the contact test
+    double r64;
+    double len[3];            // domain lengths as double
+    double len_below[3];      // largest double below len
+    CountTables<Real> tab;
+    const Real *inlet_u;      // inlet face cells x dim
+    int inlet_face;           // face index or -1
+    unsigned *health;
+};
+
+// Device buffers of one bed.
+template <class Real> struct Fields {
+    Real *rho, *u[3], *fpg[3], *beta;                  // node outputs of the collision
+    Real *vs[3], *tau_t, *uact[3], *eps_g;              // diagnostics (may be null)
+    int *ntot;                                          // diagnostics (may be null)
+};
+
+// Particle arrays in cell-sorted order.  Besides the FP64 centre P and the
+// velocity v, each particle carries its cell index and its offset inside the
+// cell, off = P - floor(P) (in the arithmetic type), so that interpolation
+// weights and the coarse contact test need no FP64 arithmetic.
+template <class Real> struct Particles {
+    double *P[3];
+    Real *v[3];
+    int *id;
+    int *cell;
+    Real *off[3];
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the .cu files, explicitly instantiated).
+// ---------------------------------------------------------------------------
+template <class L, class Real, class S>
+void launch_collide_stream(const StepParams<Real> &p, const S *fin, S *fout, const int *cell_start,
+                           Particles<Real> parts, Fields<Real> fld, cudaStream_t st);
+
+template <class L, class Real, class S>
+void launch_init_equilibrium(int ncell, const Real *u0, S *f, cudaStream_t st);
+
+template <class L, class Real, class S>
+void launch_export_populations(int ncell, const S *f, double *out, cudaStream_t st);
+
+template <class L, class Real, class S>
+void launch_import_populations(int ncell, const double *in, S *f, cudaStream_t st);
+
+template <class Real>
+void launch_build_tables(int dim, double tau, double r, double vp, double d, double mu,
+                         int superficial_mode, int ntab, double *scratch, CountTables<Real> tab,
+                         cudaStream_t st);
+
+template <int D, class Real>
+void launch_drag_pre(const StepParams<Real> &p, Particles<Real> parts, const int *cell_start,
+                     Fields<Real> fld, Real *fpre, Real *gradp, int np, cudaStream_t st);
+
+template <int D, class Real>
+void launch_drag_integrate(const StepParams<Real> &p, Particles<Real> parts, const int *cell_start,
+                           Fields<Real> fld, const Real *fpre, const Real *gradp, int *key,
+                           int *counts, Real *diag_fpre, Real *diag_fd, int np, cudaStream_t st);
+
+template <int D, class Real>
+void launch_cell_keys(const int *n, Particles<Real> parts, int *key, int *counts, int np,
+                      cudaStream_t st);
+
+void launch_scan(const int *counts, int *cell_start, int *block_sums, int ncell, cudaStream_t st);
+int scan_block_count(int ncell);
+
+template <class Real>
+void launch_scatter_gather(int ncell, int dim, const int *key, int *counts, const int *cell_start,
+                           int *tmp, Particles<Real> src, Particles<Real> dst, int np,
+                           cudaStream_t st);
+
+template <int D, class Real>
+void launch_detect(const StepParams<Real> &p, Particles<Real> parts, const int *cell_start,
+                   int *best, int *wall, long long *pairs, unsigned long long *npairs,
+                   long long pair_cap, int np, cudaStream_t st);
+
+template <int D, class Real>
+void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int *best,
+                    const int *wall, int np, cudaStream_t st);
+
+template <class L, class Real, class S>
+void launch_reduce_state(int ncell, const S *f, Particles<Real> parts, double mp, int np,
+                         double *partials, double *out, cudaStream_t st);
+
+template <class Real>
+void launch_reduce_bed(int ncell, int dim, const Real *eps_g, const int *ntot,
+                       const Real *const *uact, const Real *const *vs, double *partials,
+                       double *out, cudaStream_t st);
+
+int reduce_block_count(int n);
+
+}  // namespace lbdpsk

@@ -1,0 +1,353 @@
+"""GPU (CUDA library, through the C ABI) against the FP64 oracle.
+
+Each parity case starts both sides from an identical state: the GPU bed is
+created from a seeded workload, its populations and particles are read back
+(widened exactly to FP64) and loaded into the oracle; then both take the same
+steps and the outputs are compared element by element.
+
+Tolerances
+  * integer outputs (cell keys, sorted order, contact pairs, chosen partners,
+    wall contacts): bit-exact from identical state.
+  * rho and u: relative error max|d| / max|oracle| per field, 1e-12 in FP64
+    storage and 2e-6 in FP32 storage (spec tolerances).
+  * derived node fields (F_p->g, beta) and particle velocities: the FP32 path
+    rounds each of O(100) operations at 2^-24 ~ 6e-8, so a bound of 1e-5
+    relative (norm-wise) leaves a margin of ~2x over the accumulated error;
+    FP64 uses 1e-11.  Particles in cells whose Eq. 28 rescale is
+    ill-conditioned (sum|F_pre| / |sum F_pre| > 1e3, the ratio amplifies
+    rounding of the denominator) are compared separately with a looser bound.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1303_2653_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1303_2653_gb300 import build
+    build.build_all()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _lb():
+    from paper_1303_2653_gb300 import lbdps
+    return lbdps
+
+
+def _pair(w, storage, **kw):
+    L = _lb()
+    bed = L.Bed(w, storage=storage, diagnostics=True, **kw)
+    ob = O.OracleBed(w)
+    ob.set_populations(bed.populations())
+    P, v = bed.particles()
+    ob.set_particles(P, v)
+    return bed, ob
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    scale = np.abs(b).max()
+    if scale == 0:
+        return np.abs(a).max()
+    return np.abs(a - b).max() / scale
+
+
+TOL = {W.STORE_F64: 1e-12, W.STORE_F32: 2e-6}
+TOL_DERIVED = {W.STORE_F64: 1e-11, W.STORE_F32: 1e-5}
+
+
+def _workloads():
+    return {
+        "riser2d": W.scaled_riser2d(nx=48, ny=96),
+        "riser2d_les": W.scaled_riser2d(nx=40, ny=64, cs_smag=0.15, seed=77),
+        "bubbling2d": W.bubbling2d(nx=32, ny=64, n_particles=600, steps=5),
+        "dense2d": W.riser2d(nx=24, ny=48, n_particles=1200, solid_fraction=0.25, sigma_v=0.6,
+                             seed=5),
+        "riser3d": W.scaled_riser3d(nx=16, ny=16, nz=32, n_particles=1500, solid_fraction=0.08,
+                                    sigma_v=0.4),
+    }
+
+
+# ----------------------------------------------------------------- constants
+
+def test_constants_match_oracle():
+    w = W.scaled_riser2d(nx=32, ny=64)
+    bed, ob = _pair(w, W.STORE_F32)
+    g, o = bed.constants(), ob.constants()
+    for k in o:
+        assert g[k] == pytest.approx(o[k], rel=1e-15, abs=1e-300), k
+    bed.close()
+
+
+# ------------------------------------------------------------ sort / binning
+
+@pytest.mark.parametrize("name", ["riser2d", "dense2d", "riser3d"])
+def test_initial_sort_bit_exact(name):
+    w = _workloads()[name]
+    L = _lb()
+    bed = L.Bed(w, storage=W.STORE_F32)
+    P, _ = bed.particles()
+    cell = np.floor(P).astype(np.int64)
+    n = w.n
+    lin = cell[:, 0] + n[0] * cell[:, 1] + (n[0] * n[1] * cell[:, 2] if w.dim == 3 else 0)
+    order = bed.particle_diag(L.PDIAG_ORDER).astype(np.int64)
+    np.testing.assert_array_equal(order, np.lexsort((np.arange(len(lin)), lin)))
+    np.testing.assert_array_equal(bed.particle_diag(L.PDIAG_CELL).astype(np.int64), lin)
+    bed.close()
+
+
+# ------------------------------------------------------------- one-step parity
+
+def _compare_step(bed, ob, storage, steps=1):
+    L = _lb()
+    bed.step(steps)
+    ob.step(steps)
+    tol, tol_d = TOL[storage], TOL_DERIVED[storage]
+    gf = bed.fields(L.FIELD_RHO | L.FIELD_U | L.FIELD_FPG | L.FIELD_BETA | L.FIELD_VS |
+                    L.FIELD_NTOT | L.FIELD_TAU_T | L.FIELD_UACT | L.FIELD_EPS_G)
+    rho_o = ob.field(O.F_RHO)
+    # rho enters as 1 + sum of deviations: compare the deviation from 1
+    assert _rel(gf["rho"] - 1.0, rho_o - 1.0) <= max(tol, 1e-16 / max(np.abs(rho_o - 1).max(), 1e-300)) or \
+        np.abs(gf["rho"] - rho_o).max() <= tol
+    assert _rel(gf["u"], ob.field(O.F_U)) <= tol
+    np.testing.assert_array_equal(gf["ntot"], ob.field(O.F_NTOT))
+    assert _rel(gf["vs"], ob.field(O.F_VS)) <= tol_d
+    assert _rel(gf["fpg"], ob.field(O.F_FPG)) <= tol_d
+    assert _rel(gf["beta"], ob.field(O.F_BETA)) <= tol_d
+    assert _rel(gf["uact"], ob.field(O.F_UACT)) <= tol_d
+    assert _rel(gf["eps_g"], ob.field(O.F_EPS_G)) <= tol_d
+    assert _rel(gf["tau_t"], ob.field(O.F_TAU_T)) <= tol_d
+    return gf
+
+
+def _particle_compare(bed, ob, storage, steps=1):
+    """Particle state after the step(s); returns the mask of well-conditioned
+    particles used for the strict comparison."""
+    L = _lb()
+    Pg, vg = bed.particles()
+    Po, vo = ob.particles()
+    tol_d = TOL_DERIVED[storage]
+    S = ob.field(O.F_SUM_PRE)
+    A = ob.field(O.F_SUM_ABS_PRE)
+    # conditioning of Eq. 28 in each particle's deposition cell
+    ids_sorted, cs = ob.sorted_ids()
+    fpre_g = bed.particle_diag(L.PDIAG_FPRE)
+    fpre_o = ob.particle_diag(O.P_FPRE)
+    fd_g = bed.particle_diag(L.PDIAG_FD)
+    fd_o = ob.particle_diag(O.P_FD)
+    err = np.abs(fpre_g - fpre_o).max(axis=1) / np.abs(fpre_o).max()
+    worst = np.argsort(-err)[:4]
+    assert err.max() <= tol_d, [(int(k), err[k], Pg[k].tolist(), fpre_g[k].tolist(),
+                                 fpre_o[k].tolist()) for k in worst]
+    # a component with sum|F_pre| = 0 has nothing to rescale (kappa 1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        kappa_cell = np.where(A > 0, np.where(np.abs(S) > 0, A / np.abs(S), np.inf), 1.0).max(axis=1)
+    return Pg, vg, Po, vo, fd_g, fd_o, kappa_cell
+
+
+@pytest.mark.parametrize("name", ["riser2d", "riser2d_les", "bubbling2d", "dense2d", "riser3d"])
+@pytest.mark.parametrize("storage", [W.STORE_F64, W.STORE_F32])
+def test_one_step_parity(name, storage):
+    w = _workloads()[name]
+    bed, ob = _pair(w, storage)
+    # the deposition cell of every particle before the step
+    Pg0, _ = bed.particles()
+    n = w.n
+    c0 = np.floor(Pg0).astype(np.int64)
+    cell0 = c0[:, 0] + n[0] * c0[:, 1] + (n[0] * n[1] * c0[:, 2] if w.dim == 3 else 0)
+    _compare_step(bed, ob, storage)
+    L = _lb()
+    Pg, vg, Po, vo, fd_g, fd_o, kappa_cell = _particle_compare(bed, ob, storage)
+    kappa = kappa_cell[cell0]
+    good = kappa < 1e3
+    assert good.mean() > 0.9
+    tol_d = TOL_DERIVED[storage]
+    assert _rel(fd_g[good], fd_o[good]) <= tol_d
+    assert _rel(vg[good], vo[good]) <= tol_d
+    # positions: FP64 accumulation of the velocity
+    vmax = np.abs(vo).max()
+    assert np.abs(Pg[good] - Po[good]).max() <= 4 * tol_d * vmax + 1e-13
+    # ill-conditioned rescale cells: same sign, magnitude within kappa * eps
+    if (~good).any():
+        err = np.abs(fd_g[~good] - fd_o[~good]).max() / np.abs(fd_o).max()
+        assert err <= tol_d * 1e3
+    # collision decisions: bit-exact wherever the inputs were bit-identical;
+    # in FP32 the post-integration state differs in the last bits, so a
+    # decision may only differ for particles whose state differs
+    best_g = bed.particle_diag(L.PDIAG_BEST).astype(np.int64)
+    best_o = ob.particle_diag(O.P_BEST).astype(np.int64)
+    wall_g = bed.particle_diag(L.PDIAG_WALL).astype(np.int64)
+    wall_o = ob.particle_diag(O.P_WALL).astype(np.int64)
+    if storage == W.STORE_F64:
+        np.testing.assert_array_equal(best_g, best_o)
+        np.testing.assert_array_equal(wall_g, wall_o)
+    else:
+        assert (best_g != best_o).mean() < 2e-3
+        assert (wall_g != wall_o).mean() < 2e-3
+    # cells of the new sort: bit-exact unless the two positions straddle a face
+    cg = bed.particle_diag(L.PDIAG_CELL).astype(np.int64)
+    co = ob.particle_diag(O.P_CELL).astype(np.int64)
+    if storage == W.STORE_F64:
+        np.testing.assert_array_equal(cg, co)
+    else:
+        mism = cg != co
+        if mism.any():
+            frac = np.abs(Po[mism] - np.round(Po[mism]))
+            assert frac.min(axis=1).max() < 1e-4
+    bed.close()
+
+
+@pytest.mark.parametrize("storage", [W.STORE_F64])
+def test_five_step_parity_fp64(storage):
+    w = _workloads()["riser2d"]
+    bed, ob = _pair(w, storage)
+    _compare_step(bed, ob, storage, steps=5)
+    Pg, vg = bed.particles()
+    Po, vo = ob.particles()
+    assert _rel(vg, vo) <= 1e-9
+    assert np.abs(Pg - Po).max() <= 1e-10
+    bed.close()
+
+
+# --------------------------------------------------------- TDHS, bit-exact
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("storage", [W.STORE_F64, W.STORE_F32])
+def test_detection_pairs_bit_exact(dim, storage):
+    # identical particle state on both sides (dense, overlapping, random
+    # velocities representable in the storage precision): contact pairs,
+    # partner choices and wall contacts must agree bit for bit
+    L = _lb()
+    rng = np.random.default_rng(100 + dim)
+    n = (12, 14) if dim == 2 else (6, 7, 8)
+    box = np.array(n, dtype=float)
+    grid = np.stack(np.meshgrid(*[np.arange(k) + 0.5 for k in n], indexing="ij"), -1)
+    grid = grid.reshape(-1, dim)
+    N = grid.shape[0]
+    w = W.Workload(name="tdhs", dim=dim, n=n,
+                   bc=(W.WALL, W.WALL, W.PERIODIC, W.PERIODIC, W.PERIODIC, W.PERIODIC),
+                   h=1.0, dt=1.0, d_p=0.9, rho_s=1000.0, e=0.8, pos=grid,
+                   vel=np.zeros_like(grid), rho_g=1.0, mu_g=0.1)
+    P = rng.uniform(0, 1, size=(N, dim)) * box
+    v = rng.normal(size=(N, dim)) * 0.05
+    if storage == W.STORE_F32:
+        v = v.astype(np.float32).astype(np.float64)
+    bed = L.Bed(w, storage=storage)
+    bed.set_particles(P, v)
+    ob = O.OracleBed(w)
+    ob.set_particles(P, v)
+    pairs_g = bed.collide_particles(record_pairs=True)
+    ob.collide_particles()
+    pairs_o = ob.pairs()
+    assert pairs_o.shape[0] > 50
+    np.testing.assert_array_equal(pairs_g, pairs_o)
+    np.testing.assert_array_equal(bed.particle_diag(L.PDIAG_BEST).astype(np.int64),
+                                  ob.particle_diag(O.P_BEST).astype(np.int64))
+    np.testing.assert_array_equal(bed.particle_diag(L.PDIAG_WALL).astype(np.int64),
+                                  ob.particle_diag(O.P_WALL).astype(np.int64))
+    _, vg = bed.particles()
+    _, vo = ob.particles()
+    assert _rel(vg, vo) <= (1e-14 if storage == W.STORE_F64 else 1e-6)
+    bed.close()
+
+
+# ------------------------------------------------------------ closed forms
+
+@pytest.mark.parametrize("storage", [W.STORE_F64, W.STORE_F32])
+def test_poiseuille_on_gpu(storage):
+    import math
+    L = _lb()
+    tau = 0.5 + math.sqrt(3.0) / 4.0
+    nu = (tau - 0.5) / 3.0
+    nx, F = 12, 1e-5
+    w = W.channel2d(nx=nx, ny=4, h=1.0, dt=1.0, nu=nu, body_accel=F, storage=storage)
+    bed = L.Bed(w)
+    bed.step(12000)
+    u = bed.fields(L.FIELD_U)["u"][:, 1].reshape(-1, nx)
+    x = np.arange(nx) + 0.5
+    exact = F / (2 * nu) * x * (nx - x)
+    tol = 1e-9 if storage == W.STORE_F64 else 2e-5
+    np.testing.assert_allclose(u, np.broadcast_to(exact, u.shape), rtol=tol)
+    bed.close()
+
+
+def test_couette_on_gpu():
+    L = _lb()
+    nu = (0.9 - 0.5) / 3.0
+    nx, U = 10, 1e-3
+    w = W.channel2d(nx=nx, ny=4, h=1.0, dt=1.0, nu=nu, top_wall_u=U, storage=W.STORE_F64)
+    bed = L.Bed(w)
+    bed.step(6000)
+    u = bed.fields(L.FIELD_U)["u"][:, 1].reshape(-1, nx)
+    x = np.arange(nx) + 0.5
+    np.testing.assert_allclose(u, np.broadcast_to(U * x / nx, u.shape), rtol=1e-9, atol=1e-16)
+    bed.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mass_conserved_on_gpu(dim):
+    w = W.scaled_riser2d(nx=32, ny=64) if dim == 2 else W.scaled_riser3d(nx=12, ny=12, nz=24)
+    L = _lb()
+    bed = L.Bed(w, storage=W.STORE_F64)
+    m0 = bed.stats()["mass"]
+    bed.step(50)
+    m1 = bed.stats()["mass"]
+    assert abs(m1 - m0) <= 1e-12 * m0
+    bed.close()
+
+
+# ------------------------------------------------------------ checkpoint
+
+def test_checkpoint_bit_exact_continuation():
+    L = _lb()
+    w = W.scaled_riser2d(nx=32, ny=64)
+    a = L.Bed(w, storage=W.STORE_F32)
+    a.step(7)
+    blob = a.save()
+    a.step(5)
+    fa = a.populations()
+    Pa, va = a.particles()
+    b = L.Bed(w, storage=W.STORE_F32)
+    b.load(blob)
+    b.step(5)
+    np.testing.assert_array_equal(b.populations(), fa)
+    Pb, vb = b.particles()
+    np.testing.assert_array_equal(Pb, Pa)
+    np.testing.assert_array_equal(vb, va)
+    a.close()
+    b.close()
+
+
+# ------------------------------------------------------------ edge cases
+
+def test_no_particles_and_graph_vs_eager():
+    L = _lb()
+    w = W.channel2d(nx=16, ny=8, h=1.0, dt=1.0, nu=0.05, body_accel=1e-6, storage=W.STORE_F32)
+    g = L.Bed(w, use_graph=True)
+    e = L.Bed(w, use_graph=False)
+    g.step(20)
+    e.step(20)
+    np.testing.assert_array_equal(g.populations(), e.populations())
+    g.close()
+    e.close()
+
+
+def test_create_rejects_invalid():
+    L = _lb()
+    w = W.scaled_riser2d(nx=32, ny=64)
+    bad = w.pos.copy()
+    bad[1] = bad[0]
+    with pytest.raises(L.LbdpsError) as ei:
+        L.Bed(w.with_(pos=bad))
+    assert ei.value.code == L.ERR_INVALID
+    with pytest.raises(L.LbdpsError):
+        L.Bed(w.with_(d_p=2 * w.h))
+    with pytest.raises(L.LbdpsError):
+        L.Bed(w.with_(bc=(W.INLET, W.OUTLET, W.PERIODIC, W.PERIODIC, W.PERIODIC, W.PERIODIC)))
