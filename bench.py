@@ -45,19 +45,27 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="only build the bed and run this many steps (for ncu captures); "
+                         "no timing, no JSON line")
+    ap.add_argument("--workload", default="riser2d", choices=["riser2d", "riser3d"])
     return ap.parse_args()
 
 
-def workload(storage):
+def workload(storage, name="riser2d"):
     from paper_1303_2653_gb300 import workloads as W
     st = {"f32": W.STORE_F32, "f16": W.STORE_F16, "bf16": W.STORE_BF16, "f64": W.STORE_F64}[storage]
+    if name == "riser3d":
+        return W.riser3d(storage=st)
     return W.riser2d(storage=st)
 
 
 def config_dict(w, n_gpus, storage):
-    return {"workload": f"riser2d D2Q9 {w.n[0]}x{w.n[1]}, {w.n_particles} particles, "
+    shape = "x".join(str(v) for v in w.n)
+    lattice = "D2Q9" if w.dim == 2 else "D3Q19"
+    return {"workload": f"{w.name.split('-')[0]} {lattice} {shape}, {w.n_particles} particles, "
                         f"{storage} population storage",
-            "cells": w.ncell, "particles": w.n_particles, "lattice": "D2Q9",
+            "cells": w.ncell, "particles": w.n_particles, "lattice": lattice,
             "storage": storage, "l2": "flushed between timed steps (512 MB write)",
             "parallelism": f"replicas x{n_gpus}"}
 
@@ -220,12 +228,19 @@ def main():
     from paper_1303_2653_gb300 import lbdps as L
 
     torch.cuda.set_device(local)
+    if args.profile_steps:
+        bed = L.Bed(workload(args.storage, args.workload))
+        bed.step(args.profile_steps)
+        bed.sync()
+        bed.close()
+        print(f"profile run ok: {args.profile_steps} steps", flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = workload(args.storage)
+    w = workload(args.storage, args.workload)
     bed = L.Bed(w)
     st = bed.stream
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")

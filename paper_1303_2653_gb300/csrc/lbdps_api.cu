@@ -856,6 +856,16 @@ void free_graphs(lbdps *h)
         }
 }
 
+}  // namespace
+
+// Lets other translation units of the library report a failure through
+// lbdps_last_error().
+namespace lbdpsk {
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace lbdpsk
+
+namespace {
+
 struct CkptHeader {
     char magic[8];
     int dim, q, storage, n[3], np, ncell;
