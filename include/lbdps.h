@@ -225,6 +225,34 @@ int lbdps_shape(lbdps_t *h, int *dim, int *q, int64_t *ncell, int64_t *nparticle
 int lbdps_save(lbdps_t *h, void *buf, size_t cap, size_t *used);
 int lbdps_load(lbdps_t *h, const void *buf, size_t size);
 
+/* Cell binning without device allocation.  The paper has no counterpart:
+ * this is a service for callers that must not allocate GPU memory while they
+ * run (work being recorded into a CUDA graph, real-time loops that cannot
+ * afford the implicit synchronisation of cudaMalloc/cudaFree, hosts that own
+ * a fixed device-memory budget).
+ *
+ * Computes the same (cell, id) ordering and cell list as the handle-based
+ * path, for np particles with ids 0..np-1:
+ *   dim          2 or 3;  n: cells per axis (n[2] ignored in 2D)
+ *   pos[a]       DEVICE array of np FP64 coordinates along axis a, lattice
+ *                units; positions outside [0, n[a]) are clamped to the
+ *                first/last cell
+ *   cell_start   DEVICE output, ncell + 1 ints: particles of cell c occupy
+ *                sorted slots cell_start[c] .. cell_start[c+1]-1
+ *   order        DEVICE output, np ints: the particle id in each sorted slot
+ *   stream       cudaStream_t (NULL = legacy default stream); asynchronous
+ * Temporaries live in one fixed device array of about 12 MB, created on each
+ * GPU that loads the library and kept until the process exits; this function
+ * calls no cudaMalloc, cudaFree or allocating library routine.  Limits:
+ * ncell <= 1048576 and np <= 1048576, otherwise LBDPS_ERR_CAPACITY with no
+ * work issued.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  Every call shares the one array, so calls
+ * whose work overlaps on the GPU (other streams, other host threads) race and
+ * give wrong results: serialise them. */
+int lbdps_bin_sort_noalloc(int dim, const int n[3], int64_t np, const double *const pos[3],
+                           int *cell_start, int *order, void *stream);
+
 /* Message text of a status code, and of the last failure on this thread. */
 const char *lbdps_strerror(int code);
 const char *lbdps_last_error(void);

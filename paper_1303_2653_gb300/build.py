@@ -35,7 +35,8 @@ def build_workloads(force: bool = False) -> str:
     return out
 
 
-CU_SOURCES = ["lbm_kernels.cu", "particle_kernels.cu", "stats_kernels.cu", "lbdps_api.cu"]
+CU_SOURCES = ["lbm_kernels.cu", "particle_kernels.cu", "stats_kernels.cu", "lbdps_api.cu",
+              "noalloc_sort.cu"]
 HEADERS = ["lbdps_internal.cuh"]
 
 

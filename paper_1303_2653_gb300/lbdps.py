@@ -105,6 +105,7 @@ def lib():
             "lbdps_shape": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), _i64p, _i64p], i),
             "lbdps_save": ([vp, vp, sz, ctypes.POINTER(sz)], i),
             "lbdps_load": ([vp, vp, sz], i),
+            "lbdps_bin_sort_noalloc": ([i, ctypes.POINTER(i), i64, ctypes.POINTER(vp), vp, vp, vp], i),
             "lbdps_strerror": ([i], ctypes.c_char_p),
             "lbdps_last_error": ([], ctypes.c_char_p),
         }
@@ -124,6 +125,22 @@ def _check(code: int, what: str):
 
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(_dp)
+
+
+def bin_sort_noalloc(dim: int, n, pos_ptrs, cell_start_ptr: int, order_ptr: int, np_: int,
+                     stream_ptr: int = 0):
+    """Cell binning on caller-owned device buffers without any device
+    allocation (see ``lbdps_bin_sort_noalloc`` in include/lbdps.h).
+
+    ``pos_ptrs`` are device addresses of the FP64 coordinates per axis
+    (lattice units), ``cell_start_ptr`` / ``order_ptr`` device addresses of
+    the int32 outputs (ncell + 1 and np entries), ``stream_ptr`` a
+    cudaStream_t address.  Asynchronous on that stream."""
+    nn = (ctypes.c_int * 3)(*(list(int(v) for v in n) + [1] * (3 - len(n))))
+    pp = (ctypes.c_void_p * 3)(*([int(p) for p in pos_ptrs] + [None] * (3 - len(pos_ptrs))))
+    _check(lib().lbdps_bin_sort_noalloc(int(dim), nn, int(np_), pp, ctypes.c_void_p(cell_start_ptr),
+                                        ctypes.c_void_p(order_ptr), ctypes.c_void_p(stream_ptr)),
+           "lbdps_bin_sort_noalloc")
 
 
 class Bed:

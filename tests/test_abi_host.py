@@ -81,3 +81,11 @@ def test_create_rejects_invalid_descriptions_on_host(lib, bad):
     assert not h.value
     assert lib.lib().lbdps_last_error()
 
+
+def test_noalloc_sort_rejects_oversize_on_host(lib):
+    nn = (ctypes.c_int * 3)(4096, 4096, 1)
+    pp = (ctypes.c_void_p * 3)(1, 1, None)
+    rc = lib.lib().lbdps_bin_sort_noalloc(2, nn, 10, pp, ctypes.c_void_p(1), ctypes.c_void_p(1),
+                                          None)
+    assert rc == lib.ERR_CAPACITY
+    assert b"exceed" in lib.lib().lbdps_last_error()
