@@ -164,8 +164,8 @@ int lbdps_step(lbdps_t *h, int64_t nsteps);
 
 /* Advance nsteps steps launching each kernel separately with CUDA events
  * around it; kernel_ms[k] receives the summed milliseconds of kernel class k
- * (order: collide_stream, drag_pre, drag_integrate, sort, collide_particles),
- * cap entries at most.  Returns the number of classes in *nclass. */
+ * (order: collide_stream, drag, sort, collide_particles), cap entries at
+ * most.  Returns the number of classes in *nclass. */
 int lbdps_step_profiled(lbdps_t *h, int64_t nsteps, double *kernel_ms, int cap, int *nclass);
 
 /* Wait for the handle's stream. */

@@ -165,12 +165,16 @@ template <class L, class Real, class S> struct EngineT : Engine {
     S *f[2] = {nullptr, nullptr};
     Fields<Real> fld{};
     Particles<Real> part[2]{};
-    int *cell_start[2] = {nullptr, nullptr};
-    int *key = nullptr, *counts = nullptr, *tmp = nullptr, *block_sums = nullptr;
+    Particles<Real> stage{};   // integrated state of the step, before placement
+    int *cl_local[2] = {nullptr, nullptr}, *cl_base[2] = {nullptr, nullptr};
+    int *tile_total = nullptr;
+    unsigned *ticket = nullptr;
+    int *key = nullptr, *counts = nullptr, *slot = nullptr, *idslot = nullptr;
     Real *fpre = nullptr, *gradp = nullptr, *diag_fpre = nullptr, *diag_fd = nullptr;
     int *best = nullptr, *wall = nullptr;
     Real *tabs[10] = {};
     int *tab_branch = nullptr;
+    typename Vec4<Real>::type *tab_pk[2] = {nullptr, nullptr};
     Real *inlet_dev = nullptr;
     unsigned *health_dev = nullptr;
     double *red_partials = nullptr, *red_out = nullptr;
@@ -185,7 +189,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
         auto get = [&](size_t bytes) { return A.get(bytes); };
         for (int b = 0; b < 2; ++b) {
             f[b] = (S *)get(sizeof(S) * Q * nc);
-            cell_start[b] = (int *)get(sizeof(int) * (nc + 1));
+            cl_local[b] = (int *)get(sizeof(int) * (nc + 1));
+            cl_base[b] = (int *)get(sizeof(int) * (cell_tiles(H->ncell) + 1));
             for (int a = 0; a < D; ++a) {
                 part[b].P[a] = (double *)get(sizeof(double) * np);
                 part[b].v[a] = (Real *)get(sizeof(Real) * np);
@@ -193,6 +198,13 @@ template <class L, class Real, class S> struct EngineT : Engine {
             }
             part[b].id = (int *)get(sizeof(int) * np);
             part[b].cell = (int *)get(sizeof(int) * np);
+        }
+        for (int a = 0; a < D; ++a) {
+            stage.P[a] = (double *)get(sizeof(double) * np);
+            stage.v[a] = (Real *)get(sizeof(Real) * np);
+            stage.off[a] = (Real *)get(sizeof(Real) * np);
+            if (!stage.P[a] || !stage.v[a] || !stage.off[a])
+                return fail(LBDPS_ERR_OOM, "device allocation failed");
         }
         fld.rho = (Real *)get(sizeof(Real) * nc);
         fld.beta = (Real *)get(sizeof(Real) * nc);
@@ -212,23 +224,28 @@ template <class L, class Real, class S> struct EngineT : Engine {
             diag_fd = (Real *)get(sizeof(Real) * D * np);
         }
         key = (int *)get(sizeof(int) * np);
-        counts = (int *)get(sizeof(int) * nc);
-        tmp = (int *)get(sizeof(int) * np);
-        block_sums = (int *)get(sizeof(int) * (scan_block_count(H->ncell) + 1));
+        counts = (int *)get(sizeof(int) * (nc + 1));
+        slot = (int *)get(sizeof(int) * np);
+        idslot = (int *)get(sizeof(int) * np);
+        tile_total = (int *)get(sizeof(int) * cell_tiles(H->ncell));
+        ticket = (unsigned *)get(sizeof(unsigned));
         fpre = (Real *)get(sizeof(Real) * D * np);
         gradp = (Real *)get(sizeof(Real) * D * np);
         best = (int *)get(sizeof(int) * np);
         wall = (int *)get(sizeof(int) * np);
         for (int t = 0; t < 10; ++t) tabs[t] = (Real *)get(sizeof(Real) * H->ntab);
         tab_branch = (int *)get(sizeof(int) * H->ntab);
+        for (int t = 0; t < 2; ++t)
+            tab_pk[t] = (typename Vec4<Real>::type *)get(sizeof(typename Vec4<Real>::type) * H->ntab);
         const int nface = (int)(H->inlet_lat.size() / D);
         inlet_dev = (Real *)get(sizeof(Real) * D * std::max(nface, 1));
         health_dev = (unsigned *)get(sizeof(unsigned));
         red_partials = (double *)get(sizeof(double) * 7 * 1024);
         red_out = (double *)get(sizeof(double) * 8);
         npairs_dev = (unsigned long long *)get(sizeof(unsigned long long));
-        void *must[] = {f[0], f[1], cell_start[0], cell_start[1], fld.rho, fld.beta, key, counts,
-                        tmp, block_sums, fpre, gradp, best, wall, tab_branch, inlet_dev, health_dev,
+        void *must[] = {f[0], f[1], cl_local[0], cl_local[1], cl_base[0], cl_base[1], fld.rho,
+                        fld.beta, key, counts, slot, idslot, tile_total, ticket, fpre, gradp,
+                        best, wall, tab_branch, inlet_dev, health_dev,
                         red_partials, red_out, npairs_dev, part[0].id, part[1].id,
                         part[0].cell, part[1].cell};
         for (void *p : must)
@@ -239,9 +256,20 @@ template <class L, class Real, class S> struct EngineT : Engine {
                 return fail(LBDPS_ERR_OOM, "device allocation failed");
         for (int t = 0; t < 10; ++t)
             if (!tabs[t]) return fail(LBDPS_ERR_OOM, "device allocation failed");
+        if (!tab_pk[0] || !tab_pk[1]) return fail(LBDPS_ERR_OOM, "device allocation failed");
         if (H->prm.diagnostics && (!fld.tau_t || !fld.eps_g || !fld.ntot || !diag_fpre || !diag_fd))
             return fail(LBDPS_ERR_OOM, "device allocation failed");
         fill_params();
+        return LBDPS_OK;
+    }
+
+    CellList cells(int b) const { return CellList{cl_local[b], cl_base[b]}; }
+    CellListOut cells_out(int b) { return CellListOut{cl_local[b], cl_base[b], tile_total, ticket}; }
+
+    int clear_cells(int b)
+    {
+        CU(cudaMemsetAsync(cl_local[b], 0, sizeof(int) * (H->ncell + 1), H->stream));
+        CU(cudaMemsetAsync(cl_base[b], 0, sizeof(int) * (cell_tiles(H->ncell) + 1), H->stream));
         return LBDPS_OK;
     }
 
@@ -289,6 +317,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
         t.beta_c = tabs[7];
         t.re_k = tabs[8];
         t.sol_g = tabs[9];
+        t.pk0 = tab_pk[0];
+        t.pk1 = tab_pk[1];
         t.branch = tab_branch;
         t.ntab = H->ntab;
         p.inlet_u = inlet_dev;
@@ -315,11 +345,12 @@ template <class L, class Real, class S> struct EngineT : Engine {
             CU(cudaStreamSynchronize(st));
         }
         CU(cudaMemsetAsync(health_dev, 0, sizeof(unsigned), st));
-        CU(cudaMemsetAsync(counts, 0, sizeof(int) * H->ncell, st));
+        CU(cudaMemsetAsync(counts, 0, sizeof(int) * (H->ncell + 1), st));
+        CU(cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
         if (H->np == 0) {
-            CU(cudaMemsetAsync(cell_start[0], 0, sizeof(int) * (H->ncell + 1), st));
-            CU(cudaMemsetAsync(cell_start[1], 0, sizeof(int) * (H->ncell + 1), st));
-            return LBDPS_OK;
+            int rc = clear_cells(0);
+            if (rc == LBDPS_OK) rc = clear_cells(1);
+            return rc;
         }
         return set_particles(pos_lat, vel_lat);
     }
@@ -356,50 +387,49 @@ template <class L, class Real, class S> struct EngineT : Engine {
     int sort_from(int src, int dst)
     {
         cudaStream_t st = H->stream;
-        CU(cudaMemsetAsync(counts, 0, sizeof(int) * H->ncell, st));
+        CU(cudaMemsetAsync(counts, 0, sizeof(int) * (H->ncell + 1), st));
         launch_cell_keys<D, Real>(H->n, part[src], key, counts, H->np, st);
         CHECK_LAUNCH();
-        launch_scan(counts, cell_start[dst], block_sums, H->ncell, st);
+        launch_cell_scan(counts, cells_out(dst), H->ncell, st);
         CHECK_LAUNCH();
-        launch_scatter_gather<Real>(H->ncell, D, key, counts, cell_start[dst], tmp, part[src],
-                                    part[dst], H->np, st);
+        launch_place<Real>(D, key, counts, cells(dst), slot, idslot, part[src], part[dst], H->np, st);
         CHECK_LAUNCH();
         return LBDPS_OK;
     }
 
     // One coupled step from buffers `parity` into buffers `1 - parity`.
-    // ev (optional, 6 events) brackets the kernel classes for profiling.
+    // ev (optional, 5 events) brackets the kernel classes for profiling:
+    // collide_stream, drag, sort, collide_particles.
     int enqueue_step(int parity, cudaEvent_t *ev) override
     {
         cudaStream_t st = H->stream;
         const int a = parity, b = 1 - parity;
         const int np = H->np;
         if (ev) CU(cudaEventRecord(ev[0], st));
-        launch_collide_stream<L, Real, S>(sp, f[a], f[b], cell_start[a], part[a], fld, st);
+        launch_collide_stream<L, Real, S>(sp, f[a], f[b], cells(a), part[a], fld, st);
         CHECK_LAUNCH();
         if (ev) CU(cudaEventRecord(ev[1], st));
-        launch_drag_pre<D, Real>(sp, part[a], cell_start[a], fld, fpre, gradp, np, st);
+        launch_drag_step<D, Real>(sp, part[a], stage, cells(a), fld, key, counts, diag_fpre,
+                                  diag_fd, np, st);
         CHECK_LAUNCH();
         if (ev) CU(cudaEventRecord(ev[2], st));
-        launch_drag_integrate<D, Real>(sp, part[a], cell_start[a], fld, fpre, gradp, key, counts,
-                                       diag_fpre, diag_fd, np, st);
-        CHECK_LAUNCH();
-        if (ev) CU(cudaEventRecord(ev[3], st));
         if (np > 0) {
-            launch_scan(counts, cell_start[b], block_sums, H->ncell, st);
+            launch_cell_scan(counts, cells_out(b), H->ncell, st);
             CHECK_LAUNCH();
-            launch_scatter_gather<Real>(H->ncell, D, key, counts, cell_start[b], tmp, part[a],
-                                        part[b], np, st);
+            Particles<Real> src = stage;
+            src.id = part[a].id;
+            launch_place<Real>(D, key, counts, cells(b), slot, idslot, src, part[b], np, st);
             CHECK_LAUNCH();
         } else {
-            CU(cudaMemsetAsync(cell_start[b], 0, sizeof(int) * (H->ncell + 1), st));
+            int rc = clear_cells(b);
+            if (rc) return rc;
         }
-        if (ev) CU(cudaEventRecord(ev[4], st));
-        launch_detect<D, Real>(sp, part[b], cell_start[b], best, wall, nullptr, nullptr, 0, np, st);
+        if (ev) CU(cudaEventRecord(ev[3], st));
+        launch_detect<D, Real>(sp, part[b], cells(b), best, wall, nullptr, nullptr, 0, np, st);
         CHECK_LAUNCH();
         launch_resolve<D, Real>(sp, part[b], best, wall, np, st);
         CHECK_LAUNCH();
-        if (ev) CU(cudaEventRecord(ev[5], st));
+        if (ev) CU(cudaEventRecord(ev[4], st));
         return LBDPS_OK;
     }
 
@@ -428,7 +458,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
             }
         }
         CU(cudaMemsetAsync(npairs_dev, 0, sizeof(unsigned long long), st));
-        launch_detect<D, Real>(sp, part[cur], cell_start[cur], best, wall, pairs_dev, npairs_dev,
+        launch_detect<D, Real>(sp, part[cur], cells(cur), best, wall, pairs_dev, npairs_dev,
                                pcap, np, st);
         CHECK_LAUNCH();
         launch_resolve<D, Real>(sp, part[cur], best, wall, np, st);
@@ -619,10 +649,12 @@ template <class L, class Real, class S> struct EngineT : Engine {
         } else if (which == LBDPS_PDIAG_ORDER) {
             for (int k = 0; k < np; ++k) out[k] = (double)ids[k];
         } else if (which == LBDPS_PDIAG_CELL) {
-            std::vector<int> cs;
-            if ((rc = d2h(cs, cell_start[cur], (size_t)H->ncell + 1))) return rc;
+            std::vector<int> loc, bas;
+            if ((rc = d2h(loc, cl_local[cur], (size_t)H->ncell + 1))) return rc;
+            if ((rc = d2h(bas, cl_base[cur], (size_t)cell_tiles(H->ncell) + 1))) return rc;
+            auto begin = [&](int c) { return loc[c] + bas[c >> kCellTileLog2]; };
             for (int c = 0; c < H->ncell; ++c)
-                for (int k = cs[c]; k < cs[c + 1]; ++k) out[ids[k]] = (double)c;
+                for (int k = begin(c); k < begin(c + 1); ++k) out[ids[k]] = (double)c;
         } else {
             return fail(LBDPS_ERR_INVALID, "unknown diagnostic %d", which);
         }
@@ -679,7 +711,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
     {
         const size_t nc = (size_t)H->ncell, np = (size_t)H->np;
         return sizeof(S) * Q * nc + (sizeof(double) + 2 * sizeof(Real)) * D * np +
-               2 * sizeof(int) * np + sizeof(int) * (nc + 1);
+               2 * sizeof(int) * np + sizeof(int) * (nc + 1) +
+               sizeof(int) * (cell_tiles(H->ncell) + 1);
     }
 
     int save(char *buf) override
@@ -702,7 +735,10 @@ template <class L, class Real, class S> struct EngineT : Engine {
         o += sizeof(int) * np;
         CU(cudaMemcpyAsync(buf + o, part[cur].cell, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
         o += sizeof(int) * np;
-        CU(cudaMemcpyAsync(buf + o, cell_start[cur], sizeof(int) * (nc + 1), cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(buf + o, cl_local[cur], sizeof(int) * (nc + 1), cudaMemcpyDeviceToHost, st));
+        o += sizeof(int) * (nc + 1);
+        CU(cudaMemcpyAsync(buf + o, cl_base[cur], sizeof(int) * (cell_tiles(H->ncell) + 1),
+                           cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
         return LBDPS_OK;
     }
@@ -727,8 +763,11 @@ template <class L, class Real, class S> struct EngineT : Engine {
         o += sizeof(int) * np;
         CU(cudaMemcpyAsync(part[cur].cell, buf + o, sizeof(int) * np, cudaMemcpyHostToDevice, st));
         o += sizeof(int) * np;
-        CU(cudaMemcpyAsync(cell_start[cur], buf + o, sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, st));
-        CU(cudaMemsetAsync(counts, 0, sizeof(int) * nc, st));
+        CU(cudaMemcpyAsync(cl_local[cur], buf + o, sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, st));
+        o += sizeof(int) * (nc + 1);
+        CU(cudaMemcpyAsync(cl_base[cur], buf + o, sizeof(int) * (cell_tiles(H->ncell) + 1),
+                           cudaMemcpyHostToDevice, st));
+        CU(cudaMemsetAsync(counts, 0, sizeof(int) * (nc + 1), st));
         CU(cudaStreamSynchronize(st));
         return LBDPS_OK;
     }
@@ -1035,16 +1074,16 @@ int lbdps_step(lbdps_t *h, int64_t nsteps)
 int lbdps_step_profiled(lbdps_t *h, int64_t nsteps, double *kernel_ms, int cap, int *nclass)
 {
     if (!h || nsteps < 0 || (!kernel_ms && cap > 0)) return fail(LBDPS_ERR_INVALID, "bad arguments");
-    constexpr int kClasses = 5;
+    constexpr int kClasses = 4;
     if (nclass) *nclass = kClasses;
-    cudaEvent_t ev[6];
-    for (int e = 0; e < 6; ++e) CU(cudaEventCreate(&ev[e]));
-    double acc[kClasses] = {0, 0, 0, 0, 0};
+    cudaEvent_t ev[kClasses + 1];
+    for (int e = 0; e <= kClasses; ++e) CU(cudaEventCreate(&ev[e]));
+    double acc[kClasses] = {0, 0, 0, 0};
     int rc = LBDPS_OK;
     for (int64_t s = 0; s < nsteps && rc == LBDPS_OK; ++s) {
         rc = h->eng->enqueue_step(h->parity, ev);
         if (rc) break;
-        if (cudaEventSynchronize(ev[5]) != cudaSuccess) {
+        if (cudaEventSynchronize(ev[kClasses]) != cudaSuccess) {
             rc = fail(LBDPS_ERR_CUDA, "profiling: %s", cudaGetErrorString(cudaGetLastError()));
             break;
         }
@@ -1056,7 +1095,7 @@ int lbdps_step_profiled(lbdps_t *h, int64_t nsteps, double *kernel_ms, int cap, 
         h->parity ^= 1;
         h->steps++;
     }
-    for (int e = 0; e < 6; ++e) cudaEventDestroy(ev[e]);
+    for (int e = 0; e <= kClasses; ++e) cudaEventDestroy(ev[e]);
     for (int c = 0; c < kClasses && c < cap; ++c) kernel_ms[c] = acc[c];
     return rc;
 }

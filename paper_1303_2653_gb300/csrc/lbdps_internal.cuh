@@ -32,6 +32,8 @@ struct D2Q9 {
     {
         return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
     }
+    // first member of the k-th opposite pair (k = 0..3): 1, 2, 5, 6
+    __host__ __device__ static constexpr int pair_first(int k) { return k < 2 ? k + 1 : k + 3; }
     __host__ __device__ static constexpr double w(int i)
     {
         return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
@@ -50,6 +52,8 @@ struct D3Q19 {
                          : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
     }
     __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+    // first member of the k-th opposite pair (k = 0..8): 1, 3, 5, ..., 17
+    __host__ __device__ static constexpr int pair_first(int k) { return 2 * k + 1; }
     __host__ __device__ static constexpr double w(int i)
     {
         return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
@@ -89,7 +93,15 @@ template <> struct Store<__nv_bfloat16> {
 // Index n = particles whose centre lies in the cell, clamped to ntab - 1
 // (beyond that the solid fraction is at its close-packing cap).
 // ---------------------------------------------------------------------------
+template <class R> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4; };
+
 template <class Real> struct CountTables {
+    // packed copies for the lattice kernel: pk0 = {og, gam, inv_div, beta_a},
+    // pk1 = {beta_b, beta_c, re_k, branch}
+    const typename Vec4<Real>::type *pk0;
+    const typename Vec4<Real>::type *pk1;
     const Real *eps_s;    // solid fraction (Eq. 10, capped)
     const Real *eps_g;    // gas voidage for the drag (Eq. 11 in 2D)
     const Real *sol_g;    // 1 - eps_g, kept separately so 1 - eps_k needs no cancellation
@@ -153,8 +165,28 @@ template <class Real> struct Particles {
 // ---------------------------------------------------------------------------
 // Launchers (defined in the .cu files, explicitly instantiated).
 // ---------------------------------------------------------------------------
+// Cell list after a sort: particles of cell c occupy sorted slots
+// begin(c) .. begin(c + 1) - 1.  It is kept in two levels so that one kernel
+// can produce it: an exclusive prefix of the per-cell counts inside each tile
+// of 4096 cells, and the exclusive prefix of the tile totals.
+constexpr int kCellTileLog2 = 12;
+constexpr int kCellTile = 1 << kCellTileLog2;
+struct CellList {
+    const int *local;   // ncell + 1 entries
+    const int *base;    // cell_tiles(ncell) + 1 entries
+    __device__ __forceinline__ int begin(int c) const
+    {
+        return __ldg(local + c) + __ldg(base + (c >> kCellTileLog2));
+    }
+};
+struct CellListOut {
+    int *local, *base, *tile_total;
+    unsigned *ticket;   // zero between launches
+};
+inline int cell_tiles(int ncell) { return (ncell + 1 + kCellTile - 1) / kCellTile; }
+
 template <class L, class Real, class S>
-void launch_collide_stream(const StepParams<Real> &p, const S *fin, S *fout, const int *cell_start,
+void launch_collide_stream(const StepParams<Real> &p, const S *fin, S *fout, CellList cells,
                            Particles<Real> parts, Fields<Real> fld, cudaStream_t st);
 
 template <class L, class Real, class S>
@@ -171,31 +203,34 @@ void launch_build_tables(int dim, double tau, double r, double vp, double d, dou
                          int superficial_mode, int ntab, double *scratch, CountTables<Real> tab,
                          cudaStream_t st);
 
+// Fig. 4 steps 4-5 in one launch: Eq. 26-28 and the integration of Eq. 16.
+// `out` receives the integrated P, v and in-cell offset in the same slots.
 template <int D, class Real>
-void launch_drag_pre(const StepParams<Real> &p, Particles<Real> parts, const int *cell_start,
-                     Fields<Real> fld, Real *fpre, Real *gradp, int np, cudaStream_t st);
-
-template <int D, class Real>
-void launch_drag_integrate(const StepParams<Real> &p, Particles<Real> parts, const int *cell_start,
-                           Fields<Real> fld, const Real *fpre, const Real *gradp, int *key,
-                           int *counts, Real *diag_fpre, Real *diag_fd, int np, cudaStream_t st);
+void launch_drag_step(const StepParams<Real> &p, Particles<Real> parts, Particles<Real> out,
+                      CellList cells, Fields<Real> fld, int *key, int *counts, Real *diag_fpre,
+                      Real *diag_fd, int np, cudaStream_t st);
 
 template <int D, class Real>
 void launch_cell_keys(const int *n, Particles<Real> parts, int *key, int *counts, int np,
                       cudaStream_t st);
 
-void launch_scan(const int *counts, int *cell_start, int *block_sums, int ncell, cudaStream_t st);
-int scan_block_count(int ncell);
+// one-launch scan of counts[0..ncell] (counts[ncell] = 0) into a CellList
+void launch_cell_scan(const int *counts, CellListOut out, int ncell, cudaStream_t st);
 
+// slot placement and in-cell ordering by id: src (any order) -> dst (cell, id)
 template <class Real>
-void launch_scatter_gather(int ncell, int dim, const int *key, int *counts, const int *cell_start,
-                           int *tmp, Particles<Real> src, Particles<Real> dst, int np,
-                           cudaStream_t st);
+void launch_place(int dim, const int *key, int *counts, CellList cells, int *slot, int *idslot,
+                  Particles<Real> src, Particles<Real> dst, int np, cudaStream_t st);
 
 template <int D, class Real>
-void launch_detect(const StepParams<Real> &p, Particles<Real> parts, const int *cell_start,
-                   int *best, int *wall, long long *pairs, unsigned long long *npairs,
-                   long long pair_cap, int np, cudaStream_t st);
+void launch_detect(const StepParams<Real> &p, Particles<Real> parts, CellList cells, int *best,
+                   int *wall, long long *pairs, unsigned long long *npairs, long long pair_cap,
+                   int np, cudaStream_t st);
+
+// three-kernel scan into a plain cell_start[ncell + 1] (used by the
+// allocation-free binning entry point)
+void launch_scan(const int *counts, int *cell_start, int *block_sums, int ncell, cudaStream_t st);
+int scan_block_count(int ncell);
 
 template <int D, class Real>
 void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int *best,

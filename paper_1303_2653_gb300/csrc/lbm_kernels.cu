@@ -16,6 +16,7 @@ namespace lbdpsk {
 template <class Real> struct TableOut {
     Real *eps_s, *eps_g, *inv_div, *og, *gam, *beta_a, *beta_b, *beta_c, *re_k, *sol_g;
     int *branch;
+    typename Vec4<Real>::type *pk0, *pk1;
 };
 
 __device__ double emms_omega(double eg)
@@ -79,6 +80,8 @@ __global__ void k_build_tables(int dim, double tau, double r, double vp, double 
             t.beta_c[n] = (Real)0.0;
             t.re_k[n] = (Real)0.0;
         }
+        t.pk0[n] = {t.og[n], t.gam[n], t.inv_div[n], t.beta_a[n]};
+        t.pk1[n] = {t.beta_b[n], t.beta_c[n], t.re_k[n], (Real)t.branch[n]};
     }
 }
 
@@ -92,7 +95,9 @@ void launch_build_tables(int dim, double tau, double r, double vp, double d, dou
                      const_cast<Real *>(tab.gam), const_cast<Real *>(tab.beta_a),
                      const_cast<Real *>(tab.beta_b), const_cast<Real *>(tab.beta_c),
                      const_cast<Real *>(tab.re_k), const_cast<Real *>(tab.sol_g),
-                     const_cast<int *>(tab.branch)};
+                     const_cast<int *>(tab.branch),
+                     const_cast<typename Vec4<Real>::type *>(tab.pk0),
+                     const_cast<typename Vec4<Real>::type *>(tab.pk1)};
     int blocks = (ntab + 127) / 128;
     k_build_tables<Real><<<blocks, 128, 0, st>>>(dim, tau, r, vp, d, mu, superficial_mode, ntab, t);
 }
@@ -130,11 +135,61 @@ __device__ __forceinline__ Real cdot(int i, const Real *u)
 // correctly rounded pow in FP64.
 __device__ __forceinline__ float re_pow(float re) { return re > 0.f ? __powf(re, 0.687f) : 0.f; }
 __device__ __forceinline__ double re_pow(double re) { return pow(re, 0.687); }
+// Reciprocal and square root: hardware approximations (a few ulp) in FP32,
+// correctly rounded in FP64.
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_pos(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double sqrt_pos(double x) { return sqrt(x); }
 
+// Blocks per SM requested from the register allocator: D2Q9 in FP32 fits in
+// ~40 registers (6 blocks of 256 threads), D3Q19 and FP64 need more.
+template <class L, class Real> struct K2Occupancy { static constexpr int value = 4; };
+#ifndef LBDPS_K2_BLOCKS_D2Q9_F32
+#define LBDPS_K2_BLOCKS_D2Q9_F32 6
+#endif
+#ifndef LBDPS_K2_BLOCKS_D3Q19_F32
+#define LBDPS_K2_BLOCKS_D3Q19_F32 4
+#endif
+template <> struct K2Occupancy<D2Q9, float> { static constexpr int value = LBDPS_K2_BLOCKS_D2Q9_F32; };
+template <> struct K2Occupancy<D3Q19, float> { static constexpr int value = LBDPS_K2_BLOCKS_D3Q19_F32; };
+template <> struct K2Occupancy<D3Q19, double> { static constexpr int value = 2; };
+
+// Store one post-collision population of direction I: to the neighbour, or
+// reflected into this cell's opposite slot by a wall (half-way bounce-back
+// with the moving-wall term -6 w_i rho c_i.u_w of the first wall crossed), or
+// dropped through an inlet/outlet face.
 template <class L, class Real, class S>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void emit_population(int I, const StepParams<Real> &p, S *__restrict__ fout,
+                                                size_t nc, int x, Real post, Real rho, bool on_face,
+                                                int wall_mask, int open_mask, int offp0, int offm0,
+                                                int offp1, int offm1, int offp2, int offm2)
+{
+    const int cx = L::c(I, 0), cy = L::c(I, 1), cz = L::c(I, 2);
+    const int off = (cx == 1 ? offp0 : cx == -1 ? offm0 : 0) + (cy == 1 ? offp1 : cy == -1 ? offm1 : 0) +
+                    (cz == 1 ? offp2 : cz == -1 ? offm2 : 0);
+    if (!on_face) {
+        fout[(size_t)I * nc + (x + off)] = Store<S>::save(post);
+        return;
+    }
+    // faces crossed by this direction, as bits of the masks
+    const int crossed = (cx == 1 ? 2 : cx == -1 ? 1 : 0) | (cy == 1 ? 8 : cy == -1 ? 4 : 0) |
+                            (cz == 1 ? 32 : cz == -1 ? 16 : 0);
+    const int walls = wall_mask & crossed;
+    if (walls) {
+        const int face = __ffs(walls) - 1;   // first (lowest-axis) wall crossed
+        const Real cw = Real(cx) * p.wall_u[face][0] + Real(cy) * p.wall_u[face][1] +
+                        Real(cz) * p.wall_u[face][2];
+        fout[(size_t)L::opp(I) * nc + x] = Store<S>::save(post - Real(6) * Real(L::w(I)) * rho * cw);
+    } else if (!(open_mask & crossed)) {
+        fout[(size_t)I * nc + (x + off)] = Store<S>::save(post);
+    }
+}
+
+template <class L, class Real, class S, bool LES, bool FB>
+__global__ void __launch_bounds__(256, K2Occupancy<L, Real>::value)
 k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ fout,
-                 const int *__restrict__ cell_start, Particles<Real> parts, Fields<Real> fld)
+                 CellList cells, Particles<Real> parts, Fields<Real> fld)
 {
     constexpr int D = L::D, Q = L::Q;
     // grid: x along blockIdx.x/threadIdx.x, y = blockIdx.y, z = blockIdx.z
@@ -151,7 +206,7 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
     for (int i = 0; i < Q; ++i) f[i] = Store<S>::load(fin[(size_t)i * nc + x]);
 
     // ---- deposition (Eq. 8) ----
-    const int s0 = cell_start[x], s1 = cell_start[x + 1];
+    const int s0 = cells.begin(x), s1 = cells.begin(x + 1);
     const int n = s1 - s0;
     Real vs[3] = {Real(0), Real(0), Real(0)};
     for (int k = s0; k < s1; ++k) {
@@ -159,12 +214,15 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
         for (int a = 0; a < D; ++a) vs[a] += parts.v[a][k];
     }
     if (n > 1) {
-        const Real inv_n = Real(1) / Real(n);
+        const Real inv_n = rcp(Real(n));
 #pragma unroll
         for (int a = 0; a < D; ++a) vs[a] *= inv_n;
     }
     const int nn = n < p.tab.ntab ? n : p.tab.ntab - 1;
-    const Real og = p.tab.og[nn];
+    const auto t0 = p.tab.pk0[nn];   // og, gam, inv_div, beta_a
+    const auto t1 = p.tab.pk1[nn];   // beta_b, beta_c, re_k, branch
+    // an empty cell has og = 0 and v_s = 0, so the solid term below vanishes
+    const Real og = t0.x;
 
     // ---- moments ----
     Real drho = Real(0), m[3] = {Real(0), Real(0), Real(0)};
@@ -181,41 +239,44 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
 
     // ---- Eq. 24 in closed form ----
     const Real half_og = Real(0.5) * og;
-    const Real inv_denom = Real(1) / (rho * (Real(1) - half_og));
+    const Real inv_denom = rcp(rho * (Real(1) - half_og));
     Real u[3] = {Real(0), Real(0), Real(0)};
-    Real uu = Real(0);
+    Real uu = Real(0), vv = Real(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         u[a] = (m[a] * (Real(1) - og) + half_og * rho * vs[a] + Real(0.5) * p.fb[a]) * inv_denom;
         uu += u[a] * u[a];
+        vv += vs[a] * vs[a];
     }
-
-    // equilibrium deviations feq_i - w_i = w_i [(rho-1) + rho (3cu + 9/2 cu^2 - 3/2 uu)]
-    Real feu[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        Real cu = cdot<L>(i, u);
-        feu[i] = Real(L::w(i)) * (drho + rho * (Real(3) * cu + Real(4.5) * cu * cu - Real(1.5) * uu));
-    }
+    // feq_i - w_i = w_i [(rho - 1) + rho (3 cu + 9/2 cu^2 - 3/2 uu)], Eq. 4
+    const Real eq0 = drho - Real(1.5) * rho * uu;
+    const Real es0 = drho - Real(1.5) * rho * vv;
 
     // ---- LES (Eq. 13-15) ----
-    Real inv_tau_t = p.inv_tau, gam_t = p.tab.gam[nn], tau_t = p.tau;
-    if (p.les_k > Real(0)) {
-        Real qs = Real(0);
+    Real inv_tau_t = p.inv_tau, gam_t = t0.y, tau_t = p.tau;
+    if (LES) {
+        Real qab[6] = {Real(0), Real(0), Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
+        for (int i = 0; i < Q; ++i) {
+            const Real cu = cdot<L>(i, u);
+            const Real neq = f[i] - Real(L::w(i)) * (eq0 + rho * (Real(3) * cu + Real(4.5) * cu * cu));
+            int k = 0;
 #pragma unroll
-            for (int b = a; b < D; ++b) {
-                Real qab = Real(0);
+            for (int a = 0; a < D; ++a) {
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
+                for (int b = a; b < D; ++b, ++k) {
                     const int cc = L::c(i, a) * L::c(i, b);
-                    if (cc == 1) qab += f[i] - feu[i];
-                    else if (cc == -1) qab -= f[i] - feu[i];
+                    if (cc == 1) qab[k] += neq;
+                    else if (cc == -1) qab[k] -= neq;
                 }
-                qs += (a == b ? Real(1) : Real(2)) * qab * qab;
             }
         }
+        Real qs = Real(0);
+        int k = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = a; b < D; ++b, ++k) qs += (a == b ? Real(1) : Real(2)) * qab[k] * qab[k];
         const Real qn = sqrt(Real(2) * qs);
         tau_t = Real(0.5) * (p.tau + sqrt(p.tau * p.tau + p.les_k * qn / rho));
         inv_tau_t = Real(1) / tau_t;
@@ -223,59 +284,94 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
         gam_t = es * (tau_t - Real(0.5)) / ((Real(1) - es) + (tau_t - Real(0.5)));
     }
     const Real relax = inv_tau_t * (Real(1) - gam_t);
+    const Real pref = Real(1) - Real(0.5) * inv_tau_t;
+    Real uF = Real(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) uF += u[a] * p.fb[a];
 
-    // ---- collision (Eq. 7, 23) ----
-    Real fpost[Q];
-    if (n > 0) {
-        Real vv = Real(0);
+    // ---- streaming geometry of this cell (Eq. 2, push) ----
+    // offp/offm: linear offset to the +/- neighbour along each axis with
+    // periodic wrap folded in; bit 2a (2a+1) of wall_mask / open_mask: the
+    // low (high) face of this cell along axis a is a wall / an inlet-outlet.
+    int offp0 = 1, offm0 = -1, offp1 = p.n[0], offm1 = -p.n[0];
+    int offp2 = p.n[0] * p.n[1], offm2 = -p.n[0] * p.n[1];
+    int wall_mask = 0, open_mask = 0;
 #pragma unroll
-        for (int a = 0; a < D; ++a) vv += vs[a] * vs[a];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int io = L::opp(i);
-            Real cv = cdot<L>(i, vs);
-            Real fes = Real(L::w(i)) * (drho + rho * (Real(3) * cv + Real(4.5) * cv * cv - Real(1.5) * vv));
-            Real omega_s = f[io] - f[i] + fes - feu[io];
-            fpost[i] = f[i] - relax * (f[i] - feu[i]) + og * omega_s;
+    for (int a = 0; a < D; ++a) {
+        const int st = a == 0 ? 1 : (a == 1 ? p.n[0] : p.n[0] * p.n[1]);
+        int op = st, om = -st;
+        if (idx[a] == p.n[a] - 1) {
+            const int bc = p.bc[2 * a + 1];
+            if (bc == BC_PERIODIC) op = -(p.n[a] - 1) * st;
+            else if (bc == BC_WALL) wall_mask |= 1 << (2 * a + 1);
+            else open_mask |= 1 << (2 * a + 1);
         }
-    } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) fpost[i] = f[i] - relax * (f[i] - feu[i]);
+        if (idx[a] == 0) {
+            const int bc = p.bc[2 * a];
+            if (bc == BC_PERIODIC) om = (p.n[a] - 1) * st;
+            else if (bc == BC_WALL) wall_mask |= 1 << (2 * a);
+            else open_mask |= 1 << (2 * a);
+        }
+        if (a == 0) { offp0 = op; offm0 = om; }
+        else if (a == 1) { offp1 = op; offm1 = om; }
+        else { offp2 = op; offm2 = om; }
     }
-    if (p.has_fb) {
-        // Guo source w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F_b (1 - 1/(2 tau_t))
-        const Real pref = Real(1) - Real(0.5) * inv_tau_t;
-        Real uF = Real(0);
+    const bool on_face = (wall_mask | open_mask) != 0;
+#define LBDPS_EMIT(I, POST)                                                                        \
+    emit_population<L, Real, S>((I), p, fout, nc, x, (POST), rho, on_face, wall_mask, open_mask,  \
+                                      offp0, offm0, offp1, offm1, offp2, offm2)
+    {
+        // rest population: cu = cv = 0
+        const Real w = Real(L::w(0));
+        Real post = f[0] - relax * (f[0] - w * eq0) + og * w * (es0 - eq0);
+        if (FB) post -= pref * w * Real(3) * uF;
+        LBDPS_EMIT(0, post);
+    }
+    const Real r3 = Real(3) * rho, r45 = Real(4.5) * rho;
 #pragma unroll
-        for (int a = 0; a < D; ++a) uF += u[a] * p.fb[a];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const Real cu = cdot<L>(i, u);
+    for (int k = 0; k < (Q - 1) / 2; ++k) {
+        const int i = L::pair_first(k), io = L::opp(i);
+        const Real w = Real(L::w(i));
+        const Real cu = cdot<L>(i, u);
+        const Real cv = cdot<L>(i, vs);
+        const Real Eu = w * (eq0 + r45 * cu * cu), Au = w * r3 * cu;
+        const Real Es = w * (es0 + r45 * cv * cv), As = w * r3 * cv;
+        const Real feu_i = Eu + Au, feu_o = Eu - Au;      // feq_i(u), feq_-i(u), minus w
+        const Real fi = f[i], fo = f[io];
+        Real post_i = fi - relax * (fi - feu_i) + og * (fo - fi + (Es + As) - feu_o);
+        Real post_o = fo - relax * (fo - feu_o) + og * (fi - fo + (Es - As) - feu_i);
+        if (FB) {
             const Real cF = cdot<L>(i, p.fb);
-            const Real src = Real(3) * (cF - uF) + Real(9) * cu * cF;
-            fpost[i] += pref * Real(L::w(i)) * src;
+            const Real even = pref * w * (Real(9) * cu * cF - Real(3) * uF);
+            const Real odd = pref * w * Real(3) * cF;
+            post_i += even + odd;
+            post_o += even - odd;
         }
+        LBDPS_EMIT(i, post_i);
+        LBDPS_EMIT(io, post_o);
     }
+
+#undef LBDPS_EMIT
 
     // ---- node outputs (Eq. 5, 24, 25, 19) ----
-    const Real inv_div = p.tab.inv_div[nn];
+    const Real inv_div = t0.z;
     Real slip2 = Real(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         fld.u[a][x] = u[a];
         fld.fpg[a][x] = og * (rho * u[a] + rho * vs[a] - Real(2) * m[a]);
-        Real sl = u[a] * inv_div - vs[a];
+        const Real sl = u[a] * inv_div - vs[a];
         slip2 += sl * sl;
     }
     fld.rho[x] = rho;
-    const Real slip = sqrt(slip2);
+    const Real slip = sqrt_pos(slip2);
     Real beta;
-    if (p.tab.branch[nn] == 0) {
-        beta = p.tab.beta_a[nn] + p.tab.beta_b[nn] * slip;
+    if (t1.w == Real(0)) {
+        beta = t0.w + t1.x * slip;                                   // Ergun
     } else {
-        const Real re = p.tab.re_k[nn] * slip;
-        beta = (re < Real(1000)) ? p.tab.beta_a[nn] * (Real(1) + Real(0.15) * re_pow(re))
-                                 : p.tab.beta_c[nn] * slip;
+        const Real re = t1.z * slip;                                 // Eq. 22
+        beta = (re < Real(1000)) ? t0.w * (Real(1) + Real(0.15) * re_pow(re))   // Eq. 19, 21
+                                 : t1.y * slip;
     }
     fld.beta[x] = beta;
     if (fld.ntot) {
@@ -290,54 +386,14 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
     }
     if (!(rho > Real(0)) || !(uu < Real(0.09))) atomicOr(p.health, HEALTH_DIVERGED);
 
-    // ---- streaming (Eq. 2, push) ----
-    bool interior = true;
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-        if (idx[a] == 0 || idx[a] == p.n[a] - 1) interior = false;
-    const int stride[3] = {1, p.n[0], p.n[0] * p.n[1]};
-    if (interior) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            int off = 0;
-#pragma unroll
-            for (int a = 0; a < D; ++a) off += L::c(i, a) * stride[a];
-            fout[(size_t)i * nc + (x + off)] = Store<S>::save(fpost[i]);
-        }
-        return;
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        int wall = -1, open = -1, tgt = 0;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            int q = idx[a] + L::c(i, a);
-            if (q < 0 || q >= p.n[a]) {
-                const int face = 2 * a + (q < 0 ? 0 : 1);
-                const int bc = p.bc[face];
-                if (bc == BC_PERIODIC) q = (q + p.n[a]) % p.n[a];
-                else if (bc == BC_WALL) { if (wall < 0) wall = face; }
-                else { if (open < 0) open = face; }
-            }
-            tgt += q * stride[a];
-        }
-        if (wall >= 0) {
-            Real cw = Real(0);
-#pragma unroll
-            for (int a = 0; a < D; ++a) cw += Real(L::c(i, a)) * p.wall_u[wall][a];
-            fout[(size_t)L::opp(i) * nc + x] =
-                Store<S>::save(fpost[i] - Real(6) * Real(L::w(i)) * rho * cw);
-        } else if (open < 0) {
-            fout[(size_t)i * nc + tgt] = Store<S>::save(fpost[i]);
-        }
-    }
-    // populations entering through an inlet or outlet face
+    // ---- populations entering through an inlet or outlet face ----
+    if (open_mask == 0) return;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         int wall = -1, open = -1;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            int q = idx[a] - L::c(i, a);
+            const int q = idx[a] - L::c(i, a);
             if (q < 0 || q >= p.n[a]) {
                 const int face = 2 * a + (q < 0 ? 0 : 1);
                 const int bc = p.bc[face];
@@ -365,13 +421,21 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
 }
 
 template <class L, class Real, class S>
-void launch_collide_stream(const StepParams<Real> &p, const S *fin, S *fout, const int *cell_start,
+void launch_collide_stream(const StepParams<Real> &p, const S *fin, S *fout, CellList cells,
                            Particles<Real> parts, Fields<Real> fld, cudaStream_t st)
 {
     // one block row per lattice row; up to 256 threads along x
     const int tx = p.n[0] >= 256 ? 256 : ((p.n[0] + 31) / 32) * 32;
     const dim3 grid((p.n[0] + tx - 1) / tx, p.n[1], L::D == 3 ? p.n[2] : 1);
-    k_collide_stream<L, Real, S><<<grid, tx, 0, st>>>(p, fin, fout, cell_start, parts, fld);
+    const bool les = p.les_k > Real(0), fb = p.has_fb != 0;
+    if (les && fb)
+        k_collide_stream<L, Real, S, true, true><<<grid, tx, 0, st>>>(p, fin, fout, cells, parts, fld);
+    else if (les)
+        k_collide_stream<L, Real, S, true, false><<<grid, tx, 0, st>>>(p, fin, fout, cells, parts, fld);
+    else if (fb)
+        k_collide_stream<L, Real, S, false, true><<<grid, tx, 0, st>>>(p, fin, fout, cells, parts, fld);
+    else
+        k_collide_stream<L, Real, S, false, false><<<grid, tx, 0, st>>>(p, fin, fout, cells, parts, fld);
 }
 
 // ---------------------------------------------------------------------------
@@ -437,8 +501,7 @@ void launch_import_populations(int ncell, const double *in, S *f, cudaStream_t s
 // ---------------------------------------------------------------------------
 #define LBDPS_INST_LBM(L, R, S)                                                                    \
     template void launch_collide_stream<L, R, S>(const StepParams<R> &, const S *, S *,            \
-                                                 const int *, Particles<R>, Fields<R>,             \
-                                                 cudaStream_t);                                    \
+                                                 CellList, Particles<R>, Fields<R>, cudaStream_t);  \
     template void launch_init_equilibrium<L, R, S>(int, const R *, S *, cudaStream_t);             \
     template void launch_export_populations<L, R, S>(int, const S *, double *, cudaStream_t);      \
     template void launch_import_populations<L, R, S>(int, const double *, S *, cudaStream_t);

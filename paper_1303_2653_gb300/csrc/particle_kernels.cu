@@ -3,10 +3,10 @@
 // Fig. 1, and the time-driven hard-sphere collisions (step 6, Eq. 17-18).
 //
 // FP64 is slow on this part, so per-particle FP64 work is limited to the
-// position update and its floor; everything per pair or per stencil node uses
-// the cell index and the in-cell offset carried with each particle, and the
-// exact FP64 contact test runs only for pairs that an FP32 test with a safety
-// margin cannot exclude.
+// position update (and its floor when the particle may leave its cell);
+// everything per pair or per stencil node uses the cell index and the in-cell
+// offset carried with each particle, and the exact FP64 contact test runs
+// only for pairs that an FP32 test with a safety margin cannot exclude.
 #include "lbdps_internal.cuh"
 
 #include <climits>
@@ -49,13 +49,14 @@ __device__ __forceinline__ double sep_axis(double pi, double pj, bool periodic, 
 }
 
 // ---------------------------------------------------------------------------
-// K3a: pre-estimated drag of Eq. 26 per particle.  u, beta, eps and grad p
+// Pre-estimated drag of Eq. 26 for one particle.  u, beta, 1 - eps and grad p
 // are interpolated bilinearly (trilinearly in 3D) from the cell-centre nodes
 // around the particle (Fig. 4 step 4); nodes outside a wall clamp to the
 // nearest cell, periodic faces wrap.  grad p uses central differences of
-// p = rho/3 (one-sided next to non-periodic faces).
+// p = rho/3 (one-sided next to non-periodic faces).  1 - eps is interpolated
+// from the tabulated solid fraction so that it needs no cancellation.
 // ---------------------------------------------------------------------------
-template <int D, class Real>
+template <class Real>
 __device__ __forceinline__ Real node_gradp(const StepParams<Real> &p, const Real *rho, const int *q,
                                            int a)
 {
@@ -72,14 +73,10 @@ __device__ __forceinline__ Real node_gradp(const StepParams<Real> &p, const Real
 }
 
 template <int D, class Real>
-__global__ void __launch_bounds__(256)
-k_drag_pre(StepParams<Real> p, Particles<Real> parts, const int *__restrict__ cell_start,
-           Fields<Real> fld, Real *__restrict__ fpre, Real *__restrict__ gradp, int np)
+__device__ __forceinline__ void drag_pre_one(const StepParams<Real> &p, const Particles<Real> &parts,
+                                             const CellList &cells, const Fields<Real> &fld,
+                                             const int *idx, int k, Real *fp, Real *gp)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= np) return;
-    int idx[3];
-    cell_coords(D, p.n, parts.cell[k], idx);
     int i0[3] = {0, 0, 0}, i1[3] = {0, 0, 0};
     Real w1[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
@@ -113,13 +110,13 @@ k_drag_pre(StepParams<Real> p, Particles<Real> parts, const int *__restrict__ ce
             wt *= bit ? w1[a] : (Real(1) - w1[a]);
         }
         const int node = q[0] + p.n[0] * (q[1] + p.n[1] * q[2]);
-        const int cnt = cell_start[node + 1] - cell_start[node];
+        const int cnt = cells.begin(node + 1) - cells.begin(node);
         const int nn = cnt < p.tab.ntab ? cnt : p.tab.ntab - 1;
         const Real inv_div = p.tab.inv_div[nn];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             uk[a] += wt * (fld.u[a][node] * inv_div);
-            gk[a] += wt * node_gradp<D>(p, fld.rho, q, a);
+            gk[a] += wt * node_gradp<Real>(p, fld.rho, q, a);
         }
         sk += wt * p.tab.sol_g[nn];
         bk += wt * fld.beta[node];
@@ -127,112 +124,150 @@ k_drag_pre(StepParams<Real> p, Particles<Real> parts, const int *__restrict__ ce
     const Real coef = p.vp * bk / sk;   // V_p beta_k / (1 - eps_k), Eq. 26
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        fpre[(size_t)a * np + k] = coef * (uk[a] - parts.v[a][k]);
-        gradp[(size_t)a * np + k] = gk[a];
+        fp[a] = coef * (uk[a] - parts.v[a][k]);
+        gp[a] = gk[a];
     }
 }
 
-template <int D, class Real>
-void launch_drag_pre(const StepParams<Real> &p, Particles<Real> parts, const int *cell_start,
-                     Fields<Real> fld, Real *fpre, Real *gradp, int np, cudaStream_t st)
-{
-    if (np == 0) return;
-    k_drag_pre<D, Real><<<(np + 255) / 256, 256, 0, st>>>(p, parts, cell_start, fld, fpre, gradp, np);
-}
-
 // ---------------------------------------------------------------------------
-// K3b: Eq. 27-28 and the step-5 integration of Eq. 16.
-//   S^a(c) = sum of F_pre^a over the particles of cell c in sorted order
-//   F_d^a  = |F_p->g^a(c)| / |S^a(c)| * F_pre^a   (scale 1 when |S| <= 1e-12 sum|F_pre|)
-//   v     += (1 - rho_g/rho_s) g + (F_d -+ V_p grad p) / m_p
-//   P     += v  (FP64), specular walls (v_n -> -e v_n), periodic wrap
-// then the new cell key, the new in-cell offset and the key's count
-// (histogram for the sort).
+// Drag and integration (Fig. 4 steps 4-5), one thread per particle.
+//   F_pre of the thread's particle (Eq. 26);
+//   S^a(c) = sum of F_pre^a over the particles of its cell in sorted order
+//           (Eq. 27): members in the same warp come by shuffle, members in a
+//           neighbouring warp are recomputed (bit-identical), so every member
+//           of a cell adds the same values in the same order;
+//   F_d^a  = |F_p->g^a(c)| / |S^a| F_pre^a (Eq. 28; scale 1 when
+//           |S| <= 1e-12 sum |F_pre|);
+//   v += (1 - rho_g/rho_s) g + (F_d -+ V_p grad p) / m_p, P += v in FP64
+//   (Eq. 16, symplectic Euler), specular walls (v_n -> -e v_n), periodic
+//   wrap, then the new cell key, in-cell offset and its count for the sort.
+// A particle that stays well inside its cell (FP32 offset test with a 1e-3
+// margin, far above the offset rounding) takes its new offset from one FP64
+// subtraction; otherwise the full FP64 wall / wrap / floor path runs.  Both
+// give bit-identical results.
 // ---------------------------------------------------------------------------
 template <int D, class Real>
 __global__ void __launch_bounds__(256)
-k_drag_integrate(StepParams<Real> p, Particles<Real> parts, const int *__restrict__ cell_start,
-                 Fields<Real> fld, const Real *__restrict__ fpre, const Real *__restrict__ gradp,
-                 int *__restrict__ key, int *__restrict__ counts, Real *diag_fpre, Real *diag_fd,
-                 int np)
+k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, CellList cells,
+            Fields<Real> fld, int *__restrict__ key, int *__restrict__ counts, Real *diag_fpre,
+            Real *diag_fd, int np)
 {
+    // the integrated state goes to `out` (same slots): other warps may still
+    // read this particle's pre-step state to complete their cell sums
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= np) return;
-    const int c = parts.cell[k];
-    const int s0 = cell_start[c], s1 = cell_start[c + 1];
+    const int lane = threadIdx.x & 31;
+    const bool active = k < np;
+    const int warp_first = k - lane;
+    int c = -1, s0 = 0, s1 = 0;
+    int idx[3] = {0, 0, 0};
+    Real fp[3] = {Real(0), Real(0), Real(0)}, gp[3] = {Real(0), Real(0), Real(0)};
+    if (active) {
+        c = parts.cell[k];
+        s0 = cells.begin(c);
+        s1 = cells.begin(c + 1);
+        cell_coords(D, p.n, c, idx);
+        drag_pre_one<D, Real>(p, parts, cells, fld, idx, k, fp, gp);
+    }
+    // Eq. 27 in sorted order
+    const int len = s1 - s0;
+    const int maxlen = __reduce_max_sync(0xffffffffu, len);
     Real S[3] = {Real(0), Real(0), Real(0)}, A[3] = {Real(0), Real(0), Real(0)};
-    for (int j = s0; j < s1; ++j) {
+    for (int t = 0; t < maxlen; ++t) {
+        const int j = s0 + t;
+        const bool in_warp = (j >= warp_first) && (j < warp_first + 32);
+        Real val[3];
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const Real fj = fpre[(size_t)a * np + j];
-            S[a] += fj;
-            A[a] += fabs(fj);
+        for (int a = 0; a < D; ++a) val[a] = __shfl_sync(0xffffffffu, fp[a], (j - warp_first) & 31);
+        if (t < len) {
+            if (!in_warp) {
+                Real g2[3];
+                drag_pre_one<D, Real>(p, parts, cells, fld, idx, j, val, g2);
+            }
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                S[a] += val[a];
+                A[a] += fabs(val[a]);
+            }
         }
     }
+    if (!active) return;
+
     const int id = parts.id[k];
-    unsigned flags = 0;
     double P[3] = {0.0, 0.0, 0.0};
-    Real v[3] = {Real(0), Real(0), Real(0)};
+    Real v[3] = {Real(0), Real(0), Real(0)}, off[3] = {Real(0), Real(0), Real(0)};
+    int q[3] = {0, 0, 0};
+    bool stays = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        P[a] = parts.P[a][k];
-        v[a] = parts.v[a][k];
         Real scale = Real(1);
         if (!(fabs(S[a]) <= Real(1e-12) * A[a])) scale = fabs(fld.fpg[a][c]) / fabs(S[a]);
-        const Real fp = fpre[(size_t)a * np + k];
-        const Real fd = scale * fp;
+        const Real fd = scale * fp[a];
         if (diag_fd) {
             diag_fd[(size_t)a * np + id] = fd;
-            diag_fpre[(size_t)a * np + id] = fp;
+            diag_fpre[(size_t)a * np + id] = fp[a];
         }
-        const Real acc = p.geff[a] + (fd + p.psign * p.vp * gradp[(size_t)a * np + k]) / p.mp;
-        v[a] += acc;
-        P[a] += (double)v[a];
-        const double L = p.len[a];
-        if (p.bc[2 * a] == BC_PERIODIC) {
-            if (P[a] >= L) P[a] -= L;
-            else if (P[a] < 0.0) {
-                P[a] += L;
-                if (P[a] >= L) P[a] = 0.0;
-            }
+        v[a] = parts.v[a][k] + (p.geff[a] + (fd + p.psign * p.vp * gp[a]) / p.mp);
+        P[a] = parts.P[a][k] + (double)v[a];
+        const Real on = parts.off[a][k] + v[a];
+        if (on > Real(1e-3) && on < Real(1) - Real(1e-3)) {
+            q[a] = idx[a];
+            off[a] = (Real)(P[a] - (double)idx[a]);
         } else {
-            if (P[a] < 0.0) {
-                P[a] = -P[a];
-                v[a] = -p.e * v[a];
-            } else if (P[a] >= L) {
-                P[a] = 2.0 * L - P[a];
-                v[a] = -p.e * v[a];
-            }
-            if (P[a] < 0.0) P[a] = 0.0;
-            if (P[a] >= L) P[a] = p.len_below[a];
-        }
-        if (!(P[a] >= 0.0 && P[a] < L)) {   // NaN position: keep the state finite and report
-            P[a] = 0.0;
-            flags |= HEALTH_DOMAIN;
+            stays = false;
         }
     }
-    if (flags) atomicOr(p.health, flags);
-    Real off[3];
-    const int nk = cell_and_offset<Real>(D, p.n, P, off);
+    if (!stays) {
+        unsigned flags = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const double L = p.len[a];
+            if (p.bc[2 * a] == BC_PERIODIC) {
+                if (P[a] >= L) P[a] -= L;
+                else if (P[a] < 0.0) {
+                    P[a] += L;
+                    if (P[a] >= L) P[a] = 0.0;
+                }
+            } else {
+                if (P[a] < 0.0) {
+                    P[a] = -P[a];
+                    v[a] = -p.e * v[a];
+                } else if (P[a] >= L) {
+                    P[a] = 2.0 * L - P[a];
+                    v[a] = -p.e * v[a];
+                }
+                if (P[a] < 0.0) P[a] = 0.0;
+                if (P[a] >= L) P[a] = p.len_below[a];
+            }
+            if (!(P[a] >= 0.0 && P[a] < L)) {   // NaN position: keep it finite, report
+                P[a] = 0.0;
+                flags |= HEALTH_DOMAIN;
+            }
+            int vq = (int)floor(P[a]);
+            vq = vq < 0 ? 0 : (vq >= p.n[a] ? p.n[a] - 1 : vq);
+            q[a] = vq;
+            off[a] = (Real)(P[a] - (double)vq);
+        }
+        if (flags) atomicOr(p.health, flags);
+    }
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        parts.P[a][k] = P[a];
-        parts.v[a][k] = v[a];
-        parts.off[a][k] = off[a];
+        out.P[a][k] = P[a];
+        out.v[a][k] = v[a];
+        out.off[a][k] = off[a];
     }
+    const int nk = q[0] + p.n[0] * (q[1] + p.n[1] * q[2]);
     key[k] = nk;
     atomicAdd(&counts[nk], 1);
 }
 
 template <int D, class Real>
-void launch_drag_integrate(const StepParams<Real> &p, Particles<Real> parts, const int *cell_start,
-                           Fields<Real> fld, const Real *fpre, const Real *gradp, int *key,
-                           int *counts, Real *diag_fpre, Real *diag_fd, int np, cudaStream_t st)
+void launch_drag_step(const StepParams<Real> &p, Particles<Real> parts, Particles<Real> out,
+                      CellList cells, Fields<Real> fld, int *key, int *counts, Real *diag_fpre,
+                      Real *diag_fd, int np, cudaStream_t st)
 {
     if (np == 0) return;
-    k_drag_integrate<D, Real><<<(np + 255) / 256, 256, 0, st>>>(p, parts, cell_start, fld, fpre,
-                                                                 gradp, key, counts, diag_fpre,
-                                                                 diag_fd, np);
+    k_drag_step<D, Real><<<(np + 255) / 256, 256, 0, st>>>(p, parts, out, cells, fld, key, counts,
+                                                           diag_fpre, diag_fd, np);
 }
 
 // Keys, offsets and counts of the current positions (used when a particle
@@ -262,16 +297,8 @@ void launch_cell_keys(const int *n, Particles<Real> parts, int *key, int *counts
 }
 
 // ---------------------------------------------------------------------------
-// Exclusive scan of the per-cell counts into cell_start[0..ncell] in three
-// passes: per-block scans (4096 cells per block) with block totals, a scan of
-// the block totals in one block, and the addition of block offsets.
+// Block-wide exclusive scan helper (warp shuffles, then the warp totals).
 // ---------------------------------------------------------------------------
-constexpr int kScanThreads = 512;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;
-
-int scan_block_count(int ncell) { return (ncell + kScanTile - 1) / kScanTile; }
-
 __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot, int *total)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -298,6 +325,80 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot, int *t
     __syncthreads();
     return warp_tot[warp] + inc - v;
 }
+
+// ---------------------------------------------------------------------------
+// One-launch scan of counts[0..ncell] into a two-level cell list.  Each block
+// scans one tile of 4096 counts and writes its total; the block that finishes
+// last (ticket counter, nothing waits) scans the tile totals and resets the
+// ticket for the next launch.
+// ---------------------------------------------------------------------------
+constexpr int kCellScanThreads = 512;
+constexpr int kCellScanItems = kCellTile / kCellScanThreads;   // 8
+
+__global__ void __launch_bounds__(kCellScanThreads)
+k_cell_scan(const int *__restrict__ counts, CellListOut out, int n)
+{
+    __shared__ int warp_tot[32];
+    __shared__ int total;
+    __shared__ bool last;
+    const int base = blockIdx.x * kCellTile + threadIdx.x * kCellScanItems;
+    int vals[kCellScanItems];
+    int sum = 0;
+#pragma unroll
+    for (int j = 0; j < kCellScanItems; ++j) {
+        const int e = base + j;
+        vals[j] = e < n ? counts[e] : 0;
+        sum += vals[j];
+    }
+    int run = block_exclusive_scan(sum, warp_tot, &total);
+#pragma unroll
+    for (int j = 0; j < kCellScanItems; ++j) {
+        const int e = base + j;
+        if (e < n) out.local[e] = run;
+        run += vals[j];
+    }
+    if (threadIdx.x == 0) {
+        out.tile_total[blockIdx.x] = total;
+        __threadfence();
+        const unsigned done = atomicAdd(out.ticket, 1u);
+        last = (done == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last block: exclusive scan of the tile totals into base[]
+    __threadfence();
+    const int nt = gridDim.x;
+    int carry = 0;
+    for (int b0 = 0; b0 < nt; b0 += blockDim.x) {
+        const int e = b0 + threadIdx.x;
+        const int v = e < nt ? __ldcg(out.tile_total + e) : 0;
+        const int ex = block_exclusive_scan(v, warp_tot, &total);
+        if (e < nt) out.base[e] = carry + ex;
+        carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out.base[nt] = carry;
+        *out.ticket = 0u;
+    }
+}
+
+void launch_cell_scan(const int *counts, CellListOut out, int ncell, cudaStream_t st)
+{
+    const int n = ncell + 1;
+    const int nt = cell_tiles(ncell);
+    k_cell_scan<<<nt, kCellScanThreads, 0, st>>>(counts, out, n);
+}
+
+// ---------------------------------------------------------------------------
+// Three-kernel scan into a plain cell_start array (per-block scans with block
+// totals, a scan of the block totals in one block, the block offsets added).
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+int scan_block_count(int ncell) { return (ncell + kScanTile - 1) / kScanTile; }
 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_tiles(const int *__restrict__ counts, int *__restrict__ out, int *__restrict__ block_sums,
@@ -358,33 +459,36 @@ void launch_scan(const int *counts, int *cell_start, int *block_sums, int ncell,
 // ---------------------------------------------------------------------------
 // Placement.  Each particle takes a slot in its cell's range by an atomic
 // decrement of the cell count (which also returns the counts to zero for the
-// next histogram).  The order inside a cell is then made canonical: each slot
-// ranks its particle among the cell's members by id and the payload is
-// gathered to cell_start + rank, giving the (cell, id) order.
+// next histogram) and records its id there.  The order inside a cell is then
+// made canonical: each slot ranks its particle among the cell's members by id
+// and the payload is gathered to begin(cell) + rank, the (cell, id) order.
 // ---------------------------------------------------------------------------
-__global__ void k_scatter(const int *__restrict__ key, int *__restrict__ counts,
-                          const int *__restrict__ cell_start, int *__restrict__ tmp, int np)
+__global__ void k_scatter(const int *__restrict__ key, const int *__restrict__ id,
+                          int *__restrict__ counts, CellList cells, int *__restrict__ slot,
+                          int *__restrict__ idslot, int np)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= np) return;
     const int c = key[k];
     const int old = atomicSub(&counts[c], 1);
-    tmp[cell_start[c] + old - 1] = k;
+    const int s = cells.begin(c) + old - 1;
+    slot[s] = k;
+    idslot[s] = id[k];
 }
 
 template <class Real>
-__global__ void k_gather(int dim, const int *__restrict__ key, const int *__restrict__ cell_start,
-                         const int *__restrict__ tmp, Particles<Real> src, Particles<Real> dst,
-                         int np)
+__global__ void k_gather(int dim, const int *__restrict__ key, CellList cells,
+                         const int *__restrict__ slot, const int *__restrict__ idslot,
+                         Particles<Real> src, Particles<Real> dst, int np)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= np) return;
-    const int k = tmp[s];
+    const int k = slot[s];
+    const int my = idslot[s];
     const int c = key[k];
-    const int my = src.id[k];
-    const int lo = cell_start[c], hi = cell_start[c + 1];
+    const int lo = cells.begin(c), hi = cells.begin(c + 1);
     int rank = 0;
-    for (int q = lo; q < hi; ++q) rank += (src.id[tmp[q]] < my) ? 1 : 0;
+    for (int q = lo; q < hi; ++q) rank += (idslot[q] < my) ? 1 : 0;
     const int d = lo + rank;
     for (int a = 0; a < dim; ++a) {
         dst.P[a][d] = src.P[a][k];
@@ -396,18 +500,16 @@ __global__ void k_gather(int dim, const int *__restrict__ key, const int *__rest
 }
 
 template <class Real>
-void launch_scatter_gather(int ncell, int dim, const int *key, int *counts, const int *cell_start,
-                           int *tmp, Particles<Real> src, Particles<Real> dst, int np,
-                           cudaStream_t st)
+void launch_place(int dim, const int *key, int *counts, CellList cells, int *slot, int *idslot,
+                  Particles<Real> src, Particles<Real> dst, int np, cudaStream_t st)
 {
-    (void)ncell;
     if (np == 0) return;
-    k_scatter<<<(np + 255) / 256, 256, 0, st>>>(key, counts, cell_start, tmp, np);
-    k_gather<Real><<<(np + 255) / 256, 256, 0, st>>>(dim, key, cell_start, tmp, src, dst, np);
+    k_scatter<<<(np + 255) / 256, 256, 0, st>>>(key, src.id, counts, cells, slot, idslot, np);
+    k_gather<Real><<<(np + 255) / 256, 256, 0, st>>>(dim, key, cells, slot, idslot, src, dst, np);
 }
 
 // ---------------------------------------------------------------------------
-// K4a: contact detection (section 2.2).  A pair collides when the centres are
+// Contact detection (section 2.2).  A pair collides when the centres are
 // closer than d and (P_i - P_j).(v_i - v_j) < 0; both tests in FP64 with
 // explicitly rounded multiplies and adds (no fused multiply-add) so that the
 // decisions are reproducible.  A pair is first tested in FP32 from the cell
@@ -419,9 +521,9 @@ void launch_scatter_gather(int ncell, int dim, const int *key, int *counts, cons
 // ---------------------------------------------------------------------------
 template <int D, class Real>
 __global__ void __launch_bounds__(256)
-k_detect(StepParams<Real> p, Particles<Real> parts, const int *__restrict__ cell_start,
-         int *__restrict__ best_out, int *__restrict__ wall_out, long long *pairs,
-         unsigned long long *npairs, long long pair_cap, int np)
+k_detect(StepParams<Real> p, Particles<Real> parts, CellList cells, int *__restrict__ best_out,
+         int *__restrict__ wall_out, long long *pairs, unsigned long long *npairs,
+         long long pair_cap, int np)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
@@ -461,7 +563,7 @@ k_detect(StepParams<Real> p, Particles<Real> parts, const int *__restrict__ cell
         }
         if (skip) continue;
         const int cc = q[0] + p.n[0] * (q[1] + p.n[1] * q[2]);
-        const int j0 = cell_start[cc], j1 = cell_start[cc + 1];
+        const int j0 = cells.begin(cc), j1 = cells.begin(cc + 1);
         for (int j = j0; j < j1; ++j) {
             if (j == i) continue;
             // coarse test: P_i - P_j = (o_i - o_j) - shift, minimum image on periodic axes
@@ -534,18 +636,18 @@ k_detect(StepParams<Real> p, Particles<Real> parts, const int *__restrict__ cell
 }
 
 template <int D, class Real>
-void launch_detect(const StepParams<Real> &p, Particles<Real> parts, const int *cell_start,
-                   int *best, int *wall, long long *pairs, unsigned long long *npairs,
-                   long long pair_cap, int np, cudaStream_t st)
+void launch_detect(const StepParams<Real> &p, Particles<Real> parts, CellList cells, int *best,
+                   int *wall, long long *pairs, unsigned long long *npairs, long long pair_cap,
+                   int np, cudaStream_t st)
 {
     if (np == 0) return;
-    k_detect<D, Real><<<(np + 255) / 256, 256, 0, st>>>(p, parts, cell_start, best, wall, pairs,
-                                                        npairs, pair_cap, np);
+    k_detect<D, Real><<<(np + 255) / 256, 256, 0, st>>>(p, parts, cells, best, wall, pairs, npairs,
+                                                        pair_cap, np);
 }
 
 // ---------------------------------------------------------------------------
-// K4b: resolution.  A pair collides when each particle chose the other; the
-// one with the smaller id applies Eq. 17-18 (equal masses) to both from the
+// Resolution.  A pair collides when each particle chose the other; the one
+// with the smaller id applies Eq. 17-18 (equal masses) to both from the
 // pre-collision velocities.  Particles without a mutual pair reflect off the
 // walls they touch (Eq. 17 with an infinitely heavy wall at rest:
 // v_n -> -e v_n).
@@ -597,13 +699,11 @@ void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int 
 
 // ---------------------------------------------------------------------------
 #define LBDPS_INST_P(D, R)                                                                          \
-    template void launch_drag_pre<D, R>(const StepParams<R> &, Particles<R>, const int *,         \
-                                        Fields<R>, R *, R *, int, cudaStream_t);                   \
-    template void launch_drag_integrate<D, R>(const StepParams<R> &, Particles<R>, const int *,   \
-                                              Fields<R>, const R *, const R *, int *, int *, R *, \
-                                              R *, int, cudaStream_t);                             \
-    template void launch_detect<D, R>(const StepParams<R> &, Particles<R>, const int *, int *,     \
-                                      int *, long long *, unsigned long long *, long long, int,    \
+    template void launch_drag_step<D, R>(const StepParams<R> &, Particles<R>, Particles<R>,        \
+                                         CellList, Fields<R>, int *, int *, R *, R *, int,          \
+                                         cudaStream_t);                                             \
+    template void launch_detect<D, R>(const StepParams<R> &, Particles<R>, CellList, int *, int *,  \
+                                      long long *, unsigned long long *, long long, int,           \
                                       cudaStream_t);                                               \
     template void launch_resolve<D, R>(const StepParams<R> &, Particles<R>, const int *,           \
                                        const int *, int, cudaStream_t);                            \
@@ -615,10 +715,9 @@ LBDPS_INST_P(2, float)
 LBDPS_INST_P(3, double)
 LBDPS_INST_P(3, float)
 
-template void launch_scatter_gather<double>(int, int, const int *, int *, const int *, int *,
-                                            Particles<double>, Particles<double>, int,
-                                            cudaStream_t);
-template void launch_scatter_gather<float>(int, int, const int *, int *, const int *, int *,
-                                           Particles<float>, Particles<float>, int, cudaStream_t);
+template void launch_place<double>(int, const int *, int *, CellList, int *, int *,
+                                   Particles<double>, Particles<double>, int, cudaStream_t);
+template void launch_place<float>(int, const int *, int *, CellList, int *, int *,
+                                  Particles<float>, Particles<float>, int, cudaStream_t);
 
 }  // namespace lbdpsk

@@ -30,7 +30,7 @@ VECTOR_FIELDS = {"u", "fpg", "vs", "uact"}
 PDIAG_FPRE, PDIAG_FD, PDIAG_BEST, PDIAG_WALL, PDIAG_CELL, PDIAG_ORDER = 0, 1, 2, 3, 4, 5
 CONST_NAMES = ["tau", "nu", "mu", "rho_s", "d", "r", "vp", "mp", "e", "g_eff_x", "g_eff_y",
                "g_eff_z", "fb_x", "fb_y", "fb_z", "u0_x", "u0_y", "u0_z", "cs_smag"]
-KERNEL_CLASSES = ["collide_stream", "drag_pre", "drag_integrate", "sort", "collide_particles"]
+KERNEL_CLASSES = ["collide_stream", "drag", "sort", "collide_particles"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _i64p = ctypes.POINTER(ctypes.c_int64)
