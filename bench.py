@@ -49,6 +49,12 @@ def parse():
                     help="only build the bed and run this many steps (for ncu captures); "
                          "no timing, no JSON line")
     ap.add_argument("--workload", default="riser2d", choices=["riser2d", "riser3d"])
+    ap.add_argument("--serving", action="store_true",
+                    help="serving benchmark: Poisson stream of independent beds")
+    ap.add_argument("--requests", type=int, default=96)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--max-active", type=int, default=128)
+    ap.add_argument("--steps-per-tick", type=int, default=32)
     return ap.parse_args()
 
 
@@ -221,6 +227,10 @@ def main():
     if args.impl == "reference":
         reference_main(args, rank, world)
         return
+    if args.serving:
+        if rank == 0:
+            serving_main(args)
+        return
 
     import torch
     import __graft_entry__ as ge
@@ -348,6 +358,116 @@ def main():
     bed.close()
     if dist:
         dist.destroy_process_group()
+
+
+
+# ------------------------------------------------------------------ serving
+
+def serving_requests(count, rate, seed=1303004):
+    """Seeded stream of bed requests: Poisson arrivals at `rate` per second;
+    bubbling or riser with p = 1/2; nx log-uniform in [64, 512] and ny in
+    [128, 2048], both multiples of 32; particle count log-uniform in
+    [1e3, 5e5], capped at a 2D area fraction of 0.25 in the particle region;
+    step count log-uniform in [100, 5000]; FP16 or FP32 storage with p = 1/2."""
+    import numpy as np
+    from paper_1303_2653_gb300 import workloads as W
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, count))
+    reqs = []
+    lu = lambda lo, hi: float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+    for i in range(count):
+        kind = "bubbling" if rng.random() < 0.5 else "riser"
+        nx = max(64, int(round(lu(64, 512) / 32)) * 32)
+        ny = max(128, int(round(lu(128, 2048) / 32)) * 32)
+        n = int(lu(1e3, 5e5))
+        steps = int(lu(100, 5000))
+        storage = W.STORE_F16 if rng.random() < 0.5 else W.STORE_F32
+        if kind == "riser":
+            h = 1.322e-4
+            area = math.pi * (0.5 * 54e-6 / h) ** 2
+            n = min(n, int(0.25 * nx * ny / area))
+            w = W.riser2d(nx=nx, ny=ny, n_particles=n, seed=1303100 + i, storage=storage, h=h,
+                          steps=steps)
+        else:
+            area = math.pi * (0.5 * 0.5e-3 / 2e-3) ** 2
+            n = min(n, int(0.25 * 0.4 * nx * ny / area))
+            w = W.bubbling2d(nx=nx, ny=ny, n_particles=n, seed=1303100 + i, storage=storage,
+                             steps=steps)
+        reqs.append((float(t[i]), w))
+    return reqs
+
+
+def serving_main(args):
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1303_2653_gb300 import lbdps as L
+    from paper_1303_2653_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    reqs = serving_requests(args.requests, args.rate)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.5 * free)
+    work = sum(w.ncell * w.steps for _, w in reqs)
+
+    # served: continuous batching, mixed storage
+    server = L.Server(hbm_budget=budget, max_active=args.max_active,
+                      steps_per_tick=args.steps_per_tick)
+    ids, done, lat = {}, {}, {}
+    nxt = 0
+    t0 = time.perf_counter()
+    while len(done) < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt][0] <= now:
+            ids[server.submit(reqs[nxt][1], reqs[nxt][1].steps)] = nxt
+            nxt += 1
+        for r in server.poll(wait_s=0.0005):
+            i = ids[r["id"]]
+            done[i] = r
+            lat[i] = (time.perf_counter() - t0) - reqs[i][0]
+    makespan = time.perf_counter() - t0 - reqs[0][0]
+    server.close()
+    served_lat = np.array([lat[i] for i in range(len(reqs))])
+    eps_served = np.array([done[i]["mean_eps_g"] for i in range(len(reqs))])
+    bad = sum(1 for i in range(len(reqs)) if done[i]["status"] != 0)
+
+    # baseline: the same requests one by one in plain FP32 (FIFO in arrival order)
+    t_free, base_lat, eps_fp32 = 0.0, [], []
+    t_start = time.perf_counter()
+    for arrival, w in reqs:
+        b = L.Bed(w, storage=W.STORE_F32)
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        b.step(w.steps)
+        b.sync()
+        dt = time.perf_counter() - s0
+        eps_fp32.append(b.stats()["mean_eps_g"])
+        b.close()
+        begin = max(t_free, arrival)
+        t_free = begin + dt
+        base_lat.append(t_free - arrival)
+    base_lat = np.array(base_lat)
+    base_makespan = t_free - reqs[0][0]
+    eps_fp32 = np.array(eps_fp32)
+    rel = np.abs(eps_served - eps_fp32) / eps_fp32
+    solid_rel = np.abs(eps_served - eps_fp32) / np.maximum(1 - eps_fp32, 1e-12)
+    line = {"metric": "served p50/p99 time-to-K-steps and aggregate MLUPS", "unit": "s / MLUPS",
+            "requests": len(reqs), "rate_per_s": args.rate, "cell_updates": work,
+            "data": "synthetic",
+            "served": {"p50_s": float(np.percentile(served_lat, 50)),
+                       "p99_s": float(np.percentile(served_lat, 99)),
+                       "aggregate_mlups": work / makespan / 1e6, "makespan_s": makespan,
+                       "failed": bad, "budget_bytes": budget, "max_active": args.max_active,
+                       "steps_per_tick": args.steps_per_tick,
+                       "fp16_requests": sum(1 for _, w in reqs if w.storage == W.STORE_F16)},
+            "one_by_one_fp32": {"p50_s": float(np.percentile(base_lat, 50)),
+                                "p99_s": float(np.percentile(base_lat, 99)),
+                                "aggregate_mlups": work / base_makespan / 1e6,
+                                "makespan_s": base_makespan},
+            "mean_voidage_rel_err": {"max": float(rel.max()), "mean": float(rel.mean()),
+                                     "max_rel_to_solid_fraction": float(solid_rel.max())}}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -140,8 +140,10 @@ typedef struct {
     double mass;                 /* sum of gas populations                          */
     double gas_momentum[3];      /* sum_i c_i f_i over the lattice                  */
     double particle_momentum[3]; /* sum m_p v                                       */
-    double mean_eps_g;           /* lattice-mean gas voidage of the last step       */
-    double mean_slip;            /* particle-weighted mean |u_act - v_s| (diagnostics) */
+    double mean_eps_g;           /* lattice-mean gas voidage eps_g (Eq. 10-11) of the
+                                    current particle positions                        */
+    double mean_slip;            /* particle-weighted mean |u_act - v_s| of the last
+                                    step (needs diagnostics, else NaN)                */
     int64_t steps;               /* steps taken so far                              */
     int health;                  /* bitmask: 1 diverged, 2 domain, 4 capacity       */
 } lbdps_stats_t;
@@ -224,6 +226,58 @@ int lbdps_shape(lbdps_t *h, int *dim, int *q, int64_t *ncell, int64_t *nparticle
  * handle of the same shape and storage; the continuation is bit-identical. */
 int lbdps_save(lbdps_t *h, void *buf, size_t cap, size_t *used);
 int lbdps_load(lbdps_t *h, const void *buf, size_t size);
+
+/* Exact device-memory footprint, in bytes, of the bed lbdps_create would
+ * build from this description (all buffers, rounded to 256 B each).  No
+ * device work; the same validation as create except the overlap test. */
+int lbdps_memory_estimate(const lbdps_lattice_desc *lattice, const lbdps_particle_desc *particles,
+                          const lbdps_params *params, size_t *bytes);
+
+/* Record the CUDA event `event` (a cudaEvent_t) on the handle's stream,
+ * after all work issued so far. */
+int lbdps_record_event(lbdps_t *h, void *event);
+
+/* ---- serving: continuous batching of independent beds ----------------
+ * Not in the paper: a request loop for many independent beds of different
+ * sizes.  Requests queue in FIFO order; the head is admitted when its exact
+ * footprint (lbdps_memory_estimate) fits in the HBM budget and fewer than
+ * max_active beds are resident.  Every resident bed keeps its populations
+ * and particles on the device, on a stream of its own; each poll advances
+ * every resident bed by one tick (steps_per_tick steps, each a replay of the
+ * bed's captured step graph), so the beds' work overlaps on the GPU.  A bed
+ * that reached its step count is harvested: its statistics and times are
+ * reported and its memory is released (or kept for lbdps_server_take), which
+ * admits the next requests.  A bed's results are identical to running it
+ * alone.  Times are seconds on the host's steady clock since server
+ * creation.  The server is not thread safe. */
+typedef struct lbdps_server lbdps_server_t;
+
+typedef struct {
+    uint64_t id;          /* request id from lbdps_server_submit                     */
+    int status;           /* LBDPS_OK, or the error that ended the request           */
+    int64_t steps;        /* steps taken                                             */
+    double cells;         /* lattice cells                                           */
+    double t_submit, t_admit, t_done;   /* seconds                                  */
+    lbdps_stats_t stats;  /* FP64 statistics at completion                           */
+} lbdps_done_t;
+
+int lbdps_server_create(size_t hbm_budget, int max_active, int steps_per_tick,
+                        lbdps_server_t **out);
+/* Queue a bed (descriptions and arrays are copied).  keep = 1 keeps the
+ * finished handle for lbdps_server_take.  LBDPS_ERR_CAPACITY if the bed can
+ * never fit the budget. */
+int lbdps_server_submit(lbdps_server_t *s, const lbdps_lattice_desc *lattice,
+                        const lbdps_particle_desc *particles, const lbdps_params *params,
+                        int64_t nsteps, int keep, uint64_t *req_id);
+/* Admit, advance one tick and harvest, repeating for up to wait_s seconds
+ * until at least one request completes; completion records are written to
+ * out (cap entries at most), their number to *ndone. */
+int lbdps_server_poll(lbdps_server_t *s, double wait_s, lbdps_done_t *out, int cap, int *ndone);
+/* Queue length, resident beds and bytes of the budget in use. */
+int lbdps_server_load(lbdps_server_t *s, int *queued, int *active, size_t *used);
+/* Hand over a finished kept bed; the caller then owns the handle (lbdps_destroy). */
+int lbdps_server_take(lbdps_server_t *s, uint64_t req_id, lbdps_t **out);
+void lbdps_server_destroy(lbdps_server_t *s);
 
 /* Cell binning without device allocation.  The paper has no counterpart:
  * this is a service for callers that must not allocate GPU memory while they

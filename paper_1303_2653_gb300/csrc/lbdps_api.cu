@@ -86,11 +86,17 @@ struct DeviceAlloc {
     void (*release)(void *, void *) = nullptr;
     void *ctx = nullptr;
     std::vector<void *> owned;
+    bool count_only = false;     // only add up the sizes (memory estimate)
+    size_t counted = 0;
 
     void *get(size_t bytes)
     {
         bytes = (bytes + 255) & ~size_t(255);
         if (bytes == 0) bytes = 256;
+        if (count_only) {
+            counted += bytes;
+            return (void *)(uintptr_t)256;   // never dereferenced
+        }
         void *p = nullptr;
         if (alloc) {
             p = alloc(bytes, ctx);
@@ -103,6 +109,7 @@ struct DeviceAlloc {
     }
     void release_all()
     {
+        if (count_only) return;
         for (void *p : owned) {
             if (release) release(p, ctx);
             else cudaFree(p);
@@ -675,8 +682,13 @@ template <class L, class Real, class S> struct EngineT : Engine {
             out->gas_momentum[a] = a < D ? v[1 + a] : 0.0;
             out->particle_momentum[a] = a < D ? v[4 + a] : 0.0;
         }
-        out->mean_eps_g = NAN;
         out->mean_slip = NAN;
+        launch_reduce_voidage<Real>(H->ncell, cells(cur), sp.tab.eps_g, H->ntab, red_partials,
+                                    red_out, H->stream);
+        CHECK_LAUNCH();
+        CU(cudaMemcpyAsync(v, red_out, sizeof(double), cudaMemcpyDeviceToHost, H->stream));
+        CU(cudaStreamSynchronize(H->stream));
+        out->mean_eps_g = v[0] / (double)H->ncell;
         if (H->prm.diagnostics && H->steps > 0) {
             const Real *ua[3] = {fld.uact[0], fld.uact[1], D > 2 ? fld.uact[2] : nullptr};
             const Real *va[3] = {fld.vs[0], fld.vs[1], D > 2 ? fld.vs[2] : nullptr};
@@ -685,7 +697,6 @@ template <class L, class Real, class S> struct EngineT : Engine {
             CHECK_LAUNCH();
             CU(cudaMemcpyAsync(v, red_out, sizeof(double) * 3, cudaMemcpyDeviceToHost, H->stream));
             CU(cudaStreamSynchronize(H->stream));
-            out->mean_eps_g = v[0] / (double)H->ncell;
             out->mean_slip = v[2] > 0 ? v[1] / v[2] : 0.0;
         }
         out->steps = H->steps;
@@ -919,11 +930,14 @@ struct CkptHeader {
 // ===========================================================================
 extern "C" {
 
-int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
-                 const lbdps_params *prm, lbdps_t **out)
+}  // extern "C"
+
+// Validation, derived constants and lattice-unit particles of a description
+// (no device work).  Shared by lbdps_create and lbdps_memory_estimate.
+static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
+                       const lbdps_params *prm, bool check_overlap, std::unique_ptr<lbdps> &hout,
+                       std::vector<double> &pos, std::vector<double> &vel)
 {
-    if (!out) return fail(LBDPS_ERR_INVALID, "out is NULL");
-    *out = nullptr;
     if (!lat || !par || !prm) return fail(LBDPS_ERR_INVALID, "NULL description");
     const int D = lat->dim;
     if (D != 2 && D != 3) return fail(LBDPS_ERR_INVALID, "dim must be 2 or 3");
@@ -1010,14 +1024,48 @@ int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
         }
     }
     // particles in lattice units
-    std::vector<double> pos((size_t)h->np * D), vel((size_t)h->np * D);
+    pos.assign((size_t)h->np * D, 0.0);
+    vel.assign((size_t)h->np * D, 0.0);
     const double vscale = lat->dt / lat->h;
     for (size_t i = 0; i < pos.size(); ++i) {
         pos[i] = par->pos[i] / lat->h;
         vel[i] = par->vel[i] * vscale;
     }
-    int rc = validate_positions(h.get(), pos.data(), true);
+    int rc = validate_positions(h.get(), pos.data(), check_overlap);
     if (rc) return rc;
+    hout = std::move(h);
+    return LBDPS_OK;
+}
+
+extern "C" {
+
+int lbdps_memory_estimate(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
+                          const lbdps_params *prm, size_t *bytes)
+{
+    if (!bytes) return fail(LBDPS_ERR_INVALID, "bytes is NULL");
+    std::unique_ptr<lbdps> h;
+    std::vector<double> pos, vel;
+    int rc = prepare_bed(lat, par, prm, false, h, pos, vel);
+    if (rc) return rc;
+    h->mem.count_only = true;
+    h->eng.reset(h->dim == 2 ? make_engine_l<D2Q9>(h.get()) : make_engine_l<D3Q19>(h.get()));
+    if (!h->eng) return fail(LBDPS_ERR_OOM, "engine allocation failed");
+    rc = h->eng->allocate(h->mem);
+    if (rc) return rc;
+    *bytes = h->mem.counted;
+    return LBDPS_OK;
+}
+
+int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
+                 const lbdps_params *prm, lbdps_t **out)
+{
+    if (!out) return fail(LBDPS_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    std::unique_ptr<lbdps> h;
+    std::vector<double> pos, vel;
+    int rc = prepare_bed(lat, par, prm, true, h, pos, vel);
+    if (rc) return rc;
+    const int D = h->dim;
 
     if (prm->stream) {
         h->stream = (cudaStream_t)prm->stream;
@@ -1098,6 +1146,13 @@ int lbdps_step_profiled(lbdps_t *h, int64_t nsteps, double *kernel_ms, int cap, 
     for (int e = 0; e <= kClasses; ++e) cudaEventDestroy(ev[e]);
     for (int c = 0; c < kClasses && c < cap; ++c) kernel_ms[c] = acc[c];
     return rc;
+}
+
+int lbdps_record_event(lbdps_t *h, void *event)
+{
+    if (!h || !event) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    CU(cudaEventRecord((cudaEvent_t)event, h->stream));
+    return LBDPS_OK;
 }
 
 int lbdps_sync(lbdps_t *h)

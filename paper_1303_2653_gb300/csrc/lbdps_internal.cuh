@@ -245,6 +245,10 @@ void launch_reduce_bed(int ncell, int dim, const Real *eps_g, const int *ntot,
                        const Real *const *uact, const Real *const *vs, double *partials,
                        double *out, cudaStream_t st);
 
+template <class Real>
+void launch_reduce_voidage(int ncell, CellList cells, const Real *eps_g_tab, int ntab,
+                           double *partials, double *out, cudaStream_t st);
+
 int reduce_block_count(int n);
 
 }  // namespace lbdpsk

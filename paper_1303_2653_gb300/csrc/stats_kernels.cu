@@ -108,6 +108,33 @@ void launch_reduce_bed(int ncell, int dim, const Real *eps_g, const int *ntot,
     k_reduce_final<<<1, 32, 0, st>>>(partials, nb, 3, out);
 }
 
+// lattice mean of eps_g for the current particle positions: [0] sum over cells
+template <class Real>
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce_voidage(int ncell, CellList cells, const Real *eps_g_tab, int ntab, double *partials)
+{
+    double acc[1] = {0.0};
+    const int stride = gridDim.x * blockDim.x;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < ncell; x += stride) {
+        const int n = cells.begin(x + 1) - cells.begin(x);
+        acc[0] += (double)eps_g_tab[n < ntab ? n : ntab - 1];
+    }
+    block_sum_write<1>(acc, partials);
+}
+
+template <class Real>
+void launch_reduce_voidage(int ncell, CellList cells, const Real *eps_g_tab, int ntab,
+                           double *partials, double *out, cudaStream_t st)
+{
+    const int nb = reduce_block_count(ncell);
+    k_reduce_voidage<Real><<<nb, kRedThreads, 0, st>>>(ncell, cells, eps_g_tab, ntab, partials);
+    k_reduce_final<<<1, 32, 0, st>>>(partials, nb, 1, out);
+}
+template void launch_reduce_voidage<double>(int, CellList, const double *, int, double *, double *,
+                                            cudaStream_t);
+template void launch_reduce_voidage<float>(int, CellList, const float *, int, double *, double *,
+                                           cudaStream_t);
+
 #define LBDPS_INST_RED(L, R, S)                                                                   \
     template void launch_reduce_state<L, R, S>(int, const S *, Particles<R>, double, int,         \
                                                double *, double *, cudaStream_t);

@@ -67,6 +67,12 @@ class Stats(ctypes.Structure):
                 ("health", ctypes.c_int)]
 
 
+class DoneRec(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int), ("steps", ctypes.c_int64),
+                ("cells", ctypes.c_double), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("stats", Stats)]
+
+
 class LbdpsError(RuntimeError):
     def __init__(self, code: int, what: str, detail: str):
         super().__init__(f"{what}: {detail} (status {code})")
@@ -105,6 +111,17 @@ def lib():
             "lbdps_shape": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), _i64p, _i64p], i),
             "lbdps_save": ([vp, vp, sz, ctypes.POINTER(sz)], i),
             "lbdps_load": ([vp, vp, sz], i),
+            "lbdps_memory_estimate": ([ctypes.POINTER(LatticeDesc), ctypes.POINTER(ParticleDesc),
+                                       ctypes.POINTER(Params), ctypes.POINTER(sz)], i),
+            "lbdps_record_event": ([vp, vp], i),
+            "lbdps_server_create": ([sz, i, i, ctypes.POINTER(vp)], i),
+            "lbdps_server_submit": ([vp, ctypes.POINTER(LatticeDesc), ctypes.POINTER(ParticleDesc),
+                                     ctypes.POINTER(Params), i64, i, ctypes.POINTER(ctypes.c_uint64)], i),
+            "lbdps_server_poll": ([vp, ctypes.c_double, ctypes.POINTER(DoneRec), i,
+                                   ctypes.POINTER(i)], i),
+            "lbdps_server_load": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz)], i),
+            "lbdps_server_take": ([vp, ctypes.c_uint64, ctypes.POINTER(vp)], i),
+            "lbdps_server_destroy": ([vp], None),
             "lbdps_bin_sort_noalloc": ([i, ctypes.POINTER(i), i64, ctypes.POINTER(vp), vp, vp, vp], i),
             "lbdps_strerror": ([i], ctypes.c_char_p),
             "lbdps_last_error": ([], ctypes.c_char_p),
@@ -143,6 +160,56 @@ def bin_sort_noalloc(dim: int, n, pos_ptrs, cell_start_ptr: int, order_ptr: int,
            "lbdps_bin_sort_noalloc")
 
 
+def describe(w, storage: Optional[int] = None, diagnostics: bool = False,
+             use_graph: bool = True, check_every: int = 0):
+    """C descriptions of a workload; returns (lattice, particles, params,
+    keepalive arrays).  No allocator and no stream are set."""
+    keep = []
+    lat = LatticeDesc()
+    lat.dim = w.dim
+    for a in range(3):
+        lat.n[a] = int(w.n[a]) if a < len(w.n) else 1
+    for f in range(6):
+        lat.bc[f] = int(w.bc[f])
+    lat.h, lat.dt = float(w.h), float(w.dt)
+    if w.inlet_u is not None:
+        iu = np.ascontiguousarray(w.inlet_u, dtype=np.float64)
+        keep.append(iu)
+        lat.inlet_u = _ptr(iu)
+    if w.wall_u is not None:
+        for f in range(6):
+            for a in range(3):
+                lat.wall_u[f][a] = float(w.wall_u[f][a])
+    pos = np.ascontiguousarray(w.pos, dtype=np.float64)
+    vel = np.ascontiguousarray(w.vel, dtype=np.float64)
+    keep += [pos, vel]
+    par = ParticleDesc(pos.shape[0], float(w.d_p), float(w.rho_s), float(w.e), _ptr(pos),
+                       _ptr(vel))
+    prm = Params()
+    prm.rho_g, prm.mu_g = float(w.rho_g), float(w.mu_g)
+    for a in range(3):
+        prm.g[a] = float(w.g[a])
+        prm.body_accel[a] = float(w.body_accel[a])
+        prm.u0[a] = float(w.u0[a])
+    prm.cs_smag = float(w.cs_smag)
+    prm.superficial_mode = int(w.superficial_mode)
+    prm.pressure_plus = int(w.pressure_plus)
+    prm.storage = int(w.storage if storage is None else storage)
+    prm.check_every = int(check_every)
+    prm.diagnostics = int(bool(diagnostics))
+    prm.use_graph = int(bool(use_graph))
+    return lat, par, prm, keep
+
+
+def memory_estimate(w, storage: Optional[int] = None, diagnostics: bool = False) -> int:
+    """Exact device bytes of the bed lbdps_create would build."""
+    lat, par, prm, keep = describe(w, storage, diagnostics)
+    out = ctypes.c_size_t()
+    _check(lib().lbdps_memory_estimate(ctypes.byref(lat), ctypes.byref(par), ctypes.byref(prm),
+                                       ctypes.byref(out)), "lbdps_memory_estimate")
+    return out.value
+
+
 class Bed:
     """One bed advanced by the CUDA library.
 
@@ -159,39 +226,7 @@ class Bed:
         self._torch = torch
         self.dim = w.dim
         self.stream = torch.cuda.Stream()
-        self._keep = []
-        lat = LatticeDesc()
-        lat.dim = w.dim
-        for a in range(3):
-            lat.n[a] = int(w.n[a]) if a < len(w.n) else 1
-        for f in range(6):
-            lat.bc[f] = int(w.bc[f])
-        lat.h, lat.dt = float(w.h), float(w.dt)
-        if w.inlet_u is not None:
-            iu = np.ascontiguousarray(w.inlet_u, dtype=np.float64)
-            self._keep.append(iu)
-            lat.inlet_u = _ptr(iu)
-        if w.wall_u is not None:
-            for f in range(6):
-                for a in range(3):
-                    lat.wall_u[f][a] = float(w.wall_u[f][a])
-        pos = np.ascontiguousarray(w.pos, dtype=np.float64)
-        vel = np.ascontiguousarray(w.vel, dtype=np.float64)
-        par = ParticleDesc(pos.shape[0], float(w.d_p), float(w.rho_s), float(w.e), _ptr(pos),
-                           _ptr(vel))
-        prm = Params()
-        prm.rho_g, prm.mu_g = float(w.rho_g), float(w.mu_g)
-        for a in range(3):
-            prm.g[a] = float(w.g[a])
-            prm.body_accel[a] = float(w.body_accel[a])
-            prm.u0[a] = float(w.u0[a])
-        prm.cs_smag = float(w.cs_smag)
-        prm.superficial_mode = int(w.superficial_mode)
-        prm.pressure_plus = int(w.pressure_plus)
-        prm.storage = int(w.storage if storage is None else storage)
-        prm.check_every = int(check_every)
-        prm.diagnostics = int(bool(diagnostics))
-        prm.use_graph = int(bool(use_graph))
+        lat, par, prm, self._keep = describe(w, storage, diagnostics, use_graph, check_every)
         prm.stream = ctypes.c_void_p(self.stream.cuda_stream)
         if torch_memory:
             stream = self.stream
@@ -221,6 +256,23 @@ class Bed:
         self.n = tuple(int(w.n[a]) for a in range(w.dim))
         self.storage = prm.storage
         self.diagnostics = bool(diagnostics)
+
+    @classmethod
+    def adopt(cls, handle: ctypes.c_void_p, w, diagnostics: bool = False) -> "Bed":
+        """Wrap a handle created elsewhere (for example taken from a Server)."""
+        self = cls.__new__(cls)
+        self._h = handle
+        self.dim = w.dim
+        self.stream = None
+        self._keep = []
+        d, q, nc, npart = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().lbdps_shape(self._h, ctypes.byref(d), ctypes.byref(q), ctypes.byref(nc),
+                                 ctypes.byref(npart)), "lbdps_shape")
+        self.q, self.ncell, self.np = q.value, nc.value, npart.value
+        self.n = tuple(int(w.n[a]) for a in range(w.dim))
+        self.storage = None
+        self.diagnostics = diagnostics
+        return self
 
     # -- life cycle ---------------------------------------------------------
     def close(self):
@@ -342,3 +394,72 @@ class Bed:
     def load(self, data: bytes):
         buf = ctypes.create_string_buffer(data, len(data))
         _check(lib().lbdps_load(self._h, buf, len(data)), "lbdps_load")
+
+
+class Server:
+    """Continuous batching of independent beds (see lbdps_server_* in
+    include/lbdps.h).  Beds get their own CUDA streams and device memory from
+    cudaMalloc inside the library; the budget bounds their total footprint."""
+
+    def __init__(self, hbm_budget: int, max_active: int = 64, steps_per_tick: int = 16):
+        h = ctypes.c_void_p()
+        _check(lib().lbdps_server_create(int(hbm_budget), int(max_active), int(steps_per_tick),
+                                         ctypes.byref(h)), "lbdps_server_create")
+        self._h = h
+        self._workloads = {}
+        self._callbacks = []
+
+    def submit(self, w, steps: int, storage: Optional[int] = None, keep: bool = False,
+               alloc=None, free=None) -> int:
+        """Queue a bed for `steps` steps.  `alloc(nbytes) -> int|None` and
+        `free(ptr)` optionally replace cudaMalloc/cudaFree for this bed."""
+        lat, par, prm, keepalive = describe(w, storage)
+        if alloc is not None:
+            cb_a = ALLOC_FN(lambda n, ctx: alloc(n))
+            cb_f = FREE_FN(lambda ptr, ctx: free(ptr) if free else None)
+            prm.alloc, prm.free = cb_a, cb_f
+            self._callbacks.append((cb_a, cb_f))
+        rid = ctypes.c_uint64()
+        _check(lib().lbdps_server_submit(self._h, ctypes.byref(lat), ctypes.byref(par),
+                                         ctypes.byref(prm), int(steps), int(bool(keep)),
+                                         ctypes.byref(rid)), "lbdps_server_submit")
+        if keep:
+            self._workloads[rid.value] = w
+        return rid.value
+
+    def poll(self, wait_s: float = 0.0, cap: int = 256):
+        buf = (DoneRec * cap)()
+        n = ctypes.c_int()
+        _check(lib().lbdps_server_poll(self._h, float(wait_s), buf, cap, ctypes.byref(n)),
+               "lbdps_server_poll")
+        out = []
+        for r in buf[: n.value]:
+            out.append({"id": r.id, "status": r.status, "steps": r.steps, "cells": r.cells,
+                        "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done,
+                        "mass": r.stats.mass, "mean_eps_g": r.stats.mean_eps_g,
+                        "health": r.stats.health})
+        return out
+
+    def load(self):
+        q, a, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _check(lib().lbdps_server_load(self._h, ctypes.byref(q), ctypes.byref(a), ctypes.byref(u)),
+               "lbdps_server_load")
+        return q.value, a.value, u.value
+
+    def take(self, req_id: int) -> Bed:
+        h = ctypes.c_void_p()
+        _check(lib().lbdps_server_take(self._h, ctypes.c_uint64(req_id), ctypes.byref(h)),
+               "lbdps_server_take")
+        return Bed.adopt(h, self._workloads.pop(req_id))
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h and h.value:
+            lib().lbdps_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -163,7 +163,7 @@ def bubbling2d(nx=64, ny=128, n_particles=2000, seed=SEED_BASE + 0, storage=STOR
 
 def riser2d(nx=256, ny=2048, n_particles=200000, seed=SEED_BASE + 1, storage=STORE_F32,
             steps=10000, cs_smag=0.0, solid_fraction=0.05, u_gas=1.5, u_lat=0.0338,
-            sigma_v=0.1) -> Workload:
+            sigma_v=0.1, h=None) -> Workload:
     """Periodic riser section in the shape of the paper's §3.2 case (Table 2).
 
     54 um, 930 kg/m^3 particles at a mean 2D area fraction ``solid_fraction``
@@ -171,12 +171,14 @@ def riser2d(nx=256, ny=2048, n_particles=200000, seed=SEED_BASE + 1, storage=STO
     deviation ``sigma_v`` per component, gas initially at ``u_gas`` upward,
     time step from the lattice inlet velocity of Table 2, walls at the sides,
     periodic vertically, and an upward gas body acceleration that carries the
-    particles' effective weight.
+    particles' effective weight.  With ``h`` given the cell size is fixed and
+    the solid fraction follows from ``n_particles``.
     """
     d_p = 54e-6
     r = 0.5 * d_p
     rho_s, rho_g, mu_g, g = 930.0, 1.1795, 1.8872e-5, 9.81
-    h = math.sqrt(n_particles * math.pi * r * r / (nx * ny * solid_fraction))
+    if h is None:   # the cell size that gives the requested mean solid fraction
+        h = math.sqrt(n_particles * math.pi * r * r / (nx * ny * solid_fraction))
     dt = u_lat * h / u_gas
     W, H = nx * h, ny * h
     pos = rsa(2, (W, H), (r, 0.0), (W - r, H), (0, 1), d_p * (1 + 1e-9), n_particles, seed)

@@ -1,0 +1,126 @@
+"""Serving: continuous batching of independent beds (lbdps_server_*).
+
+A bed's result must be the same when it runs alone, directly through
+lbdps_create/lbdps_step, or inside a mix of beds that arrive while it runs;
+admission must keep the resident footprint within the HBM budget; a request
+that can never fit is rejected; an allocator failure (injected on the host
+through the allocator callback) fails that request and leaves the server
+serving the others.
+"""
+import numpy as np
+import pytest
+
+from paper_1303_2653_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1303_2653_gb300 import build
+    build.build_all()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _lb():
+    from paper_1303_2653_gb300 import lbdps
+    return lbdps
+
+
+def _mix():
+    return [W.scaled_riser2d(nx=64, ny=128, seed=11),
+            W.bubbling2d(nx=32, ny=64, n_particles=300, seed=12, storage=W.STORE_F32),
+            W.scaled_riser2d(nx=96, ny=64, seed=13, storage=W.STORE_F16),
+            W.scaled_riser3d(nx=12, ny=12, nz=24, n_particles=500, solid_fraction=0.05, seed=14)]
+
+
+def _drain(server, want, max_polls=200000):
+    done = {}
+    for _ in range(max_polls):
+        for r in server.poll(wait_s=0.001):
+            done[r["id"]] = r
+        if want <= set(done):
+            return done
+    raise AssertionError("server did not finish")
+
+
+def test_result_alone_equals_mix_and_direct():
+    L = _lb()
+    beds = _mix()
+    target, K = beds[0], 47
+    direct = L.Bed(target)
+    direct.step(K)
+    f_d = direct.populations()
+    P_d, v_d = direct.particles()
+    direct.close()
+
+    s = L.Server(hbm_budget=4 << 30, max_active=8, steps_per_tick=5)
+    rid = s.submit(target, K, keep=True)
+    assert _drain(s, {rid})[rid]["status"] == 0
+    alone = s.take(rid)
+    np.testing.assert_array_equal(alone.populations(), f_d)
+    P_a, v_a = alone.particles()
+    np.testing.assert_array_equal(P_a, P_d)
+    np.testing.assert_array_equal(v_a, v_d)
+    alone.close()
+
+    ids = [s.submit(beds[1], 80), s.submit(beds[2], 33)]
+    rid = s.submit(target, K, keep=True)
+    s.poll(wait_s=0.0)
+    ids.append(s.submit(beds[3], 25))          # arrives while the target runs
+    done = _drain(s, set(ids) | {rid})
+    assert all(done[i]["status"] == 0 for i in ids + [rid])
+    mixed = s.take(rid)
+    np.testing.assert_array_equal(mixed.populations(), f_d)
+    P_m, v_m = mixed.particles()
+    np.testing.assert_array_equal(P_m, P_d)
+    np.testing.assert_array_equal(v_m, v_d)
+    mixed.close()
+    s.close()
+
+
+def test_admission_stays_within_budget():
+    L = _lb()
+    w = W.scaled_riser2d(nx=64, ny=64, seed=21)
+    need = L.memory_estimate(w)
+    s = L.Server(hbm_budget=2 * need + need // 2, max_active=16, steps_per_tick=4)
+    ids = [s.submit(w, 30) for _ in range(5)]
+    seen_active, done = 0, {}
+    for _ in range(200000):
+        q, a, used = s.load()
+        assert used <= 2 * need + need // 2
+        seen_active = max(seen_active, a)
+        for r in s.poll(wait_s=0.0005):
+            done[r["id"]] = r
+        if set(ids) <= set(done):
+            break
+    assert set(ids) <= set(done)
+    assert seen_active == 2
+    assert all(done[i]["status"] == 0 and done[i]["steps"] == 30 for i in ids)
+    assert s.load() == (0, 0, 0)
+    s.close()
+
+
+def test_request_beyond_budget_is_rejected():
+    L = _lb()
+    w = W.scaled_riser2d(nx=64, ny=64, seed=22)
+    s = L.Server(hbm_budget=L.memory_estimate(w) - 1, max_active=4, steps_per_tick=4)
+    with pytest.raises(L.LbdpsError) as ei:
+        s.submit(w, 10)
+    assert ei.value.code == L.ERR_CAPACITY
+    s.close()
+
+
+def test_allocator_failure_fails_only_that_request():
+    L = _lb()
+    w = W.scaled_riser2d(nx=64, ny=64, seed=23)
+    s = L.Server(hbm_budget=1 << 30, max_active=4, steps_per_tick=4)
+    ok1 = s.submit(w, 20)
+    bad = s.submit(w, 20, alloc=lambda n: None, free=lambda p: None)   # refuses every allocation
+    ok2 = s.submit(w, 20)
+    done = _drain(s, {ok1, bad, ok2})
+    assert done[ok1]["status"] == 0 and done[ok2]["status"] == 0
+    assert done[bad]["status"] == L.ERR_OOM
+    s.close()
