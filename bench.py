@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--max-active", type=int, default=128)
     ap.add_argument("--steps-per-tick", type=int, default=32)
+    ap.add_argument("--precision", action="store_true",
+                    help="per-field error of FP32/FP16/BF16 storage against the FP64 oracle")
+    ap.add_argument("--precision-steps", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -230,6 +233,10 @@ def main():
     if args.serving:
         if rank == 0:
             serving_main(args)
+        return
+    if args.precision:
+        if rank == 0:
+            precision_main(args)
         return
 
     import torch
@@ -430,7 +437,10 @@ def serving_main(args):
     server.close()
     served_lat = np.array([lat[i] for i in range(len(reqs))])
     eps_served = np.array([done[i]["mean_eps_g"] for i in range(len(reqs))])
-    bad = sum(1 for i in range(len(reqs)) if done[i]["status"] != 0)
+    failed = [{"request": i, "workload": reqs[i][1].name, "storage": reqs[i][1].storage,
+               "status": done[i]["status"], "health": done[i].get("health")}
+              for i in range(len(reqs)) if done[i]["status"] != 0]
+    ok = np.array([done[i]["status"] == 0 for i in range(len(reqs))])
 
     # baseline: the same requests one by one in plain FP32 (FIFO in arrival order)
     t_free, base_lat, eps_fp32 = 0.0, [], []
@@ -450,15 +460,15 @@ def serving_main(args):
     base_lat = np.array(base_lat)
     base_makespan = t_free - reqs[0][0]
     eps_fp32 = np.array(eps_fp32)
-    rel = np.abs(eps_served - eps_fp32) / eps_fp32
-    solid_rel = np.abs(eps_served - eps_fp32) / np.maximum(1 - eps_fp32, 1e-12)
+    rel = (np.abs(eps_served - eps_fp32) / eps_fp32)[ok]
+    solid_rel = (np.abs(eps_served - eps_fp32) / np.maximum(1 - eps_fp32, 1e-12))[ok]
     line = {"metric": "served p50/p99 time-to-K-steps and aggregate MLUPS", "unit": "s / MLUPS",
             "requests": len(reqs), "rate_per_s": args.rate, "cell_updates": work,
             "data": "synthetic",
             "served": {"p50_s": float(np.percentile(served_lat, 50)),
                        "p99_s": float(np.percentile(served_lat, 99)),
                        "aggregate_mlups": work / makespan / 1e6, "makespan_s": makespan,
-                       "failed": bad, "budget_bytes": budget, "max_active": args.max_active,
+                       "failed": len(failed), "failed_requests": failed, "budget_bytes": budget, "max_active": args.max_active,
                        "steps_per_tick": args.steps_per_tick,
                        "fp16_requests": sum(1 for _, w in reqs if w.storage == W.STORE_F16)},
             "one_by_one_fp32": {"p50_s": float(np.percentile(base_lat, 50)),
@@ -467,6 +477,64 @@ def serving_main(args):
                                 "makespan_s": base_makespan},
             "mean_voidage_rel_err": {"max": float(rel.max()), "mean": float(rel.mean()),
                                      "max_rel_to_solid_fraction": float(solid_rel.max())}}
+    print(json.dumps(line), flush=True)
+
+
+
+# ------------------------------------------------------------------ precision table
+
+def precision_main(args):
+    """Per-field error of FP32, FP16 and BF16 population storage against the
+    FP64 oracle on the riser (scaled to a lattice the oracle steps quickly),
+    after 1 step and after args.precision_steps steps, all started from the
+    same description.  After many steps the particle trajectories are
+    chaotic, so bed-averaged quantities are reported beside the pointwise
+    errors."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from oracle import oracle as O
+    from paper_1303_2653_gb300 import lbdps as L
+    from paper_1303_2653_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    w = W.scaled_riser2d(nx=64, ny=512, seed=1303002)
+    mask = L.FIELD_RHO | L.FIELD_U | L.FIELD_FPG | L.FIELD_VS | L.FIELD_NTOT | L.FIELD_EPS_G
+    names = {"f64": W.STORE_F64, "f32": W.STORE_F32, "f16": W.STORE_F16, "bf16": W.STORE_BF16}
+    beds = {k: L.Bed(w, storage=v, diagnostics=True) for k, v in names.items()}
+    ob = O.OracleBed(w)
+    table = {}
+    done = 0
+    for target in (1, args.precision_steps):
+        ob.step(target - done)
+        for b in beds.values():
+            b.step(target - done)
+        done = target
+        ref = {"rho": ob.field(O.F_RHO), "u": ob.field(O.F_U), "fpg": ob.field(O.F_FPG),
+               "vs": ob.field(O.F_VS), "eps_g": ob.field(O.F_EPS_G)}
+        Po, vo = ob.particles()
+        so = ob.stats()
+        row = {}
+        for k, b in beds.items():
+            g = b.fields(mask)
+            Pg, vg = b.particles()
+            st = b.stats()
+            e = {f: float(np.abs(g[f] - ref[f]).max() / max(np.abs(ref[f]).max(), 1e-300))
+                 for f in ("u", "fpg", "vs")}
+            e["rho_abs"] = float(np.abs(g["rho"] - ref["rho"]).max())
+            e["eps_g_abs"] = float(np.abs(g["eps_g"] - ref["eps_g"]).max())
+            e["P_abs_max"] = float(np.abs(Pg - Po).max())
+            e["v"] = float(np.abs(vg - vo).max() / np.abs(vo).max())
+            e["mean_eps_g_rel"] = float(abs(st["mean_eps_g"] - so["mean_eps_g"]) / so["mean_eps_g"])
+            e["mean_slip_rel"] = float(abs(st["mean_slip"] - so["mean_slip"]) / so["mean_slip"])
+            e["mass_rel"] = float(abs(st["mass"] - so["mass"]) / so["mass"])
+            row[k] = e
+        table[f"after_{target}_steps"] = row
+    line = {"metric": "per-field error against the FP64 oracle", "workload":
+            f"riser2d D2Q9 {w.n[0]}x{w.n[1]}, {w.n_particles} particles", "table": table,
+            "note": "u, fpg, vs, v: max|d|/max|oracle|; rho, eps_g: max|d|; P: max|d| in cells; "
+                    "mean_*: relative error of the lattice/particle averages"}
     print(json.dumps(line), flush=True)
 
 

@@ -468,10 +468,27 @@ static void sort_particles(ob_bed *b)
 /* ------------------------------------------------------------------------ */
 /* Step 2 of Fig. 4: deposition of momentum (Eq. 8) and voidage (Eq. 10-11). */
 /* ------------------------------------------------------------------------ */
-static void deposit(ob_bed *b)
+/* Solid fraction (Eq. 10, capped at close packing, reading R3) and gas
+ * voidage (Eq. 11 in 2D) of a cell holding n particle centres. */
+static double voidage_of_count(const ob_bed *b, int64_t n, double *eps_s, double *eps_2d)
 {
     const double cap2d = M_PI / (2.0 * sqrt(3.0));   /* close-packed discs (R3) */
     const double cap3d = M_PI / (3.0 * sqrt(2.0));   /* close-packed spheres */
+    double es;
+    if (b->dim == 2) {
+        es = (double)n * M_PI * b->k.r * b->k.r;      /* Eq. 10, h = 1 */
+        if (es > cap2d) es = cap2d;
+    } else {
+        es = (double)n * b->k.vp;
+        if (es > cap3d) es = cap3d;
+    }
+    *eps_s = es;
+    *eps_2d = 1.0 - es;
+    return b->dim == 2 ? ob_eps3d(1.0 - es) : 1.0 - es;  /* Eq. 11 */
+}
+
+static void deposit(ob_bed *b)
+{
     for (int64_t x = 0; x < b->ncell; ++x) {
         int64_t s = b->cell_start[x], t = b->cell_start[x + 1];
         int64_t n = t - s;
@@ -480,19 +497,7 @@ static void deposit(ob_bed *b)
             for (int a = 0; a < 3; ++a) sum[a] += b->v[p * 3 + a];
         b->ntot[x] = n;
         for (int a = 0; a < 3; ++a) b->vs[x * 3 + a] = (n > 0) ? sum[a] / (double)n : 0.0;
-        if (b->dim == 2) {
-            double es = (double)n * M_PI * b->k.r * b->k.r;      /* Eq. 10, h = 1 */
-            if (es > cap2d) es = cap2d;
-            b->eps_s[x] = es;
-            b->eps_2d[x] = 1.0 - es;
-            b->eps_g[x] = ob_eps3d(b->eps_2d[x]);                 /* Eq. 11 */
-        } else {
-            double es = (double)n * b->k.vp;
-            if (es > cap3d) es = cap3d;
-            b->eps_s[x] = es;
-            b->eps_2d[x] = 1.0 - es;
-            b->eps_g[x] = 1.0 - es;
-        }
+        b->eps_g[x] = voidage_of_count(b, n, &b->eps_s[x], &b->eps_2d[x]);
         b->omega[x] = ob_omega(b->eps_g[x]);                      /* Eq. 20 */
     }
 }
@@ -1139,7 +1144,10 @@ void ob_stats(const ob_bed *b, double *out)
     for (int k = 0; k < 7; ++k) out[k] = s[k] + c[k];
     double se = 0.0, ss = 0.0, nw = 0.0;
     for (int64_t x = 0; x < b->ncell; ++x) {
-        se += b->eps_g[x];
+        /* voidage of the current positions (the particles were re-sorted
+         * after the move, so cell_start is up to date) */
+        double es, e2;
+        se += voidage_of_count(b, b->cell_start[x + 1] - b->cell_start[x], &es, &e2);
         if (b->ntot[x] > 0) {
             double sl = 0.0;
             for (int a = 0; a < b->dim; ++a) {

@@ -196,6 +196,10 @@ def test_one_step_parity(name, storage):
     co = ob.particle_diag(O.P_CELL).astype(np.int64)
     if storage == W.STORE_F64:
         np.testing.assert_array_equal(cg, co)
+        # bed statistics: FP64 reductions of the same quantities
+        sg, so = bed.stats(), ob.stats()
+        assert sg["mean_eps_g"] == pytest.approx(so["mean_eps_g"], rel=1e-13)
+        assert sg["mass"] == pytest.approx(so["mass"], rel=1e-13)
     else:
         mism = cg != co
         if mism.any():

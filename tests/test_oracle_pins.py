@@ -533,6 +533,25 @@ def test_sort_and_deposition_bruteforce():
                                rtol=1e-15)
 
 
+def test_mean_voidage_of_current_positions():
+    # The bed-mean voidage reported after a step is that of the particle
+    # positions at the end of the step (Eq. 10 counts, Eq. 11 mapping), not
+    # of the deposition at its start.
+    w = _dense_bed(2)
+    bed = O.OracleBed(w)
+    bed.step(3)
+    P, _ = bed.particles()
+    nx, ny = w.n
+    cell = np.floor(P[:, 0]).astype(np.int64) + nx * np.floor(P[:, 1]).astype(np.int64)
+    n = np.bincount(cell, minlength=nx * ny)
+    r = bed.constants()["r"]
+    es = np.minimum(n * math.pi * r * r, math.pi / (2 * math.sqrt(3)))
+    expect = np.mean([O.eps3d(1.0 - e) for e in es])
+    assert bed.stats()["mean_eps_g"] == pytest.approx(expect, rel=1e-14)
+    # the deposition of the last step used the positions before the move
+    assert np.any(bed.field(O.F_NTOT) != n)
+
+
 def test_les_reduces_to_bgk_and_solves_quadratic():
     w0 = _small_riser(2, 0.0)
     w1 = _small_riser(2, 0.2)
