@@ -22,7 +22,10 @@
  *     Inputs are copied; the caller keeps ownership of its arrays.
  *   - Device memory is owned by the handle.  It is obtained from params.alloc
  *     (for example a framework's caching allocator) or, when that is NULL,
- *     from cudaMalloc, and released at lbdps_destroy.
+ *     from cudaMalloc, and released at lbdps_destroy.  Every block params.alloc
+ *     returns must be 256-byte aligned (the kernels use 16-byte vector
+ *     accesses); a misaligned block makes lbdps_create fail with
+ *     LBDPS_ERR_INVALID before any kernel runs.
  *   - Work is issued on params.stream (a cudaStream_t, NULL = a stream the
  *     handle creates).  lbdps_step is asynchronous; functions that return
  *     host data synchronise that stream first.
@@ -70,15 +73,17 @@ extern "C" {
 #define LBDPS_UNITS_SI      1
 
 /* ---- node fields of the last step (lbdps_fields mask bits) ---------- */
+/* always available */
 #define LBDPS_FIELD_RHO    (1 << 0)  /* gas density, Eq. 5                          (1)   */
-#define LBDPS_FIELD_U      (1 << 1)  /* superficial gas velocity, Eq. 24            (dim) */
 #define LBDPS_FIELD_FPG    (1 << 2)  /* force on the gas from particles, Eq. 25     (dim) */
 #define LBDPS_FIELD_BETA   (1 << 3)  /* inter-phase coefficient, Eq. 19             (1)   */
+#define LBDPS_FIELD_UACT   (1 << 7)  /* interstitial gas velocity u / eps, the velocity
+                                        the drag interpolates (Eq. 26)              (dim) */
 /* the following need params.diagnostics = 1 */
+#define LBDPS_FIELD_U      (1 << 1)  /* superficial gas velocity, Eq. 24            (dim) */
 #define LBDPS_FIELD_VS     (1 << 4)  /* mean solid velocity, Eq. 8                  (dim) */
 #define LBDPS_FIELD_NTOT   (1 << 5)  /* particles per cell, Fig. 1                  (1)   */
 #define LBDPS_FIELD_TAU_T  (1 << 6)  /* LES relaxation time, Eq. 15                 (1)   */
-#define LBDPS_FIELD_UACT   (1 << 7)  /* actual (interstitial) gas velocity          (dim) */
 #define LBDPS_FIELD_EPS_G  (1 << 8)  /* gas voidage used by the drag, Eq. 11        (1)   */
 
 /* ---- per-particle diagnostics (lbdps_particle_diag) ----------------- */
@@ -176,8 +181,9 @@ int lbdps_sync(lbdps_t *h);
 /* Copy node fields of the last step (collision-time values, Eq. 5, 24, 25,
  * 19) into out: for each bit of mask in increasing order, ncell values (or
  * ncell x dim, cell-major) as double.  cap is the capacity of out in doubles;
- * LBDPS_ERR_CAPACITY if too small.  Bits LBDPS_FIELD_VS and above need
- * params.diagnostics = 1.  units: LBDPS_UNITS_LATTICE or _SI. */
+ * LBDPS_ERR_CAPACITY if too small.  Bits other than RHO, FPG, BETA and UACT
+ * need params.diagnostics = 1 (else LBDPS_ERR_INVALID).  units:
+ * LBDPS_UNITS_LATTICE or _SI. */
 int lbdps_fields(lbdps_t *h, int mask, int units, double *out, size_t cap);
 
 /* Copy the particle state (section 2.2: P, v) in id order, n x dim each.

@@ -87,6 +87,7 @@ struct DeviceAlloc {
     void *ctx = nullptr;
     std::vector<void *> owned;
     bool count_only = false;     // only add up the sizes (memory estimate)
+    bool misaligned = false;     // params.alloc returned a block off a 256-byte boundary
     size_t counted = 0;
 
     void *get(size_t bytes)
@@ -100,6 +101,11 @@ struct DeviceAlloc {
         void *p = nullptr;
         if (alloc) {
             p = alloc(bytes, ctx);
+            if (p && ((uintptr_t)p & 255u)) {
+                owned.push_back(p);
+                misaligned = true;
+                return nullptr;
+            }
         } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
@@ -176,8 +182,9 @@ template <class L, class Real, class S> struct EngineT : Engine {
     int *cl_local[2] = {nullptr, nullptr}, *cl_base[2] = {nullptr, nullptr};
     int *tile_total = nullptr;
     unsigned *ticket = nullptr;
-    int *key = nullptr, *counts = nullptr, *slot = nullptr, *idslot = nullptr;
-    Real *fpre = nullptr, *gradp = nullptr, *diag_fpre = nullptr, *diag_fd = nullptr;
+    int *key = nullptr, *counts = nullptr, *idslot = nullptr;
+    int2 *slot = nullptr;     // (source index, cell) of each sorted slot
+    Real *diag_fpre = nullptr, *diag_fd = nullptr;
     int *best = nullptr, *wall = nullptr;
     Real *tabs[10] = {};
     int *tab_branch = nullptr;
@@ -215,8 +222,9 @@ template <class L, class Real, class S> struct EngineT : Engine {
         }
         fld.rho = (Real *)get(sizeof(Real) * nc);
         fld.beta = (Real *)get(sizeof(Real) * nc);
+        fld.solg = (Real *)get(sizeof(Real) * nc);
         for (int a = 0; a < D; ++a) {
-            fld.u[a] = (Real *)get(sizeof(Real) * nc);
+            fld.uact[a] = (Real *)get(sizeof(Real) * nc);
             fld.fpg[a] = (Real *)get(sizeof(Real) * nc);
         }
         if (H->prm.diagnostics) {
@@ -225,19 +233,17 @@ template <class L, class Real, class S> struct EngineT : Engine {
             fld.ntot = (int *)get(sizeof(int) * nc);
             for (int a = 0; a < D; ++a) {
                 fld.vs[a] = (Real *)get(sizeof(Real) * nc);
-                fld.uact[a] = (Real *)get(sizeof(Real) * nc);
+                fld.u[a] = (Real *)get(sizeof(Real) * nc);
             }
             diag_fpre = (Real *)get(sizeof(Real) * D * np);
             diag_fd = (Real *)get(sizeof(Real) * D * np);
         }
         key = (int *)get(sizeof(int) * np);
         counts = (int *)get(sizeof(int) * (nc + 1));
-        slot = (int *)get(sizeof(int) * np);
+        slot = (int2 *)get(sizeof(int2) * np);
         idslot = (int *)get(sizeof(int) * np);
         tile_total = (int *)get(sizeof(int) * cell_tiles(H->ncell));
         ticket = (unsigned *)get(sizeof(unsigned));
-        fpre = (Real *)get(sizeof(Real) * D * np);
-        gradp = (Real *)get(sizeof(Real) * D * np);
         best = (int *)get(sizeof(int) * np);
         wall = (int *)get(sizeof(int) * np);
         for (int t = 0; t < 10; ++t) tabs[t] = (Real *)get(sizeof(Real) * H->ntab);
@@ -251,20 +257,21 @@ template <class L, class Real, class S> struct EngineT : Engine {
         red_out = (double *)get(sizeof(double) * 8);
         npairs_dev = (unsigned long long *)get(sizeof(unsigned long long));
         void *must[] = {f[0], f[1], cl_local[0], cl_local[1], cl_base[0], cl_base[1], fld.rho,
-                        fld.beta, key, counts, slot, idslot, tile_total, ticket, fpre, gradp,
+                        fld.beta, fld.solg, key, counts, slot, idslot, tile_total, ticket,
                         best, wall, tab_branch, inlet_dev, health_dev,
                         red_partials, red_out, npairs_dev, part[0].id, part[1].id,
                         part[0].cell, part[1].cell};
         for (void *p : must)
             if (!p) return fail(LBDPS_ERR_OOM, "device allocation failed");
         for (int a = 0; a < D; ++a)
-            if (!fld.u[a] || !fld.fpg[a] || !part[0].P[a] || !part[1].P[a] || !part[0].v[a] ||
+            if (!fld.uact[a] || !fld.fpg[a] || !part[0].P[a] || !part[1].P[a] || !part[0].v[a] ||
                 !part[1].v[a] || !part[0].off[a] || !part[1].off[a])
                 return fail(LBDPS_ERR_OOM, "device allocation failed");
         for (int t = 0; t < 10; ++t)
             if (!tabs[t]) return fail(LBDPS_ERR_OOM, "device allocation failed");
         if (!tab_pk[0] || !tab_pk[1]) return fail(LBDPS_ERR_OOM, "device allocation failed");
-        if (H->prm.diagnostics && (!fld.tau_t || !fld.eps_g || !fld.ntot || !diag_fpre || !diag_fd))
+        if (H->prm.diagnostics && (!fld.tau_t || !fld.eps_g || !fld.ntot || !diag_fpre || !diag_fd ||
+                                   !fld.vs[0] || !fld.u[0] || !fld.vs[D - 1] || !fld.u[D - 1]))
             return fail(LBDPS_ERR_OOM, "device allocation failed");
         fill_params();
         return LBDPS_OK;
@@ -528,7 +535,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
             if (mask & (1 << bit)) need += nc * (((1 << bit) & vec_bits) ? D : 1);
         if (mask & ~((1 << 9) - 1)) return fail(LBDPS_ERR_INVALID, "unknown field bits");
         if (need > cap) return fail(LBDPS_ERR_CAPACITY, "fields need %zu doubles", need);
-        if ((mask & ~0xF) && !H->prm.diagnostics)
+        const int plain = LBDPS_FIELD_RHO | LBDPS_FIELD_FPG | LBDPS_FIELD_BETA | LBDPS_FIELD_UACT;
+        if ((mask & ~plain) && !H->prm.diagnostics)
             return fail(LBDPS_ERR_INVALID, "diagnostic fields need params.diagnostics = 1");
         const double us = units == LBDPS_UNITS_SI ? H->h / H->dt : 1.0;
         const double rs = units == LBDPS_UNITS_SI ? H->prm.rho_g : 1.0;
@@ -1084,7 +1092,11 @@ int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
         if (h->own_stream) cudaStreamDestroy(h->stream);
         return code;
     };
-    if ((rc = h->eng->allocate(h->mem))) return cleanup(rc);
+    if ((rc = h->eng->allocate(h->mem))) {
+        if (h->mem.misaligned)
+            rc = fail(LBDPS_ERR_INVALID, "params.alloc returned a block that is not 256-byte aligned");
+        return cleanup(rc);
+    }
     if (cudaMallocHost(&h->health_host, sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         return cleanup(fail(LBDPS_ERR_OOM, "pinned allocation failed"));

@@ -145,8 +145,8 @@ template <class Real> struct StepParams {
 
 // Device buffers of one bed.
 template <class Real> struct Fields {
-    Real *rho, *u[3], *fpg[3], *beta;                  // node outputs of the collision
-    Real *vs[3], *tau_t, *uact[3], *eps_g;              // diagnostics (may be null)
+    Real *rho, *uact[3], *fpg[3], *beta, *solg;         // node outputs of the collision
+    Real *vs[3], *tau_t, *u[3], *eps_g;                 // diagnostics (may be null)
     int *ntot;                                          // diagnostics (may be null)
 };
 
@@ -219,7 +219,7 @@ void launch_cell_scan(const int *counts, CellListOut out, int ncell, cudaStream_
 
 // slot placement and in-cell ordering by id: src (any order) -> dst (cell, id)
 template <class Real>
-void launch_place(int dim, const int *key, int *counts, CellList cells, int *slot, int *idslot,
+void launch_place(int dim, const int *key, int *counts, CellList cells, int2 *slot, int *idslot,
                   Particles<Real> src, Particles<Real> dst, int np, cudaStream_t st);
 
 template <int D, class Real>

@@ -252,6 +252,34 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
     const Real eq0 = drho - Real(1.5) * rho * uu;
     const Real es0 = drho - Real(1.5) * rho * vv;
 
+    // ---- node outputs (Eq. 5, 24, 25, 19) ----
+    // Written before the collision so that m and the drag tables are dead
+    // while the populations are relaxed and streamed.  The drag
+    // interpolation reads u_act, beta and 1 - eps of each stencil node from
+    // these arrays alone (no cell-list or table lookups).
+    const Real inv_div = t0.z;
+    Real slip2 = Real(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        fld.fpg[a][x] = og * (rho * u[a] + rho * vs[a] - Real(2) * m[a]);
+        const Real ua = u[a] * inv_div;
+        fld.uact[a][x] = ua;
+        const Real sl = ua - vs[a];
+        slip2 += sl * sl;
+    }
+    fld.rho[x] = rho;
+    fld.solg[x] = p.tab.sol_g[nn];
+    const Real slip = sqrt_pos(slip2);
+    Real beta;
+    if (t1.w == Real(0)) {
+        beta = t0.w + t1.x * slip;                                   // Ergun
+    } else {
+        const Real re = t1.z * slip;                                 // Eq. 22
+        beta = (re < Real(1000)) ? t0.w * (Real(1) + Real(0.15) * re_pow(re))   // Eq. 19, 21
+                                 : t1.y * slip;
+    }
+    fld.beta[x] = beta;
+
     // ---- LES (Eq. 13-15) ----
     Real inv_tau_t = p.inv_tau, gam_t = t0.y, tau_t = p.tau;
     if (LES) {
@@ -353,27 +381,6 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
 
 #undef LBDPS_EMIT
 
-    // ---- node outputs (Eq. 5, 24, 25, 19) ----
-    const Real inv_div = t0.z;
-    Real slip2 = Real(0);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        fld.u[a][x] = u[a];
-        fld.fpg[a][x] = og * (rho * u[a] + rho * vs[a] - Real(2) * m[a]);
-        const Real sl = u[a] * inv_div - vs[a];
-        slip2 += sl * sl;
-    }
-    fld.rho[x] = rho;
-    const Real slip = sqrt_pos(slip2);
-    Real beta;
-    if (t1.w == Real(0)) {
-        beta = t0.w + t1.x * slip;                                   // Ergun
-    } else {
-        const Real re = t1.z * slip;                                 // Eq. 22
-        beta = (re < Real(1000)) ? t0.w * (Real(1) + Real(0.15) * re_pow(re))   // Eq. 19, 21
-                                 : t1.y * slip;
-    }
-    fld.beta[x] = beta;
     if (fld.ntot) {
         fld.ntot[x] = n;
         fld.tau_t[x] = tau_t;
@@ -381,7 +388,7 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             fld.vs[a][x] = vs[a];
-            fld.uact[a][x] = u[a] * inv_div;
+            fld.u[a][x] = u[a];
         }
     }
     if (!(rho > Real(0)) || !(uu < Real(0.09))) atomicOr(p.health, HEALTH_DIVERGED);

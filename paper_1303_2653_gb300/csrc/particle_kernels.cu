@@ -10,8 +10,56 @@
 #include "lbdps_internal.cuh"
 
 #include <climits>
+#include <map>
+#include <mutex>
 
 namespace lbdpsk {
+
+// Block size for a kernel with one thread per item: the candidate that covers
+// n items in the fewest waves of co-resident blocks (the largest candidate on
+// a tie).  A grid a little larger than one wave pays a whole second wave for
+// its last blocks, which dominates short particle kernels.
+template <class K>
+int wave_block(K kern, long long n)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> fit;   // (kernel, block) -> blocks per SM
+    static int nsm = 0;
+    constexpr int cand[3] = {256, 128, 64};
+    std::lock_guard<std::mutex> lock(mu);
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            nsm = 0;
+            return 256;
+        }
+    }
+    int best = 256;
+    long long best_waves = LLONG_MAX;
+    for (int b : cand) {
+        const auto key = std::make_pair((const void *)kern, b);
+        auto it = fit.find(key);
+        if (it == fit.end()) {
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b, 0) != cudaSuccess) {
+                cudaGetLastError();
+                per_sm = 0;
+            }
+            it = fit.emplace(key, per_sm).first;
+        }
+        if (it->second <= 0) continue;
+        const long long blocks = (n + b - 1) / b;
+        const long long slots = (long long)it->second * nsm;
+        const long long waves = (blocks + slots - 1) / slots;
+        if (waves < best_waves) {
+            best_waves = waves;
+            best = b;
+        }
+    }
+    return best;
+}
 
 __device__ __forceinline__ void cell_coords(int D, const int *n, int c, int *idx)
 {
@@ -69,20 +117,20 @@ __device__ __forceinline__ Real node_gradp(const StepParams<Real> &p, const Real
     if (lo < 0) { if (per) lo += p.n[a]; else { lo = q[a]; scale = Real(1) / Real(3); } }
     if (hi >= p.n[a]) { if (per) hi -= p.n[a]; else { hi = q[a]; scale = Real(1) / Real(3); } }
     const int xl = x + (lo - q[a]) * stride, xh = x + (hi - q[a]) * stride;
-    return (rho[xh] - rho[xl]) * scale;
+    return (__ldg(rho + xh) - __ldg(rho + xl)) * scale;
 }
 
 template <int D, class Real>
 __device__ __forceinline__ void drag_pre_one(const StepParams<Real> &p, const Particles<Real> &parts,
-                                             const CellList &cells, const Fields<Real> &fld,
-                                             const int *idx, int k, Real *fp, Real *gp)
+                                             const Fields<Real> &fld, const int *idx,
+                                             const Real *ok, const Real *vk, Real *fp, Real *gp)
 {
     int i0[3] = {0, 0, 0}, i1[3] = {0, 0, 0};
     Real w1[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         // t = P - 1/2 = cell + off - 1/2; floor(t) and t - floor(t) from the offset
-        const Real o = parts.off[a][k];
+        const Real o = ok[a];
         int lo;
         if (o >= Real(0.5)) { lo = idx[a]; w1[a] = o - Real(0.5); }
         else { lo = idx[a] - 1; w1[a] = o + Real(0.5); }
@@ -110,21 +158,18 @@ __device__ __forceinline__ void drag_pre_one(const StepParams<Real> &p, const Pa
             wt *= bit ? w1[a] : (Real(1) - w1[a]);
         }
         const int node = q[0] + p.n[0] * (q[1] + p.n[1] * q[2]);
-        const int cnt = cells.begin(node + 1) - cells.begin(node);
-        const int nn = cnt < p.tab.ntab ? cnt : p.tab.ntab - 1;
-        const Real inv_div = p.tab.inv_div[nn];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            uk[a] += wt * (fld.u[a][node] * inv_div);
+            uk[a] += wt * __ldg(fld.uact[a] + node);
             gk[a] += wt * node_gradp<Real>(p, fld.rho, q, a);
         }
-        sk += wt * p.tab.sol_g[nn];
-        bk += wt * fld.beta[node];
+        sk += wt * __ldg(fld.solg + node);
+        bk += wt * __ldg(fld.beta + node);
     }
     const Real coef = p.vp * bk / sk;   // V_p beta_k / (1 - eps_k), Eq. 26
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        fp[a] = coef * (uk[a] - parts.v[a][k]);
+        fp[a] = coef * (uk[a] - vk[a]);
         gp[a] = gk[a];
     }
 }
@@ -146,8 +191,15 @@ __device__ __forceinline__ void drag_pre_one(const StepParams<Real> &p, const Pa
 // subtraction; otherwise the full FP64 wall / wrap / floor path runs.  Both
 // give bit-identical results.
 // ---------------------------------------------------------------------------
+// Register budget of the drag and detection kernels, as blocks of 256
+// threads per SM: 48 registers in 2D FP32, so that 200,000 particles fit in
+// one wave of 64-thread blocks (see wave_block).
+template <int D, class Real> struct ParticleOccupancy { static constexpr int value = 2; };
+template <> struct ParticleOccupancy<2, float> { static constexpr int value = 5; };
+template <> struct ParticleOccupancy<3, float> { static constexpr int value = 3; };
+
 template <int D, class Real>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, ParticleOccupancy<D, Real>::value)
 k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, CellList cells,
             Fields<Real> fld, int *__restrict__ key, int *__restrict__ counts, Real *diag_fpre,
             Real *diag_fd, int np)
@@ -161,12 +213,25 @@ k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, Cell
     int c = -1, s0 = 0, s1 = 0;
     int idx[3] = {0, 0, 0};
     Real fp[3] = {Real(0), Real(0), Real(0)}, gp[3] = {Real(0), Real(0), Real(0)};
+    // every load of this particle's own state is issued before the first
+    // dependent one, so that the thread waits on memory about twice
+    Real v0[3] = {Real(0), Real(0), Real(0)}, o0[3] = {Real(0), Real(0), Real(0)};
+    Real fpg[3] = {Real(0), Real(0), Real(0)};
+    double P[3] = {0.0, 0.0, 0.0};
     if (active) {
-        c = parts.cell[k];
+        c = __ldg(parts.cell + k);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            v0[a] = __ldg(parts.v[a] + k);
+            o0[a] = __ldg(parts.off[a] + k);
+            P[a] = __ldg(parts.P[a] + k);
+        }
         s0 = cells.begin(c);
         s1 = cells.begin(c + 1);
+#pragma unroll
+        for (int a = 0; a < D; ++a) fpg[a] = __ldg(fld.fpg[a] + c);
         cell_coords(D, p.n, c, idx);
-        drag_pre_one<D, Real>(p, parts, cells, fld, idx, k, fp, gp);
+        drag_pre_one<D, Real>(p, parts, fld, idx, o0, v0, fp, gp);
     }
     // Eq. 27 in sorted order
     const int len = s1 - s0;
@@ -180,8 +245,13 @@ k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, Cell
         for (int a = 0; a < D; ++a) val[a] = __shfl_sync(0xffffffffu, fp[a], (j - warp_first) & 31);
         if (t < len) {
             if (!in_warp) {
-                Real g2[3];
-                drag_pre_one<D, Real>(p, parts, cells, fld, idx, j, val, g2);
+                Real g2[3], vj[3], oj[3];
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    vj[a] = __ldg(parts.v[a] + j);
+                    oj[a] = __ldg(parts.off[a] + j);
+                }
+                drag_pre_one<D, Real>(p, parts, fld, idx, oj, vj, val, g2);
             }
 #pragma unroll
             for (int a = 0; a < D; ++a) {
@@ -192,23 +262,22 @@ k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, Cell
     }
     if (!active) return;
 
-    const int id = parts.id[k];
-    double P[3] = {0.0, 0.0, 0.0};
     Real v[3] = {Real(0), Real(0), Real(0)}, off[3] = {Real(0), Real(0), Real(0)};
     int q[3] = {0, 0, 0};
     bool stays = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         Real scale = Real(1);
-        if (!(fabs(S[a]) <= Real(1e-12) * A[a])) scale = fabs(fld.fpg[a][c]) / fabs(S[a]);
+        if (!(fabs(S[a]) <= Real(1e-12) * A[a])) scale = fabs(fpg[a]) / fabs(S[a]);
         const Real fd = scale * fp[a];
         if (diag_fd) {
+            const int id = parts.id[k];
             diag_fd[(size_t)a * np + id] = fd;
             diag_fpre[(size_t)a * np + id] = fp[a];
         }
-        v[a] = parts.v[a][k] + (p.geff[a] + (fd + p.psign * p.vp * gp[a]) / p.mp);
-        P[a] = parts.P[a][k] + (double)v[a];
-        const Real on = parts.off[a][k] + v[a];
+        v[a] = v0[a] + (p.geff[a] + (fd + p.psign * p.vp * gp[a]) / p.mp);
+        P[a] = P[a] + (double)v[a];
+        const Real on = o0[a] + v[a];
         if (on > Real(1e-3) && on < Real(1) - Real(1e-3)) {
             q[a] = idx[a];
             off[a] = (Real)(P[a] - (double)idx[a]);
@@ -266,8 +335,9 @@ void launch_drag_step(const StepParams<Real> &p, Particles<Real> parts, Particle
                       Real *diag_fd, int np, cudaStream_t st)
 {
     if (np == 0) return;
-    k_drag_step<D, Real><<<(np + 255) / 256, 256, 0, st>>>(p, parts, out, cells, fld, key, counts,
-                                                           diag_fpre, diag_fd, np);
+    const int b = wave_block(k_drag_step<D, Real>, np);
+    k_drag_step<D, Real><<<(np + b - 1) / b, b, 0, st>>>(p, parts, out, cells, fld, key, counts,
+                                                         diag_fpre, diag_fd, np);
 }
 
 // Keys, offsets and counts of the current positions (used when a particle
@@ -328,12 +398,14 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot, int *t
 
 // ---------------------------------------------------------------------------
 // One-launch scan of counts[0..ncell] into a two-level cell list.  Each block
-// scans one tile of 4096 counts and writes its total; the block that finishes
-// last (ticket counter, nothing waits) scans the tile totals and resets the
-// ticket for the next launch.
+// scans one tile of 4096 counts (four consecutive counts per thread, one
+// 16-byte load and store) and writes its total; the block that finishes last
+// (ticket counter, nothing waits) scans the tile totals and resets the ticket
+// for the next launch.
 // ---------------------------------------------------------------------------
-constexpr int kCellScanThreads = 512;
-constexpr int kCellScanItems = kCellTile / kCellScanThreads;   // 8
+constexpr int kCellScanThreads = 1024;
+constexpr int kCellScanItems = kCellTile / kCellScanThreads;   // 4
+static_assert(kCellScanItems == 4, "one int4 per thread");
 
 __global__ void __launch_bounds__(kCellScanThreads)
 k_cell_scan(const int *__restrict__ counts, CellListOut out, int n)
@@ -342,20 +414,22 @@ k_cell_scan(const int *__restrict__ counts, CellListOut out, int n)
     __shared__ int total;
     __shared__ bool last;
     const int base = blockIdx.x * kCellTile + threadIdx.x * kCellScanItems;
-    int vals[kCellScanItems];
-    int sum = 0;
-#pragma unroll
-    for (int j = 0; j < kCellScanItems; ++j) {
-        const int e = base + j;
-        vals[j] = e < n ? counts[e] : 0;
-        sum += vals[j];
+    int4 c4 = make_int4(0, 0, 0, 0);
+    if (base + kCellScanItems <= n) {
+        c4 = __ldg(reinterpret_cast<const int4 *>(counts + base));
+    } else {
+        if (base + 0 < n) c4.x = counts[base + 0];
+        if (base + 1 < n) c4.y = counts[base + 1];
+        if (base + 2 < n) c4.z = counts[base + 2];
     }
-    int run = block_exclusive_scan(sum, warp_tot, &total);
-#pragma unroll
-    for (int j = 0; j < kCellScanItems; ++j) {
-        const int e = base + j;
-        if (e < n) out.local[e] = run;
-        run += vals[j];
+    const int run = block_exclusive_scan(c4.x + c4.y + c4.z + c4.w, warp_tot, &total);
+    const int4 e4 = make_int4(run, run + c4.x, run + c4.x + c4.y, run + c4.x + c4.y + c4.z);
+    if (base + kCellScanItems <= n) {
+        *reinterpret_cast<int4 *>(out.local + base) = e4;
+    } else {
+        if (base + 0 < n) out.local[base + 0] = e4.x;
+        if (base + 1 < n) out.local[base + 1] = e4.y;
+        if (base + 2 < n) out.local[base + 2] = e4.z;
     }
     if (threadIdx.x == 0) {
         out.tile_total[blockIdx.x] = total;
@@ -464,7 +538,7 @@ void launch_scan(const int *counts, int *cell_start, int *block_sums, int ncell,
 // and the payload is gathered to begin(cell) + rank, the (cell, id) order.
 // ---------------------------------------------------------------------------
 __global__ void k_scatter(const int *__restrict__ key, const int *__restrict__ id,
-                          int *__restrict__ counts, CellList cells, int *__restrict__ slot,
+                          int *__restrict__ counts, CellList cells, int2 *__restrict__ slot,
                           int *__restrict__ idslot, int np)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -472,40 +546,58 @@ __global__ void k_scatter(const int *__restrict__ key, const int *__restrict__ i
     const int c = key[k];
     const int old = atomicSub(&counts[c], 1);
     const int s = cells.begin(c) + old - 1;
-    slot[s] = k;
+    slot[s] = make_int2(k, c);
     idslot[s] = id[k];
 }
 
-template <class Real>
-__global__ void k_gather(int dim, const int *__restrict__ key, CellList cells,
-                         const int *__restrict__ slot, const int *__restrict__ idslot,
-                         Particles<Real> src, Particles<Real> dst, int np)
+// The payload of the particle in slot s is loaded before its rank is known
+// (the loads do not wait on the rank loop), then stored at begin(c) + rank.
+template <int D, class Real>
+__global__ void __launch_bounds__(256)
+k_gather(CellList cells, const int2 *__restrict__ slot, const int *__restrict__ idslot,
+         Particles<Real> src, Particles<Real> dst, int np)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= np) return;
-    const int k = slot[s];
+    const int2 kc = slot[s];
     const int my = idslot[s];
-    const int c = key[k];
-    const int lo = cells.begin(c), hi = cells.begin(c + 1);
+    double P[D];
+    Real v[D], off[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        P[a] = __ldg(src.P[a] + kc.x);
+        v[a] = __ldg(src.v[a] + kc.x);
+        off[a] = __ldg(src.off[a] + kc.x);
+    }
+    const int lo = cells.begin(kc.y), hi = cells.begin(kc.y + 1);
     int rank = 0;
-    for (int q = lo; q < hi; ++q) rank += (idslot[q] < my) ? 1 : 0;
+    if (hi - lo > 1)
+        for (int q = lo; q < hi; ++q) rank += (__ldg(idslot + q) < my) ? 1 : 0;
     const int d = lo + rank;
-    for (int a = 0; a < dim; ++a) {
-        dst.P[a][d] = src.P[a][k];
-        dst.v[a][d] = src.v[a][k];
-        dst.off[a][d] = src.off[a][k];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        dst.P[a][d] = P[a];
+        dst.v[a][d] = v[a];
+        dst.off[a][d] = off[a];
     }
     dst.id[d] = my;
-    dst.cell[d] = c;
+    dst.cell[d] = kc.y;
 }
 
 template <class Real>
-void launch_place(int dim, const int *key, int *counts, CellList cells, int *slot, int *idslot,
+void launch_place(int dim, const int *key, int *counts, CellList cells, int2 *slot, int *idslot,
                   Particles<Real> src, Particles<Real> dst, int np, cudaStream_t st)
 {
     if (np == 0) return;
-    k_scatter<<<(np + 255) / 256, 256, 0, st>>>(key, src.id, counts, cells, slot, idslot, np);
-    k_gather<Real><<<(np + 255) / 256, 256, 0, st>>>(dim, key, cells, slot, idslot, src, dst, np);
+    const int bs = wave_block(k_scatter, np);
+    k_scatter<<<(np + bs - 1) / bs, bs, 0, st>>>(key, src.id, counts, cells, slot, idslot, np);
+    if (dim == 2) {
+        const int b = wave_block(k_gather<2, Real>, np);
+        k_gather<2, Real><<<(np + b - 1) / b, b, 0, st>>>(cells, slot, idslot, src, dst, np);
+    } else {
+        const int b = wave_block(k_gather<3, Real>, np);
+        k_gather<3, Real><<<(np + b - 1) / b, b, 0, st>>>(cells, slot, idslot, src, dst, np);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -520,7 +612,7 @@ void launch_place(int dim, const int *key, int *counts, CellList cells, int *slo
 // moving toward it).
 // ---------------------------------------------------------------------------
 template <int D, class Real>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, ParticleOccupancy<D, Real>::value)
 k_detect(StepParams<Real> p, Particles<Real> parts, CellList cells, int *__restrict__ best_out,
          int *__restrict__ wall_out, long long *pairs, unsigned long long *npairs,
          long long pair_cap, int np)
@@ -542,77 +634,107 @@ k_detect(StepParams<Real> p, Particles<Real> parts, CellList cells, int *__restr
 
     int best = -1, best_id = INT_MAX;
     double best_d2 = __longlong_as_double(0x7ff0000000000000ll);
-    double Pi[3] = {0.0, 0.0, 0.0}, vi[3] = {0.0, 0.0, 0.0};
-    bool have_i = false;
-    const int oz0 = (D == 3) ? -1 : 0, oz1 = (D == 3) ? 1 : 0;
-    for (int oz = oz0; oz <= oz1; ++oz)
-    for (int oy = -1; oy <= 1; ++oy)
-    for (int ox = -1; ox <= 1; ++ox) {
-        const int off3[3] = {ox, oy, oz};
-        int q[3];
-        float shift[3];
-        bool skip = false;
+    // candidate j, whose cell lies in the row starting at cell index rowbase
+    // and whose y (z) cell offset from particle i is sy (sz)
+    auto test = [&](int j, int rowbase, float sy, float sz) {
+        if (j == i) return;
+        // coarse test: P_i - P_j = (o_i - o_j) - (cell_j - cell_i), minimum
+        // image on periodic axes
+        const float shift[3] = {(float)(__ldg(parts.cell + j) - rowbase - idx[0]), sy, sz};
+        float d2f = 0.f;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            q[a] = idx[a] + off3[a];
-            shift[a] = (float)off3[a];
-            if (a < D && (q[a] < 0 || q[a] >= p.n[a])) {
-                if (per[a]) q[a] = (q[a] + p.n[a]) % p.n[a];
-                else skip = true;
+        for (int a = 0; a < D; ++a) {
+            float dx = oi[a] - (float)__ldg(parts.off[a] + j) - shift[a];
+            if (per[a]) {
+                const float L = (float)p.n[a];
+                if (dx > 0.5f * L) dx -= L;
+                else if (dx < -0.5f * L) dx += L;
+            }
+            d2f += dx * dx;
+        }
+        if (d2f > cut2) return;
+        // exact test in FP64, as written in section 2.2
+        double dx[3] = {0.0, 0.0, 0.0};
+        double d2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            dx[a] = sep_axis(parts.P[a][i], parts.P[a][j], per[a], p.len[a]);
+            d2 = __dadd_rn(d2, __dmul_rn(dx[a], dx[a]));
+        }
+        if (!(d2 < p.d2)) return;
+        double dot = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            dot = __dadd_rn(dot, __dmul_rn(dx[a], __dsub_rn((double)parts.v[a][i],
+                                                             (double)parts.v[a][j])));
+        if (!(dot < 0.0)) return;
+        const int idj = parts.id[j];
+        if (pairs && idi < idj) {
+            const unsigned long long slot = atomicAdd(npairs, 1ull);
+            if ((long long)slot < pair_cap) {
+                pairs[2 * slot] = idi;
+                pairs[2 * slot + 1] = idj;
             }
         }
-        if (skip) continue;
-        const int cc = q[0] + p.n[0] * (q[1] + p.n[1] * q[2]);
-        const int j0 = cells.begin(cc), j1 = cells.begin(cc + 1);
-        for (int j = j0; j < j1; ++j) {
-            if (j == i) continue;
-            // coarse test: P_i - P_j = (o_i - o_j) - shift, minimum image on periodic axes
-            float d2f = 0.f;
+        if (d2 < best_d2 || (d2 == best_d2 && idj < best_id)) {
+            best = j;
+            best_id = idj;
+            best_d2 = d2;
+        }
+    };
+    // The neighbourhood is visited one lattice row (along x) at a time: the
+    // cells x-1, x, x+1 of a row are consecutive in the cell list, so a row
+    // is one range of slots.  The slot ranges of the three rows of a plane
+    // are read together.  Where a periodic x face wraps, the cell across it
+    // is visited separately.
+    int x0 = idx[0] - 1, x1 = idx[0] + 1, xw = -1;
+    if (x0 < 0) {
+        x0 = 0;
+        if (per[0]) xw = p.n[0] - 1;
+    }
+    if (x1 >= p.n[0]) {
+        x1 = p.n[0] - 1;
+        if (per[0]) xw = 0;
+    }
+    const int oz0 = (D == 3) ? -1 : 0, oz1 = (D == 3) ? 1 : 0;
+#pragma unroll 1
+    for (int oz = oz0; oz <= oz1; ++oz) {
+        int qz = idx[2] + oz;
+        if (D == 3 && (qz < 0 || qz >= p.n[2])) {
+            if (!per[2]) continue;
+            qz = qz < 0 ? qz + p.n[2] : qz - p.n[2];
+        }
+        int rb[3], j0[3], j1[3];
+        unsigned rows_ok = 0;
 #pragma unroll
-            for (int a = 0; a < D; ++a) {
-                float dx = oi[a] - (float)parts.off[a][j] - shift[a];
-                if (per[a]) {
-                    const float L = (float)p.n[a];
-                    if (dx > 0.5f * L) dx -= L;
-                    else if (dx < -0.5f * L) dx += L;
-                }
-                d2f += dx * dx;
+        for (int r = 0; r < 3; ++r) {
+            int qy = idx[1] + r - 1;
+            bool ok = true;
+            if (qy < 0 || qy >= p.n[1]) {
+                ok = per[1];
+                qy = qy < 0 ? qy + p.n[1] : qy - p.n[1];
             }
-            if (d2f > cut2) continue;
-            // exact test in FP64, as written in section 2.2
-            if (!have_i) {
+            rows_ok |= ok ? 1u << r : 0u;
+            rb[r] = p.n[0] * (qy + p.n[1] * qz);
+            j0[r] = ok ? cells.begin(rb[r] + x0) : 0;
+            j1[r] = ok ? cells.begin(rb[r] + x1 + 1) : 0;
+        }
+        const float sz = (float)oz;
+        // the three ranges as one loop, so that a warp iterates max over its
+        // threads of the total rather than the sum of per-row maxima
+        const int n0 = j1[0] - j0[0], n01 = n0 + (j1[1] - j0[1]);
+        const int ntot = n01 + (j1[2] - j0[2]);
+        for (int t = 0; t < ntot; ++t) {
+            const int r = t < n0 ? 0 : (t < n01 ? 1 : 2);
+            const int j = r == 0 ? j0[0] + t : (r == 1 ? j0[1] + (t - n0) : j0[2] + (t - n01));
+            test(j, r == 0 ? rb[0] : (r == 1 ? rb[1] : rb[2]), (float)(r - 1), sz);
+        }
+        if (xw >= 0) {
 #pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    Pi[a] = parts.P[a][i];
-                    vi[a] = (double)parts.v[a][i];
-                }
-                have_i = true;
-            }
-            double dx[3] = {0.0, 0.0, 0.0};
-            double d2 = 0.0;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                dx[a] = sep_axis(Pi[a], parts.P[a][j], per[a], p.len[a]);
-                d2 = __dadd_rn(d2, __dmul_rn(dx[a], dx[a]));
-            }
-            if (!(d2 < p.d2)) continue;
-            double dot = 0.0;
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-                dot = __dadd_rn(dot, __dmul_rn(dx[a], __dsub_rn(vi[a], (double)parts.v[a][j])));
-            if (!(dot < 0.0)) continue;
-            const int idj = parts.id[j];
-            if (pairs && idi < idj) {
-                const unsigned long long slot = atomicAdd(npairs, 1ull);
-                if ((long long)slot < pair_cap) {
-                    pairs[2 * slot] = idi;
-                    pairs[2 * slot + 1] = idj;
-                }
-            }
-            if (d2 < best_d2 || (d2 == best_d2 && idj < best_id)) {
-                best = j;
-                best_id = idj;
-                best_d2 = d2;
+            for (int r = 0; r < 3; ++r) {
+                if (!((rows_ok >> r) & 1u)) continue;
+                const int w0 = cells.begin(rb[r] + xw), w1 = cells.begin(rb[r] + xw + 1);
+                for (int j = w0; j < w1; ++j) test(j, rb[r], (float)(r - 1), sz);
             }
         }
     }
@@ -641,8 +763,9 @@ void launch_detect(const StepParams<Real> &p, Particles<Real> parts, CellList ce
                    int np, cudaStream_t st)
 {
     if (np == 0) return;
-    k_detect<D, Real><<<(np + 255) / 256, 256, 0, st>>>(p, parts, cells, best, wall, pairs, npairs,
-                                                        pair_cap, np);
+    const int b = wave_block(k_detect<D, Real>, np);
+    k_detect<D, Real><<<(np + b - 1) / b, b, 0, st>>>(p, parts, cells, best, wall, pairs, npairs,
+                                                      pair_cap, np);
 }
 
 // ---------------------------------------------------------------------------
@@ -694,7 +817,8 @@ void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int 
                     const int *wall, int np, cudaStream_t st)
 {
     if (np == 0) return;
-    k_resolve<D, Real><<<(np + 255) / 256, 256, 0, st>>>(p, parts, best, wall, np);
+    const int b = wave_block(k_resolve<D, Real>, np);
+    k_resolve<D, Real><<<(np + b - 1) / b, b, 0, st>>>(p, parts, best, wall, np);
 }
 
 // ---------------------------------------------------------------------------
@@ -715,9 +839,9 @@ LBDPS_INST_P(2, float)
 LBDPS_INST_P(3, double)
 LBDPS_INST_P(3, float)
 
-template void launch_place<double>(int, const int *, int *, CellList, int *, int *,
+template void launch_place<double>(int, const int *, int *, CellList, int2 *, int *,
                                    Particles<double>, Particles<double>, int, cudaStream_t);
-template void launch_place<float>(int, const int *, int *, CellList, int *, int *,
+template void launch_place<float>(int, const int *, int *, CellList, int2 *, int *,
                                   Particles<float>, Particles<float>, int, cudaStream_t);
 
 }  // namespace lbdpsk

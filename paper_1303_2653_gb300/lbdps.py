@@ -308,7 +308,7 @@ class Bed:
         _check(lib().lbdps_sync(self._h), "lbdps_sync")
 
     # -- data -----------------------------------------------------------------
-    def fields(self, mask: int = FIELD_RHO | FIELD_U | FIELD_FPG | FIELD_BETA,
+    def fields(self, mask: int = FIELD_RHO | FIELD_UACT | FIELD_FPG | FIELD_BETA,
                units: int = UNITS_LATTICE) -> Dict[str, np.ndarray]:
         sizes = []
         for bit, name in enumerate(FIELD_NAMES):

@@ -124,3 +124,29 @@ def test_allocator_failure_fails_only_that_request():
     assert done[ok1]["status"] == 0 and done[ok2]["status"] == 0
     assert done[bad]["status"] == L.ERR_OOM
     s.close()
+
+
+def test_misaligned_allocator_block_is_rejected_before_any_kernel():
+    # A block off a 256-byte boundary would break the 16-byte vector accesses
+    # of the kernels: the bed must fail at creation with ERR_INVALID.
+    import torch
+    L = _lb()
+    w = W.scaled_riser2d(nx=64, ny=64, seed=24)
+    s = L.Server(hbm_budget=1 << 30, max_active=4, steps_per_tick=4)
+    held = {}
+
+    def alloc(n):
+        base = torch.cuda.caching_allocator_alloc(int(n) + 256)
+        held[base + 16] = base
+        return base + 16
+
+    def free(p):
+        torch.cuda.caching_allocator_delete(held.pop(p))
+
+    bad = s.submit(w, 10, alloc=alloc, free=free)
+    ok = s.submit(w, 10)
+    done = _drain(s, {bad, ok})
+    assert done[bad]["status"] == L.ERR_INVALID
+    assert done[ok]["status"] == 0
+    assert not held
+    s.close()
