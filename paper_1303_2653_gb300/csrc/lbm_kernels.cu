@@ -252,6 +252,7 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
     const Real eq0 = drho - Real(1.5) * rho * uu;
     const Real es0 = drho - Real(1.5) * rho * vv;
 
+
     // ---- node outputs (Eq. 5, 24, 25, 19) ----
     // Written before the collision so that m and the drag tables are dead
     // while the populations are relaxed and streamed.  The drag

@@ -191,15 +191,24 @@ __device__ __forceinline__ void drag_pre_one(const StepParams<Real> &p, const Pa
 // subtraction; otherwise the full FP64 wall / wrap / floor path runs.  Both
 // give bit-identical results.
 // ---------------------------------------------------------------------------
-// Register budget of the drag and detection kernels, as blocks of 256
-// threads per SM: 48 registers in 2D FP32, so that 200,000 particles fit in
-// one wave of 64-thread blocks (see wave_block).
-template <int D, class Real> struct ParticleOccupancy { static constexpr int value = 2; };
-template <> struct ParticleOccupancy<2, float> { static constexpr int value = 5; };
-template <> struct ParticleOccupancy<3, float> { static constexpr int value = 3; };
+// Register budgets of the drag and detection kernels, as blocks of 256
+// threads per SM.  Detection fits 40 registers in 2D FP32 (6 blocks: 200,000
+// particles in one wave, see wave_block); the drag spills below 48.
+#ifndef LBDPS_DRAG_BLOCKS_2D_F32
+#define LBDPS_DRAG_BLOCKS_2D_F32 5
+#endif
+#ifndef LBDPS_DRAG_BLOCKS_3D_F32
+#define LBDPS_DRAG_BLOCKS_3D_F32 3
+#endif
+template <int D, class Real> struct DragOccupancy { static constexpr int value = 2; };
+template <> struct DragOccupancy<2, float> { static constexpr int value = LBDPS_DRAG_BLOCKS_2D_F32; };
+template <> struct DragOccupancy<3, float> { static constexpr int value = LBDPS_DRAG_BLOCKS_3D_F32; };
+template <int D, class Real> struct DetectOccupancy { static constexpr int value = 2; };
+template <> struct DetectOccupancy<2, float> { static constexpr int value = 6; };
+template <> struct DetectOccupancy<3, float> { static constexpr int value = 3; };
 
 template <int D, class Real>
-__global__ void __launch_bounds__(256, ParticleOccupancy<D, Real>::value)
+__global__ void __launch_bounds__(256, DragOccupancy<D, Real>::value)
 k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, CellList cells,
             Fields<Real> fld, int *__restrict__ key, int *__restrict__ counts, Real *diag_fpre,
             Real *diag_fd, int np)
@@ -213,8 +222,7 @@ k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, Cell
     int c = -1, s0 = 0, s1 = 0;
     int idx[3] = {0, 0, 0};
     Real fp[3] = {Real(0), Real(0), Real(0)}, gp[3] = {Real(0), Real(0), Real(0)};
-    // every load of this particle's own state is issued before the first
-    // dependent one, so that the thread waits on memory about twice
+    // the particle's own state is loaded before the first dependent load
     Real v0[3] = {Real(0), Real(0), Real(0)}, o0[3] = {Real(0), Real(0), Real(0)};
     Real fpg[3] = {Real(0), Real(0), Real(0)};
     double P[3] = {0.0, 0.0, 0.0};
@@ -612,7 +620,7 @@ void launch_place(int dim, const int *key, int *counts, CellList cells, int2 *sl
 // moving toward it).
 // ---------------------------------------------------------------------------
 template <int D, class Real>
-__global__ void __launch_bounds__(256, ParticleOccupancy<D, Real>::value)
+__global__ void __launch_bounds__(256, DetectOccupancy<D, Real>::value)
 k_detect(StepParams<Real> p, Particles<Real> parts, CellList cells, int *__restrict__ best_out,
          int *__restrict__ wall_out, long long *pairs, unsigned long long *npairs,
          long long pair_cap, int np)
