@@ -152,15 +152,17 @@ def collide_stream_bytes(w, storage):
     q = 9 if w.dim == 2 else 19
     s_f = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}[storage]
     s_r = 8 if storage == "f64" else 4
-    per_cell = 2 * q * s_f + 4 + (1 + w.dim + w.dim + 1) * s_r
+    # populations read and written, the cell-list offset read, and rho,
+    # u_act[dim], F_p->g[dim], beta and 1 - eps written per cell
+    per_cell = 2 * q * s_f + 4 + (3 + 2 * w.dim) * s_r
     per_particle = w.dim * s_r
     return w.ncell * per_cell + w.n_particles * per_particle, per_cell, per_particle
 
 
-def profiled_traffic():
-    """DRAM bytes per collide_stream launch from the committed ncu summary,
-    if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "collide_stream_riser2d_256x2048.md")
+def profiled_traffic(workload_name):
+    """DRAM bytes per collide_stream launch from the committed ncu summary of
+    this workload, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"collide_stream_{workload_name}.md")
     src = os.path.join(ROOT, "paper_1303_2653_gb300", "csrc", "lbm_kernels.cu")
     if not os.path.exists(path):
         return None
@@ -191,6 +193,22 @@ def oracle_rate(w, budget_s):
     return w.ncell * steps / dt / 1e6, steps, dt
 
 
+def max_over_ranks(x, dist=None, device="cuda"):
+    """Max over all ranks of a per-rank figure (a time); barrier after."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def whole_job_mlups(world, cells, steps, seconds):
+    """Cell updates of all ranks (each rank steps its own bed) per second / 1e6."""
+    return world * cells * steps / seconds / 1e6
+
+
 def reference_main(args, rank, world):
     """The oracle as the reference arm: K timed steps, each a bounded sample
     (a slab of the riser at the same solid fraction) so the run stays short."""
@@ -198,20 +216,27 @@ def reference_main(args, rank, world):
     from oracle import oracle as O
     if rank != 0:
         return
-    full = workload(args.storage)
+    full = workload(args.storage, args.workload)
     total = args.steps + args.warmup
     per_step_budget = 120.0 / max(total, 1)
-    # oracle cost is close to 1.0 us per cell plus particles at this density
-    ny = int(max(8, min(full.n[1], per_step_budget / 1.2e-6 / full.n[0])))
-    sample = W.scaled_riser2d(nx=full.n[0], ny=ny, n_particles=int(round(
-        full.n_particles * ny / full.n[1])), storage=W.STORE_F64)
+    # oracle cost is close to 1.2 us per cell (2D) at these densities
+    if full.dim == 2:
+        ny = int(max(8, min(full.n[1], per_step_budget / 1.2e-6 / full.n[0])))
+        sample = W.scaled_riser2d(nx=full.n[0], ny=ny, n_particles=int(round(
+            full.n_particles * ny / full.n[1])), storage=W.STORE_F64)
+    else:
+        plane = full.n[0] * full.n[1]
+        nz = int(max(4, min(full.n[2], per_step_budget / 3.0e-6 / plane)))
+        sample = W.scaled_riser3d(nx=full.n[0], ny=full.n[1], nz=nz, n_particles=int(round(
+            full.n_particles * nz / full.n[2])), storage=W.STORE_F64)
     bed = O.OracleBed(sample)
     bed.step(args.warmup)
     t0 = time.perf_counter()
     bed.step(args.steps)
     dt = time.perf_counter() - t0
     value = sample.ncell * args.steps / dt / 1e6
-    desc = (f"{args.steps} oracle steps of a {sample.n[0]}x{sample.n[1]} slab of the riser "
+    shape = "x".join(str(v) for v in sample.n)
+    desc = (f"{args.steps} oracle steps of a {shape} slab of the riser "
             f"({sample.n_particles} particles, same solid fraction)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -295,14 +320,9 @@ def main():
             ev[k][1].record(st)
     torch.cuda.synchronize()
     clock_info = clocks.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist)
     health = bed.health()
-    value = world * w.ncell * args.steps / (total_ms / 1e3) / 1e6
+    value = whole_job_mlups(world, w.ncell, args.steps, total_ms / 1e3)
 
     # ---- dominant-kernel roofline from per-kernel events (L2 flushed) ----
     prof_steps = min(args.steps, 200)
@@ -318,7 +338,7 @@ def main():
     peak, peak_kind = measured_peaks()
     cs_ms = per_kernel_ms["collide_stream"]
     achieved = alg_bytes / (cs_ms / 1e3) / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled_traffic(w.name.split("-")[0] + "_" + "x".join(str(v) for v in w.n))
     roofline = {"bound": "hbm", "kernel": "collide_stream", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": traffic, "algorithmic_bytes": alg_bytes,
@@ -336,13 +356,13 @@ def main():
             b2.stats()                     # D2H of the FP64 reductions, every step
         P, V = b2.particles()              # D2H of the final particle state
         b2.sync()
-        t_e2e = time.perf_counter() - t0
+        t_e2e = max_over_ranks(time.perf_counter() - t0, dist)
         b2.close()
         real = 8 if args.storage == "f64" else 4
         h2d = w.n_particles * (w.dim * 8 + w.dim * real + 4)
         d2h_step = 7 * 8 + 4
         d2h_final = w.n_particles * (w.dim * 8 + w.dim * real + 4)
-        e2e = {"value": world * w.ncell * args.steps / t_e2e / 1e6, "unit": UNIT,
+        e2e = {"value": whole_job_mlups(world, w.ncell, args.steps, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps,
                "d2h_bytes_per_step": d2h_step + d2h_final / args.steps,
                "includes": "create from host arrays, K x (step + stats readback), final "
@@ -380,7 +400,9 @@ def serving_requests(count, rate, seed=1303004):
     bubbling or riser with p = 1/2; nx log-uniform in [64, 512] and ny in
     [128, 2048], both multiples of 32; particle count log-uniform in
     [1e3, 5e5], capped at a 2D area fraction of 0.25 in the particle region;
-    step count log-uniform in [100, 5000]; FP16 or FP32 storage with p = 1/2."""
+    step count log-uniform in [100, 5000]; FP16 or FP32 storage with p = 1/2;
+    every bed runs the Smagorinsky model (Eq. 13-15) with C_s = 0.1, since
+    tau is within 2e-3 of 1/2 in both templates."""
     import numpy as np
     from paper_1303_2653_gb300 import workloads as W
     rng = np.random.default_rng(seed)
@@ -399,12 +421,12 @@ def serving_requests(count, rate, seed=1303004):
             area = math.pi * (0.5 * 54e-6 / h) ** 2
             n = min(n, int(0.25 * nx * ny / area))
             w = W.riser2d(nx=nx, ny=ny, n_particles=n, seed=1303100 + i, storage=storage, h=h,
-                          steps=steps)
+                          steps=steps, cs_smag=0.1)
         else:
             area = math.pi * (0.5 * 0.5e-3 / 2e-3) ** 2
             n = min(n, int(0.25 * 0.4 * nx * ny / area))
             w = W.bubbling2d(nx=nx, ny=ny, n_particles=n, seed=1303100 + i, storage=storage,
-                             steps=steps)
+                             steps=steps, cs_smag=0.1)
         reqs.append((float(t[i]), w))
     return reqs
 

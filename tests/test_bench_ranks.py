@@ -1,0 +1,59 @@
+"""Multi-rank logic of bench.py on CPU: world size 2 over gloo.
+
+bench.py runs one independent bed per rank (replicas, weak scaling): the
+job time is the maximum over ranks and the value counts the cell updates of
+every rank.  The reference arm runs on rank 0 only.
+"""
+import io
+import os
+import socket
+import sys
+import contextlib
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    # rank r took (r + 1) * 10 ms: the job time is the slowest rank's
+    t = bench.max_over_ranks((rank + 1) * 10.0, dist, device="cpu")
+    value = bench.whole_job_mlups(world, 1000, 50, t / 1e3)
+    # the reference arm prints on rank 0 only; other ranks return at once
+    buf = io.StringIO()
+    if rank != 0:
+        class A:
+            pass
+        with contextlib.redirect_stdout(buf):
+            bench.reference_main(A(), rank, world)
+    out.put((rank, t, value, buf.getvalue()))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_take_the_max_time_and_count_all_cells():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, t, value, printed in res:
+        assert t == 20.0
+        assert value == pytest.approx(2 * 1000 * 50 / 0.020 / 1e6)
+        assert printed == ""

@@ -72,6 +72,8 @@ def _workloads():
                              seed=5),
         "riser3d": W.scaled_riser3d(nx=16, ny=16, nz=32, n_particles=1500, solid_fraction=0.08,
                                     sigma_v=0.4),
+        "riser3d_les": W.scaled_riser3d(nx=16, ny=16, nz=32, n_particles=1500, solid_fraction=0.08,
+                                        sigma_v=0.4, cs_smag=0.15, seed=78),
     }
 
 
@@ -152,7 +154,8 @@ def _particle_compare(bed, ob, storage, steps=1):
     return Pg, vg, Po, vo, fd_g, fd_o, kappa_cell
 
 
-@pytest.mark.parametrize("name", ["riser2d", "riser2d_les", "bubbling2d", "dense2d", "riser3d"])
+@pytest.mark.parametrize("name", ["riser2d", "riser2d_les", "bubbling2d", "dense2d", "riser3d",
+                                  "riser3d_les"])
 @pytest.mark.parametrize("storage", [W.STORE_F64, W.STORE_F32])
 def test_one_step_parity(name, storage):
     w = _workloads()[name]
