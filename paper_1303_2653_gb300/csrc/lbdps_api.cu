@@ -195,15 +195,21 @@ template <class L, class Real, class S> struct EngineT : Engine {
     double *red_partials = nullptr, *red_out = nullptr;
     unsigned long long *npairs_dev = nullptr;
     StepParams<Real> sp{};
+    PopLayout lay{};          // extended lattice of the population arrays
 
     explicit EngineT(lbdps *h) : H(h) {}
+    size_t pop_slots() const { return (size_t)Q * (size_t)lay.nce; }
 
     int allocate(DeviceAlloc &A) override
     {
         const size_t nc = (size_t)H->ncell, np = (size_t)std::max(H->np, 1);
         auto get = [&](size_t bytes) { return A.get(bytes); };
+        lay = make_layout(D, H->n);
+        if (lay.nce >= (1ll << 31))
+            return fail(LBDPS_ERR_CAPACITY, "lattice too large: %lld slots per direction (limit 2^31)",
+                        lay.nce);
         for (int b = 0; b < 2; ++b) {
-            f[b] = (S *)get(sizeof(S) * Q * nc);
+            f[b] = (S *)get(sizeof(S) * pop_slots());
             cl_local[b] = (int *)get(sizeof(int) * (nc + 1));
             cl_base[b] = (int *)get(sizeof(int) * (cell_tiles(H->ncell) + 1));
             for (int a = 0; a < D; ++a) {
@@ -351,7 +357,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
                                   nullptr, sp.tab, st);
         CHECK_LAUNCH();
         Real u0[3] = {(Real)k.u0[0], (Real)k.u0[1], (Real)k.u0[2]};
-        launch_init_equilibrium<L, Real, S>(H->ncell, u0, f[0], st);
+        launch_init_equilibrium<L, Real, S>(lay, u0, f[0], st);
         CHECK_LAUNCH();
         if (!H->inlet_lat.empty()) {
             std::vector<Real> tmpu(H->inlet_lat.begin(), H->inlet_lat.end());
@@ -421,7 +427,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
         const int a = parity, b = 1 - parity;
         const int np = H->np;
         if (ev) CU(cudaEventRecord(ev[0], st));
-        launch_collide_stream<L, Real, S>(sp, f[a], f[b], cells(a), part[a], fld, st);
+        launch_collide_stream<L, Real, S>(sp, lay, f[a], f[b], cells(a), part[a], fld, st);
         CHECK_LAUNCH();
         if (ev) CU(cudaEventRecord(ev[1], st));
         launch_drag_step<D, Real>(sp, part[a], stage, cells(a), fld, key, counts, diag_fpre,
@@ -611,7 +617,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
         if (cap < total) return fail(LBDPS_ERR_CAPACITY, "need %zu doubles", total);
         double *dev = nullptr;
         CU(cudaMalloc(&dev, sizeof(double) * total));
-        launch_export_populations<L, Real, S>(H->ncell, f[H->parity], dev, H->stream);
+        launch_export_populations<L, Real, S>(lay, H->ncell, f[H->parity], dev, H->stream);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(out, dev, sizeof(double) * total, cudaMemcpyDeviceToHost, H->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(H->stream);
@@ -628,7 +634,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
         CU(cudaMalloc(&dev, sizeof(double) * total));
         cudaError_t e = cudaMemcpyAsync(dev, in, sizeof(double) * total, cudaMemcpyHostToDevice, H->stream);
         if (e == cudaSuccess) {
-            launch_import_populations<L, Real, S>(H->ncell, dev, f[H->parity], H->stream);
+            launch_import_populations<L, Real, S>(lay, H->ncell, dev, f[H->parity], H->stream);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(H->stream);
@@ -683,8 +689,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
     {
         const int cur = H->parity;
         const bool bed = H->prm.diagnostics && H->steps > 0;
-        launch_reduce_state<L, Real, S>(H->ncell, f[cur], part[cur], H->k.mp, H->np, red_partials,
-                                        red_out, H->stream);
+        launch_reduce_state<L, Real, S>(lay, H->ncell, f[cur], part[cur], H->k.mp, H->np,
+                                        red_partials, red_out, H->stream);
         CHECK_LAUNCH();
         launch_reduce_voidage<Real>(H->ncell, cells(cur), sp.tab.eps_g, H->ntab, red_partials,
                                     red_out + 7, H->stream);
@@ -728,7 +734,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
     size_t checkpoint_bytes() const override
     {
         const size_t nc = (size_t)H->ncell, np = (size_t)H->np;
-        return sizeof(S) * Q * nc + (sizeof(double) + 2 * sizeof(Real)) * D * np +
+        return sizeof(S) * pop_slots() + (sizeof(double) + 2 * sizeof(Real)) * D * np +
                2 * sizeof(int) * np + sizeof(int) * (nc + 1) +
                sizeof(int) * (cell_tiles(H->ncell) + 1);
     }
@@ -739,8 +745,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
         const size_t nc = (size_t)H->ncell, np = (size_t)H->np;
         const int cur = H->parity;
         size_t o = 0;
-        CU(cudaMemcpyAsync(buf + o, f[cur], sizeof(S) * Q * nc, cudaMemcpyDeviceToHost, st));
-        o += sizeof(S) * Q * nc;
+        CU(cudaMemcpyAsync(buf + o, f[cur], sizeof(S) * pop_slots(), cudaMemcpyDeviceToHost, st));
+        o += sizeof(S) * pop_slots();
         for (int a = 0; a < D; ++a) {
             CU(cudaMemcpyAsync(buf + o, part[cur].P[a], sizeof(double) * np, cudaMemcpyDeviceToHost, st));
             o += sizeof(double) * np;
@@ -767,8 +773,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
         const size_t nc = (size_t)H->ncell, np = (size_t)H->np;
         const int cur = H->parity;
         size_t o = 0;
-        CU(cudaMemcpyAsync(f[cur], buf + o, sizeof(S) * Q * nc, cudaMemcpyHostToDevice, st));
-        o += sizeof(S) * Q * nc;
+        CU(cudaMemcpyAsync(f[cur], buf + o, sizeof(S) * pop_slots(), cudaMemcpyHostToDevice, st));
+        o += sizeof(S) * pop_slots();
         for (int a = 0; a < D; ++a) {
             CU(cudaMemcpyAsync(part[cur].P[a], buf + o, sizeof(double) * np, cudaMemcpyHostToDevice, st));
             o += sizeof(double) * np;

@@ -143,6 +143,52 @@ template <class Real> struct StepParams {
     unsigned *health;
 };
 
+// Layout of the population arrays: the lattice plus one ghost layer on every
+// face (x = -1 and n0, y = -1 and n1, and in 3D z = -1 and n2), rows padded to
+// a multiple of 32 slots with x = 0 at offset 32, so that the cells of a row
+// start a 128-byte line in FP32.  Direction i occupies nce consecutive slots.
+// The populations are stored after the collision and pulled by the next one:
+// f_i(x) is read at x - c_i, which is a ghost slot for directions entering
+// through a face.
+struct PopLayout {
+    static constexpr int pad = 32;
+    int n[3];
+    int s0, s1;        // row and plane strides of the extended lattice
+    int zo;            // 1 in 3D (one ghost plane below z = 0), 0 in 2D
+    long long nce;     // slots per direction
+    // slots of one direction are indexed in 32 bits (nce < 2^31, checked at
+    // creation)
+    __host__ __device__ int ext(const int *q) const
+    {
+        return pad + q[0] + s0 * ((q[1] + 1) + s1 * (q[2] + zo));
+    }
+    template <class L> __host__ __device__ int off(int i) const
+    {
+        return L::c(i, 0) + L::c(i, 1) * s0 + L::c(i, 2) * s0 * s1;
+    }
+};
+
+// Per-direction base pointers of the population arrays for one collision:
+// direction i of the cell at extended slot xe is read at pull[i][xe]
+// (pull[i] = fin + i nce - off_i, the slot of x - c_i) and the cell's own
+// post-collision value is written at own[i][xe] (own[i] = fout + i nce).
+template <class S> struct PopPtrs {
+    const S *pull[19];
+    S *own[19];
+};
+
+inline PopLayout make_layout(int dim, const int *n)
+{
+    PopLayout l;
+    for (int a = 0; a < 3; ++a) l.n[a] = n[a];
+    l.s0 = ((n[0] + 2 + 31) / 32) * 32;
+    l.s1 = n[1] + 2;
+    l.zo = dim == 3 ? 1 : 0;
+    const long long s2 = dim == 3 ? n[2] + 2 : 1;
+    l.nce = (long long)l.s0 * l.s1 * s2 + PopLayout::pad;
+    return l;
+}
+
 // Device buffers of one bed.
 template <class Real> struct Fields {
     Real *rho, *uact[3], *fpg[3], *beta, *solg;         // node outputs of the collision
@@ -186,17 +232,19 @@ struct CellListOut {
 inline int cell_tiles(int ncell) { return (ncell + 1 + kCellTile - 1) / kCellTile; }
 
 template <class L, class Real, class S>
-void launch_collide_stream(const StepParams<Real> &p, const S *fin, S *fout, CellList cells,
-                           Particles<Real> parts, Fields<Real> fld, cudaStream_t st);
+void launch_collide_stream(const StepParams<Real> &p, const PopLayout &lay, const S *fin, S *fout,
+                           CellList cells, Particles<Real> parts, Fields<Real> fld, cudaStream_t st);
 
 template <class L, class Real, class S>
-void launch_init_equilibrium(int ncell, const Real *u0, S *f, cudaStream_t st);
+void launch_init_equilibrium(const PopLayout &lay, const Real *u0, S *f, cudaStream_t st);
 
 template <class L, class Real, class S>
-void launch_export_populations(int ncell, const S *f, double *out, cudaStream_t st);
+void launch_export_populations(const PopLayout &lay, int ncell, const S *f, double *out,
+                               cudaStream_t st);
 
 template <class L, class Real, class S>
-void launch_import_populations(int ncell, const double *in, S *f, cudaStream_t st);
+void launch_import_populations(const PopLayout &lay, int ncell, const double *in, S *f,
+                               cudaStream_t st);
 
 template <class Real>
 void launch_build_tables(int dim, double tau, double r, double vp, double d, double mu,
@@ -237,7 +285,8 @@ void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int 
                     const int *wall, int np, cudaStream_t st);
 
 template <class L, class Real, class S>
-void launch_reduce_state(int ncell, const S *f, Particles<Real> parts, double mp, int np,
+void launch_reduce_state(const PopLayout &lay, int ncell, const S *f, Particles<Real> parts,
+                         double mp, int np,
                          double *partials, double *out, cudaStream_t st);
 
 template <class Real>

@@ -155,41 +155,140 @@ template <> struct K2Occupancy<D2Q9, float> { static constexpr int value = LBDPS
 template <> struct K2Occupancy<D3Q19, float> { static constexpr int value = LBDPS_K2_BLOCKS_D3Q19_F32; };
 template <> struct K2Occupancy<D3Q19, double> { static constexpr int value = 2; };
 
-// Store one post-collision population of direction I: to the neighbour, or
-// reflected into this cell's opposite slot by a wall (half-way bounce-back
-// with the moving-wall term -6 w_i rho c_i.u_w of the first wall crossed), or
-// dropped through an inlet/outlet face.
+// Streaming across the faces of the lattice (Eq. 2 with the boundary rules),
+// run by the cells on a face after their own post-collision values are
+// stored.  Populations are pulled: the next collision of cell x reads
+// direction i at x - c_i of the extended lattice.  A slot of the ghost layer
+// is written by the one rule that feeds its reader:
+//   a direction leaving through a wall returns to this cell as -c_i
+//   (half-way bounce-back, moving-wall term -6 w_i rho c_i.u_w of the first
+//   wall crossed): written where this cell pulls -c_i from;
+//   a direction leaving through periodic faces only re-enters at the image
+//   cell: written where the image pulls it from;
+//   a direction leaving through an inlet or outlet is dropped, and the
+//   direction entering through it (no wall crossed) is set to
+//   feq(1, u_in) or feq(1, u of this cell).
 template <class L, class Real, class S>
-__device__ __forceinline__ void emit_population(int I, const StepParams<Real> &p, S *__restrict__ fout,
-                                                size_t nc, int x, Real post, Real rho, bool on_face,
-                                                int wall_mask, int open_mask, int offp0, int offm0,
-                                                int offp1, int offm1, int offp2, int offm2)
+__device__ __forceinline__ void face_streaming(const StepParams<Real> &p, const PopLayout &lay,
+                                               const PopPtrs<S> &pp, int xe, const int *idx,
+                                               Real rho, const Real *u)
 {
-    const int cx = L::c(I, 0), cy = L::c(I, 1), cz = L::c(I, 2);
-    const int off = (cx == 1 ? offp0 : cx == -1 ? offm0 : 0) + (cy == 1 ? offp1 : cy == -1 ? offm1 : 0) +
-                    (cz == 1 ? offp2 : cz == -1 ? offm2 : 0);
-    if (!on_face) {
-        fout[(size_t)I * nc + (x + off)] = Store<S>::save(post);
-        return;
+    constexpr int D = L::D, Q = L::Q;
+    int wall_faces = 0, open_faces = 0;
+#pragma unroll
+    for (int f6 = 0; f6 < 2 * D; ++f6) {
+        if (p.bc[f6] == BC_WALL) wall_faces |= 1 << f6;
+        else if (p.bc[f6] != BC_PERIODIC) open_faces |= 1 << f6;
     }
-    // faces crossed by this direction, as bits of the masks
-    const int crossed = (cx == 1 ? 2 : cx == -1 ? 1 : 0) | (cy == 1 ? 8 : cy == -1 ? 4 : 0) |
-                            (cz == 1 ? 32 : cz == -1 ? 16 : 0);
-    const int walls = wall_mask & crossed;
-    if (walls) {
-        const int face = __ffs(walls) - 1;   // first (lowest-axis) wall crossed
-        const Real cw = Real(cx) * p.wall_u[face][0] + Real(cy) * p.wall_u[face][1] +
-                        Real(cz) * p.wall_u[face][2];
-        fout[(size_t)L::opp(I) * nc + x] = Store<S>::save(post - Real(6) * Real(L::w(I)) * rho * cw);
-    } else if (!(open_mask & crossed)) {
-        fout[(size_t)I * nc + (x + off)] = Store<S>::save(post);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        int out = 0, in = 0;   // faces crossed by x + c_i and by x - c_i
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int c = L::c(i, a);
+            const bool lo = idx[a] == 0, hi = idx[a] == p.n[a] - 1;
+            if (c == 1) {
+                if (hi) out |= 2 << (2 * a);
+                if (lo) in |= 1 << (2 * a);
+            } else if (c == -1) {
+                if (lo) out |= 1 << (2 * a);
+                if (hi) in |= 2 << (2 * a);
+            }
+        }
+        const int off = lay.off<L>(i);
+        if (out) {
+            const Real post = Store<S>::load(pp.own[i][xe]);
+            const int walls = out & wall_faces;
+            if (walls) {
+                const int face = __ffs(walls) - 1;   // first (lowest-axis) wall crossed
+                const Real cw = Real(L::c(i, 0)) * p.wall_u[face][0] +
+                                Real(L::c(i, 1)) * p.wall_u[face][1] +
+                                Real(L::c(i, 2)) * p.wall_u[face][2];
+                pp.own[L::opp(i)][xe + off] = Store<S>::save(post - Real(6) * Real(L::w(i)) * rho * cw);
+            } else if (!(out & open_faces)) {
+                int q[3] = {idx[0], idx[1], idx[2]};
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    q[a] += L::c(i, a);
+                    if (q[a] < 0) q[a] += p.n[a];
+                    else if (q[a] >= p.n[a]) q[a] -= p.n[a];
+                }
+                pp.own[i][lay.ext(q) - off] = Store<S>::save(post);
+            }
+        }
+        if (in && !(in & wall_faces) && (in & open_faces)) {
+            const int open = __ffs(in & open_faces) - 1;
+            Real ub[3] = {Real(0), Real(0), Real(0)};
+            if (p.bc[open] == BC_INLET) {
+                const int j = (D == 2) ? idx[0] : idx[0] + p.n[0] * idx[1];
+#pragma unroll
+                for (int a = 0; a < D; ++a) ub[a] = p.inlet_u[j * D + a];
+            } else {
+#pragma unroll
+                for (int a = 0; a < D; ++a) ub[a] = u[a];
+            }
+            Real cu = cdot<L>(i, ub), ubb = Real(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) ubb += ub[a] * ub[a];
+            pp.own[i][xe - off] =
+                Store<S>::save(Real(L::w(i)) * (Real(3) * cu + Real(4.5) * cu * cu - Real(1.5) * ubb));
+        }
+    }
+}
+
+// The same rules for a cell on an x face only (off every y and z face): just
+// the directions that cross its x face, known at compile time per side, so
+// that a warp holding one such cell pays a few stores instead of the
+// general per-direction face test.
+template <class L, class Real, class S, int SIDE>
+__device__ __forceinline__ void face_streaming_x(const StepParams<Real> &p, const PopLayout &lay,
+                                                 const PopPtrs<S> &pp, int xe, const int *idx,
+                                                 Real rho, const Real *u)
+{
+    constexpr int D = L::D, Q = L::Q;
+    constexpr int f6 = SIDE < 0 ? 0 : 1;   // the low or high x face
+    const int bc = p.bc[f6];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (L::c(i, 0) != SIDE) continue;   // leaves through this face
+        const int off = lay.off<L>(i);
+        const Real post = Store<S>::load(pp.own[i][xe]);
+        if (bc == BC_WALL) {
+            const Real cw = Real(L::c(i, 0)) * p.wall_u[f6][0] + Real(L::c(i, 1)) * p.wall_u[f6][1] +
+                            Real(L::c(i, 2)) * p.wall_u[f6][2];
+            pp.own[L::opp(i)][xe + off] = Store<S>::save(post - Real(6) * Real(L::w(i)) * rho * cw);
+        } else if (bc == BC_PERIODIC) {
+            int q[3] = {idx[0] + L::c(i, 0) - SIDE * p.n[0], idx[1] + L::c(i, 1), idx[2] + L::c(i, 2)};
+            pp.own[i][lay.ext(q) - off] = Store<S>::save(post);
+        }
+    }
+    if (bc == BC_WALL || bc == BC_PERIODIC) return;
+    // inlet or outlet on this face: the directions entering through it
+    Real ub[3] = {Real(0), Real(0), Real(0)};
+    if (bc == BC_INLET) {
+        const int j = (D == 2) ? idx[0] : idx[0] + p.n[0] * idx[1];
+#pragma unroll
+        for (int a = 0; a < D; ++a) ub[a] = p.inlet_u[j * D + a];
+    } else {
+#pragma unroll
+        for (int a = 0; a < D; ++a) ub[a] = u[a];
+    }
+    Real ubb = Real(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) ubb += ub[a] * ub[a];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (L::c(i, 0) != -SIDE) continue;
+        const Real cu = cdot<L>(i, ub);
+        pp.own[i][xe - lay.off<L>(i)] =
+            Store<S>::save(Real(L::w(i)) * (Real(3) * cu + Real(4.5) * cu * cu - Real(1.5) * ubb));
     }
 }
 
 template <class L, class Real, class S, bool LES, bool FB>
 __global__ void __launch_bounds__(256, K2Occupancy<L, Real>::value)
-k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ fout,
-                 CellList cells, Particles<Real> parts, Fields<Real> fld)
+k_collide_stream(StepParams<Real> p, PopLayout lay, PopPtrs<S> pp, CellList cells,
+                 Particles<Real> parts, Fields<Real> fld)
 {
     constexpr int D = L::D, Q = L::Q;
     // grid: x along blockIdx.x/threadIdx.x, y = blockIdx.y, z = blockIdx.z
@@ -199,11 +298,12 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
     idx[2] = blockIdx.z;
     if (idx[0] >= p.n[0]) return;
     const int x = idx[0] + p.n[0] * (idx[1] + p.n[1] * idx[2]);
-    const size_t nc = (size_t)p.ncell;
+    const int xe = lay.ext(idx);
 
+    // pull: population i of this step left x - c_i in the last one
     Real f[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = Store<S>::load(fin[(size_t)i * nc + x]);
+    for (int i = 0; i < Q; ++i) f[i] = Store<S>::load(__ldg(pp.pull[i] + xe));
 
     // ---- deposition (Eq. 8) ----
     const int s0 = cells.begin(x), s1 = cells.begin(x + 1);
@@ -318,43 +418,14 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
 #pragma unroll
     for (int a = 0; a < D; ++a) uF += u[a] * p.fb[a];
 
-    // ---- streaming geometry of this cell (Eq. 2, push) ----
-    // offp/offm: linear offset to the +/- neighbour along each axis with
-    // periodic wrap folded in; bit 2a (2a+1) of wall_mask / open_mask: the
-    // low (high) face of this cell along axis a is a wall / an inlet-outlet.
-    int offp0 = 1, offm0 = -1, offp1 = p.n[0], offm1 = -p.n[0];
-    int offp2 = p.n[0] * p.n[1], offm2 = -p.n[0] * p.n[1];
-    int wall_mask = 0, open_mask = 0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        const int st = a == 0 ? 1 : (a == 1 ? p.n[0] : p.n[0] * p.n[1]);
-        int op = st, om = -st;
-        if (idx[a] == p.n[a] - 1) {
-            const int bc = p.bc[2 * a + 1];
-            if (bc == BC_PERIODIC) op = -(p.n[a] - 1) * st;
-            else if (bc == BC_WALL) wall_mask |= 1 << (2 * a + 1);
-            else open_mask |= 1 << (2 * a + 1);
-        }
-        if (idx[a] == 0) {
-            const int bc = p.bc[2 * a];
-            if (bc == BC_PERIODIC) om = (p.n[a] - 1) * st;
-            else if (bc == BC_WALL) wall_mask |= 1 << (2 * a);
-            else open_mask |= 1 << (2 * a);
-        }
-        if (a == 0) { offp0 = op; offm0 = om; }
-        else if (a == 1) { offp1 = op; offm1 = om; }
-        else { offp2 = op; offm2 = om; }
-    }
-    const bool on_face = (wall_mask | open_mask) != 0;
-#define LBDPS_EMIT(I, POST)                                                                        \
-    emit_population<L, Real, S>((I), p, fout, nc, x, (POST), rho, on_face, wall_mask, open_mask,  \
-                                      offp0, offm0, offp1, offm1, offp2, offm2)
+    // ---- collision (Eq. 7, 23); each post-collision value is stored in this
+    // cell's own slot of the extended lattice (aligned, no face logic) ----
     {
         // rest population: cu = cv = 0
         const Real w = Real(L::w(0));
         Real post = f[0] - relax * (f[0] - w * eq0) + og * w * (es0 - eq0);
         if (FB) post -= pref * w * Real(3) * uF;
-        LBDPS_EMIT(0, post);
+        pp.own[0][xe] = Store<S>::save(post);
     }
     const Real r3 = Real(3) * rho, r45 = Real(4.5) * rho;
 #pragma unroll
@@ -376,11 +447,9 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
             post_i += even + odd;
             post_o += even - odd;
         }
-        LBDPS_EMIT(i, post_i);
-        LBDPS_EMIT(io, post_o);
+        pp.own[i][xe] = Store<S>::save(post_i);
+        pp.own[io][xe] = Store<S>::save(post_o);
     }
-
-#undef LBDPS_EMIT
 
     if (fld.ntot) {
         fld.ntot[x] = n;
@@ -394,66 +463,51 @@ k_collide_stream(StepParams<Real> p, const S *__restrict__ fin, S *__restrict__ 
     }
     if (!(rho > Real(0)) || !(uu < Real(0.09))) atomicOr(p.health, HEALTH_DIVERGED);
 
-    // ---- populations entering through an inlet or outlet face ----
-    if (open_mask == 0) return;
+    // ---- streaming across the faces of the lattice ----
+    bool yz_face = false;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        int wall = -1, open = -1;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const int q = idx[a] - L::c(i, a);
-            if (q < 0 || q >= p.n[a]) {
-                const int face = 2 * a + (q < 0 ? 0 : 1);
-                const int bc = p.bc[face];
-                if (bc == BC_WALL) { if (wall < 0) wall = face; }
-                else if (bc != BC_PERIODIC) { if (open < 0) open = face; }
-            }
-        }
-        if (wall < 0 && open >= 0) {
-            Real ub[3] = {Real(0), Real(0), Real(0)};
-            if (p.bc[open] == BC_INLET) {
-                const int j = (D == 2) ? idx[0] : idx[0] + p.n[0] * idx[1];
-#pragma unroll
-                for (int a = 0; a < D; ++a) ub[a] = p.inlet_u[j * D + a];
-            } else {
-#pragma unroll
-                for (int a = 0; a < D; ++a) ub[a] = u[a];
-            }
-            Real cu = cdot<L>(i, ub), ubb = Real(0);
-#pragma unroll
-            for (int a = 0; a < D; ++a) ubb += ub[a] * ub[a];
-            fout[(size_t)i * nc + x] =
-                Store<S>::save(Real(L::w(i)) * (Real(3) * cu + Real(4.5) * cu * cu - Real(1.5) * ubb));
-        }
-    }
+    for (int a = 1; a < D; ++a) yz_face = yz_face || idx[a] == 0 || idx[a] == p.n[a] - 1;
+    const bool xlo = idx[0] == 0, xhi = idx[0] == p.n[0] - 1;
+    if (yz_face || (xlo && xhi)) face_streaming<L, Real, S>(p, lay, pp, xe, idx, rho, u);
+    else if (xlo) face_streaming_x<L, Real, S, -1>(p, lay, pp, xe, idx, rho, u);
+    else if (xhi) face_streaming_x<L, Real, S, 1>(p, lay, pp, xe, idx, rho, u);
 }
 
 template <class L, class Real, class S>
-void launch_collide_stream(const StepParams<Real> &p, const S *fin, S *fout, CellList cells,
-                           Particles<Real> parts, Fields<Real> fld, cudaStream_t st)
+void launch_collide_stream(const StepParams<Real> &p, const PopLayout &lay, const S *fin, S *fout,
+                           CellList cells, Particles<Real> parts, Fields<Real> fld, cudaStream_t st)
 {
+    PopPtrs<S> pp{};
+    for (int i = 0; i < L::Q; ++i) {
+        pp.pull[i] = fin + (long long)i * lay.nce - lay.off<L>(i);
+        pp.own[i] = fout + (long long)i * lay.nce;
+    }
     // one block row per lattice row; up to 256 threads along x
     const int tx = p.n[0] >= 256 ? 256 : ((p.n[0] + 31) / 32) * 32;
     const dim3 grid((p.n[0] + tx - 1) / tx, p.n[1], L::D == 3 ? p.n[2] : 1);
     const bool les = p.les_k > Real(0), fb = p.has_fb != 0;
     if (les && fb)
-        k_collide_stream<L, Real, S, true, true><<<grid, tx, 0, st>>>(p, fin, fout, cells, parts, fld);
+        k_collide_stream<L, Real, S, true, true><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
     else if (les)
-        k_collide_stream<L, Real, S, true, false><<<grid, tx, 0, st>>>(p, fin, fout, cells, parts, fld);
+        k_collide_stream<L, Real, S, true, false><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
     else if (fb)
-        k_collide_stream<L, Real, S, false, true><<<grid, tx, 0, st>>>(p, fin, fout, cells, parts, fld);
+        k_collide_stream<L, Real, S, false, true><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
     else
-        k_collide_stream<L, Real, S, false, false><<<grid, tx, 0, st>>>(p, fin, fout, cells, parts, fld);
+        k_collide_stream<L, Real, S, false, false><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
 }
 
 // ---------------------------------------------------------------------------
-// Equilibrium initialisation and population import/export (full values in FP64).
+// Equilibrium initialisation and population import/export (full values in
+// FP64, cell-major per direction: index i * ncell + x).  The stored slot of
+// population i of cell x is ext(x) - c_i (the value the next collision
+// pulls).
 // ---------------------------------------------------------------------------
 template <class L, class Real, class S>
-__global__ void k_init_equilibrium(int ncell, Real u0x, Real u0y, Real u0z, S *f)
+__global__ void k_init_equilibrium(long long nce, Real u0x, Real u0y, Real u0z, S *f)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= ncell) return;
+    // a uniform state: every slot of direction i holds the same deviation
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nce) return;
     const double u[3] = {(double)u0x, (double)u0y, (double)u0z};
     double uu = 0.0;
     for (int a = 0; a < L::D; ++a) uu += u[a] * u[a];
@@ -462,57 +516,76 @@ __global__ void k_init_equilibrium(int ncell, Real u0x, Real u0y, Real u0z, S *f
         double cu = 0.0;
         for (int a = 0; a < L::D; ++a) cu += (double)L::c(i, a) * u[a];
         double dev = L::w(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-        f[(size_t)i * ncell + x] = Store<S>::save((Real)dev);
+        f[(long long)i * nce + k] = Store<S>::save((Real)dev);
     }
 }
 
 template <class L, class Real, class S>
-void launch_init_equilibrium(int ncell, const Real *u0, S *f, cudaStream_t st)
+void launch_init_equilibrium(const PopLayout &lay, const Real *u0, S *f, cudaStream_t st)
 {
-    k_init_equilibrium<L, Real, S><<<(ncell + 255) / 256, 256, 0, st>>>(ncell, u0[0], u0[1], u0[2], f);
+    k_init_equilibrium<L, Real, S><<<(unsigned)((lay.nce + 255) / 256), 256, 0, st>>>(
+        lay.nce, u0[0], u0[1], u0[2], f);
+}
+
+template <class L>
+__device__ __forceinline__ long long pop_slot(const PopLayout &lay, int i, int x)
+{
+    int q[3];
+    q[0] = x % lay.n[0];
+    q[1] = (x / lay.n[0]) % lay.n[1];
+    q[2] = x / (lay.n[0] * lay.n[1]);
+    return (long long)i * lay.nce + lay.ext(q) - lay.off<L>(i);
 }
 
 template <class L, class Real, class S>
-__global__ void k_export_populations(int ncell, const S *f, double *out)
+__global__ void k_export_populations(PopLayout lay, int ncell, const S *f, double *out)
 {
-    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (size_t)L::Q * ncell) return;
-    const int i = (int)(k / ncell);
-    out[k] = L::w(i) + (double)Store<S>::load(f[k]);
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)L::Q * ncell) return;
+    const int i = (int)(k / ncell), x = (int)(k % ncell);
+    out[k] = L::w(i) + (double)Store<S>::load(f[pop_slot<L>(lay, i, x)]);
 }
 
 template <class L, class Real, class S>
-void launch_export_populations(int ncell, const S *f, double *out, cudaStream_t st)
+void launch_export_populations(const PopLayout &lay, int ncell, const S *f, double *out,
+                               cudaStream_t st)
 {
-    size_t total = (size_t)L::Q * ncell;
-    k_export_populations<L, Real, S><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(ncell, f, out);
+    const long long total = (long long)L::Q * ncell;
+    k_export_populations<L, Real, S><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(lay, ncell, f,
+                                                                                       out);
 }
 
 template <class L, class Real, class S>
-__global__ void k_import_populations(int ncell, const double *in, S *f)
+__global__ void k_import_populations(PopLayout lay, int ncell, const double *in, S *f)
 {
-    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (size_t)L::Q * ncell) return;
-    const int i = (int)(k / ncell);
-    f[k] = Store<S>::save((Real)(in[k] - L::w(i)));
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)L::Q * ncell) return;
+    const int i = (int)(k / ncell), x = (int)(k % ncell);
+    f[pop_slot<L>(lay, i, x)] = Store<S>::save((Real)(in[k] - L::w(i)));
 }
 
 template <class L, class Real, class S>
-void launch_import_populations(int ncell, const double *in, S *f, cudaStream_t st)
+void launch_import_populations(const PopLayout &lay, int ncell, const double *in, S *f,
+                               cudaStream_t st)
 {
-    size_t total = (size_t)L::Q * ncell;
-    k_import_populations<L, Real, S><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(ncell, in, f);
+    const long long total = (long long)L::Q * ncell;
+    k_import_populations<L, Real, S><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(lay, ncell, in,
+                                                                                       f);
 }
 
 // ---------------------------------------------------------------------------
 // Explicit instantiations: (lattice, arithmetic, storage).
 // ---------------------------------------------------------------------------
 #define LBDPS_INST_LBM(L, R, S)                                                                    \
-    template void launch_collide_stream<L, R, S>(const StepParams<R> &, const S *, S *,            \
-                                                 CellList, Particles<R>, Fields<R>, cudaStream_t);  \
-    template void launch_init_equilibrium<L, R, S>(int, const R *, S *, cudaStream_t);             \
-    template void launch_export_populations<L, R, S>(int, const S *, double *, cudaStream_t);      \
-    template void launch_import_populations<L, R, S>(int, const double *, S *, cudaStream_t);
+    template void launch_collide_stream<L, R, S>(const StepParams<R> &, const PopLayout &,         \
+                                                 const S *, S *, CellList, Particles<R>, Fields<R>, \
+                                                 cudaStream_t);                                     \
+    template void launch_init_equilibrium<L, R, S>(const PopLayout &, const R *, S *,               \
+                                                   cudaStream_t);                                   \
+    template void launch_export_populations<L, R, S>(const PopLayout &, int, const S *, double *,   \
+                                                     cudaStream_t);                                 \
+    template void launch_import_populations<L, R, S>(const PopLayout &, int, const double *, S *,   \
+                                                     cudaStream_t);
 
 LBDPS_INST_LBM(D2Q9, double, double)
 LBDPS_INST_LBM(D2Q9, float, float)

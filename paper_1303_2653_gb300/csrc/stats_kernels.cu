@@ -44,14 +44,22 @@ __global__ void k_reduce_final(const double *partials, int nb, int nv, double *o
 // values: [0] sum of deviations f_i - w_i, [1..3] sum c_i f_i, [4..6] m_p sum v
 template <class L, class Real, class S>
 __global__ void __launch_bounds__(kRedThreads)
-k_reduce_state(int ncell, const S *f, Particles<Real> parts, double mp, int np, double *partials)
+k_reduce_state(PopLayout lay, int ncell, const S *f, Particles<Real> parts, double mp, int np,
+               double *partials)
 {
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     const int stride = gridDim.x * blockDim.x;
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < ncell; x += stride) {
+        int q[3];
+        q[0] = x % lay.n[0];
+        q[1] = (x / lay.n[0]) % lay.n[1];
+        q[2] = x / (lay.n[0] * lay.n[1]);
+        const long long xe = lay.ext(q);
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
-            const double fi = (double)Store<S>::load(f[(size_t)i * ncell + x]);
+            // population i of cell x as the next collision pulls it
+            const double fi =
+                (double)Store<S>::load(f[(long long)i * lay.nce + xe - lay.off<L>(i)]);
             acc[0] += fi;
 #pragma unroll
             for (int a = 0; a < L::D; ++a) acc[1 + a] += (double)L::c(i, a) * fi;
@@ -65,11 +73,11 @@ k_reduce_state(int ncell, const S *f, Particles<Real> parts, double mp, int np, 
 }
 
 template <class L, class Real, class S>
-void launch_reduce_state(int ncell, const S *f, Particles<Real> parts, double mp, int np,
-                         double *partials, double *out, cudaStream_t st)
+void launch_reduce_state(const PopLayout &lay, int ncell, const S *f, Particles<Real> parts,
+                         double mp, int np, double *partials, double *out, cudaStream_t st)
 {
     const int nb = reduce_block_count(ncell > np ? ncell : np);
-    k_reduce_state<L, Real, S><<<nb, kRedThreads, 0, st>>>(ncell, f, parts, mp, np, partials);
+    k_reduce_state<L, Real, S><<<nb, kRedThreads, 0, st>>>(lay, ncell, f, parts, mp, np, partials);
     k_reduce_final<<<1, 32, 0, st>>>(partials, nb, 7, out);
 }
 
@@ -136,8 +144,8 @@ template void launch_reduce_voidage<float>(int, CellList, const float *, int, do
                                            cudaStream_t);
 
 #define LBDPS_INST_RED(L, R, S)                                                                   \
-    template void launch_reduce_state<L, R, S>(int, const S *, Particles<R>, double, int,         \
-                                               double *, double *, cudaStream_t);
+    template void launch_reduce_state<L, R, S>(const PopLayout &, int, const S *, Particles<R>,    \
+                                               double, int, double *, double *, cudaStream_t);
 LBDPS_INST_RED(D2Q9, double, double)
 LBDPS_INST_RED(D2Q9, float, float)
 LBDPS_INST_RED(D2Q9, float, __half)
