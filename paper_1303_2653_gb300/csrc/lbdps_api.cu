@@ -193,6 +193,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
     Real *inlet_dev = nullptr;
     unsigned *health_dev = nullptr;
     double *red_partials = nullptr, *red_out = nullptr;
+    unsigned *red_ticket = nullptr;
     unsigned long long *npairs_dev = nullptr;
     StepParams<Real> sp{};
     PopLayout lay{};          // extended lattice of the population arrays
@@ -260,13 +261,14 @@ template <class L, class Real, class S> struct EngineT : Engine {
         const int nface = (int)(H->inlet_lat.size() / D);
         inlet_dev = (Real *)get(sizeof(Real) * D * std::max(nface, 1));
         health_dev = (unsigned *)get(sizeof(unsigned));
-        red_partials = (double *)get(sizeof(double) * 7 * 1024);
+        red_partials = (double *)get(sizeof(double) * 16 * 512);   // values x blocks of the reduction
         red_out = (double *)get(sizeof(double) * 16);
+        red_ticket = (unsigned *)get(sizeof(unsigned));
         npairs_dev = (unsigned long long *)get(sizeof(unsigned long long));
         void *must[] = {f[0], f[1], cl_local[0], cl_local[1], cl_base[0], cl_base[1], fld.rho,
                         fld.beta, fld.solg, key, counts, slot, idslot, tile_total, ticket,
                         best, wall, tab_branch, inlet_dev, health_dev,
-                        red_partials, red_out, npairs_dev, part[0].id, part[1].id,
+                        red_partials, red_out, red_ticket, npairs_dev, part[0].id, part[1].id,
                         part[0].cell, part[1].cell};
         for (void *p : must)
             if (!p) return fail(LBDPS_ERR_OOM, "device allocation failed");
@@ -368,6 +370,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
         CU(cudaMemsetAsync(health_dev, 0, sizeof(unsigned), st));
         CU(cudaMemsetAsync(counts, 0, sizeof(int) * (H->ncell + 1), st));
         CU(cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
+        CU(cudaMemsetAsync(red_ticket, 0, sizeof(unsigned), st));
         if (H->np == 0) {
             int rc = clear_cells(0);
             if (rc == LBDPS_OK) rc = clear_cells(1);
@@ -689,22 +692,12 @@ template <class L, class Real, class S> struct EngineT : Engine {
     {
         const int cur = H->parity;
         const bool bed = H->prm.diagnostics && H->steps > 0;
-        launch_reduce_state<L, Real, S>(lay, H->ncell, f[cur], part[cur], H->k.mp, H->np,
-                                        red_partials, red_out, H->stream);
+        launch_reduce_all<L, Real, S>(lay, H->ncell, f[cur], part[cur], H->k.mp, H->np, cells(cur),
+                                      sp.tab.eps_g, H->ntab, bed ? &fld : nullptr, red_partials,
+                                      red_ticket, red_out, H->stream);
         CHECK_LAUNCH();
-        launch_reduce_voidage<Real>(H->ncell, cells(cur), sp.tab.eps_g, H->ntab, red_partials,
-                                    red_out + 7, H->stream);
-        CHECK_LAUNCH();
-        if (bed) {
-            const Real *ua[3] = {fld.uact[0], fld.uact[1], D > 2 ? fld.uact[2] : nullptr};
-            const Real *va[3] = {fld.vs[0], fld.vs[1], D > 2 ? fld.vs[2] : nullptr};
-            launch_reduce_bed<Real>(H->ncell, D, fld.eps_g, fld.ntot, ua, va, red_partials,
-                                    red_out + 8, H->stream);
-            CHECK_LAUNCH();
-        }
         double *v = H->stats_host;
-        CU(cudaMemcpyAsync(v, red_out, sizeof(double) * (bed ? 11 : 8), cudaMemcpyDeviceToHost,
-                           H->stream));
+        CU(cudaMemcpyAsync(v, red_out, sizeof(double) * 11, cudaMemcpyDeviceToHost, H->stream));
         CU(cudaMemcpyAsync(H->health_host, health_word(), sizeof(unsigned), cudaMemcpyDeviceToHost,
                            H->stream));
         CU(cudaStreamSynchronize(H->stream));

@@ -284,19 +284,14 @@ template <int D, class Real>
 void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int *best,
                     const int *wall, int np, cudaStream_t st);
 
+// All bed statistics in one launch (values listed in stats_kernels.cu); bed
+// = the diagnostic fields or null; ticket must be zero on entry and is zero
+// again on exit.
 template <class L, class Real, class S>
-void launch_reduce_state(const PopLayout &lay, int ncell, const S *f, Particles<Real> parts,
-                         double mp, int np,
-                         double *partials, double *out, cudaStream_t st);
-
-template <class Real>
-void launch_reduce_bed(int ncell, int dim, const Real *eps_g, const int *ntot,
-                       const Real *const *uact, const Real *const *vs, double *partials,
-                       double *out, cudaStream_t st);
-
-template <class Real>
-void launch_reduce_voidage(int ncell, CellList cells, const Real *eps_g_tab, int ntab,
-                           double *partials, double *out, cudaStream_t st);
+void launch_reduce_all(const PopLayout &lay, int ncell, const S *f, Particles<Real> parts, double mp,
+                       int np, CellList cells, const Real *eps_tab, int ntab,
+                       const Fields<Real> *bed, double *partials, unsigned *ticket, double *out,
+                       cudaStream_t st);
 
 int reduce_block_count(int n);
 

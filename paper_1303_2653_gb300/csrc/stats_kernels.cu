@@ -1,7 +1,12 @@
-// Deterministic FP64 reductions of a bed: gas mass and momentum, particle
-// momentum, lattice-mean voidage and particle-weighted slip.  A fixed grid
-// with grid-stride loops, a fixed shared-memory tree per block, then one
-// block summing the block partials in order: the result does not depend on
+// Bed statistics in one launch: gas mass and momentum, particle momentum,
+// lattice-mean voidage of the current positions, and (with diagnostics) the
+// voidage and particle-weighted slip of the last collision.
+//
+// Each thread accumulates over a grid-stride range of cells and particles (in
+// FP64 in the FP64 engine; in FP32 with Kahan compensation otherwise, since
+// FP64 arithmetic is slow on this part), the blocks reduce in a fixed order
+// to FP64 partials, and the block that finishes last (ticket counter, nothing
+// waits) sums the partials in a fixed tree.  The result does not depend on
 // scheduling.
 #include "lbdps_internal.cuh"
 
@@ -10,142 +15,146 @@ namespace lbdpsk {
 constexpr int kRedThreads = 256;
 constexpr int kRedMaxBlocks = 512;
 
-int reduce_block_count(int n)
-{
-    int b = (n + kRedThreads * 4 - 1) / (kRedThreads * 4);
-    return b < 1 ? 1 : (b > kRedMaxBlocks ? kRedMaxBlocks : b);
-}
-
-template <int NV>
-__device__ void block_sum_write(double (&acc)[NV], double *partials)
-{
-    __shared__ double sh[kRedThreads];
-    for (int k = 0; k < NV; ++k) {
-        sh[threadIdx.x] = acc[k];
-        __syncthreads();
-        for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) partials[blockIdx.x * NV + k] = sh[0];
-        __syncthreads();
-    }
-}
-
-__global__ void k_reduce_final(const double *partials, int nb, int nv, double *out)
-{
-    const int k = threadIdx.x;
-    if (k >= nv) return;
+template <class Real> struct Acc;
+template <> struct Acc<double> {
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += partials[b * nv + k];
-    out[k] = s;
+    __device__ void add(double x) { s += x; }
+    __device__ double get() const { return s; }
+};
+// Kahan-compensated FP32 sum (Kahan 1965)
+template <> struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ double get() const { return (double)s - (double)c; }
+};
+
+// Block sum of v in a fixed order (warp shuffles, then the warp totals);
+// the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kRedThreads / 32; ++w) t += sh[w];
+    return t;
 }
 
-// values: [0] sum of deviations f_i - w_i, [1..3] sum c_i f_i, [4..6] m_p sum v
-template <class L, class Real, class S>
+// out: [0] sum of deviations f_i - w_i, [1..3] sum c_i f_i, [4..6] m_p sum v,
+// [7] sum of eps_g of the current counts, [8] sum of the diagnostic eps_g,
+// [9] sum n |u_act - v_s|, [10] sum n
+constexpr int kStatValues = 11;
+
+template <class L, class Real, class S, bool BED>
 __global__ void __launch_bounds__(kRedThreads)
-k_reduce_state(PopLayout lay, int ncell, const S *f, Particles<Real> parts, double mp, int np,
-               double *partials)
+k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> parts, double mp,
+             int np, CellList cells, const Real *__restrict__ eps_tab, int ntab, Fields<Real> fld,
+             double *partials, unsigned *ticket, double *out)
 {
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    constexpr int D = L::D, Q = L::Q;
+    Acc<Real> acc[kStatValues];
     const int stride = gridDim.x * blockDim.x;
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < ncell; x += stride) {
         int q[3];
         q[0] = x % lay.n[0];
         q[1] = (x / lay.n[0]) % lay.n[1];
         q[2] = x / (lay.n[0] * lay.n[1]);
-        const long long xe = lay.ext(q);
+        const int xe = lay.ext(q);
+        Real s = Real(0), m[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
+        for (int i = 0; i < Q; ++i) {
             // population i of cell x as the next collision pulls it
-            const double fi =
-                (double)Store<S>::load(f[(long long)i * lay.nce + xe - lay.off<L>(i)]);
-            acc[0] += fi;
+            const Real fi = Store<S>::load(f[(long long)i * lay.nce + xe - lay.off<L>(i)]);
+            s += fi;
 #pragma unroll
-            for (int a = 0; a < L::D; ++a) acc[1 + a] += (double)L::c(i, a) * fi;
+            for (int a = 0; a < D; ++a) {
+                if (L::c(i, a) == 1) m[a] += fi;
+                else if (L::c(i, a) == -1) m[a] -= fi;
+            }
+        }
+        acc[0].add(s);
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc[1 + a].add(m[a]);
+        const int n = cells.begin(x + 1) - cells.begin(x);
+        acc[7].add(eps_tab[n < ntab ? n : ntab - 1]);
+        if (BED) {
+            acc[8].add(fld.eps_g[x]);
+            const int nt = fld.ntot[x];
+            if (nt > 0) {
+                Real s2 = Real(0);
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const Real d = fld.uact[a][x] - fld.vs[a][x];
+                    s2 += d * d;
+                }
+                acc[9].add(Real(nt) * sqrt(s2));
+                acc[10].add(Real(nt));
+            }
         }
     }
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride) {
 #pragma unroll
-        for (int a = 0; a < L::D; ++a) acc[4 + a] += mp * (double)parts.v[a][k];
+        for (int a = 0; a < D; ++a) acc[4 + a].add(parts.v[a][k]);
     }
-    block_sum_write<7>(acc, partials);
+
+    __shared__ double sh[kRedThreads / 32];
+    __shared__ bool last;
+#pragma unroll
+    for (int k = 0; k < kStatValues; ++k) {
+        const double t = block_sum(acc[k].get(), sh);
+        if (threadIdx.x == 0) partials[blockIdx.x * kStatValues + k] = t;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int nb = gridDim.x;
+#pragma unroll 1
+    for (int k = 0; k < kStatValues; ++k) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nb; b += kRedThreads)
+            v += __ldcg(partials + b * kStatValues + k);
+        const double t = block_sum(v, sh);
+        if (threadIdx.x == 0) out[k] = (k >= 4 && k < 7) ? mp * t : t;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 template <class L, class Real, class S>
-void launch_reduce_state(const PopLayout &lay, int ncell, const S *f, Particles<Real> parts,
-                         double mp, int np, double *partials, double *out, cudaStream_t st)
+void launch_reduce_all(const PopLayout &lay, int ncell, const S *f, Particles<Real> parts, double mp,
+                       int np, CellList cells, const Real *eps_tab, int ntab,
+                       const Fields<Real> *bed, double *partials, unsigned *ticket, double *out,
+                       cudaStream_t st)
 {
-    const int nb = reduce_block_count(ncell > np ? ncell : np);
-    k_reduce_state<L, Real, S><<<nb, kRedThreads, 0, st>>>(lay, ncell, f, parts, mp, np, partials);
-    k_reduce_final<<<1, 32, 0, st>>>(partials, nb, 7, out);
+    const int n = ncell > np ? ncell : np;
+    int nb = (n + kRedThreads * 4 - 1) / (kRedThreads * 4);
+    nb = nb < 1 ? 1 : (nb > kRedMaxBlocks ? kRedMaxBlocks : nb);
+    if (bed)
+        k_reduce_all<L, Real, S, true><<<nb, kRedThreads, 0, st>>>(
+            lay, ncell, f, parts, mp, np, cells, eps_tab, ntab, *bed, partials, ticket, out);
+    else
+        k_reduce_all<L, Real, S, false><<<nb, kRedThreads, 0, st>>>(
+            lay, ncell, f, parts, mp, np, cells, eps_tab, ntab, Fields<Real>{}, partials, ticket, out);
 }
 
-// values: [0] sum eps_g, [1] sum n |u_act - v_s|, [2] sum n
-template <class Real>
-__global__ void __launch_bounds__(kRedThreads)
-k_reduce_bed(int ncell, int dim, const Real *eps_g, const int *ntot, const Real *u0, const Real *u1,
-             const Real *u2, const Real *v0, const Real *v1, const Real *v2, double *partials)
-{
-    double acc[3] = {0, 0, 0};
-    const int stride = gridDim.x * blockDim.x;
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < ncell; x += stride) {
-        acc[0] += (double)eps_g[x];
-        const int n = ntot[x];
-        if (n > 0) {
-            double s = 0.0, d;
-            d = (double)u0[x] - (double)v0[x]; s += d * d;
-            d = (double)u1[x] - (double)v1[x]; s += d * d;
-            if (dim == 3) { d = (double)u2[x] - (double)v2[x]; s += d * d; }
-            acc[1] += (double)n * sqrt(s);
-            acc[2] += (double)n;
-        }
-    }
-    block_sum_write<3>(acc, partials);
-}
-
-template <class Real>
-void launch_reduce_bed(int ncell, int dim, const Real *eps_g, const int *ntot,
-                       const Real *const *uact, const Real *const *vs, double *partials,
-                       double *out, cudaStream_t st)
-{
-    const int nb = reduce_block_count(ncell);
-    k_reduce_bed<Real><<<nb, kRedThreads, 0, st>>>(ncell, dim, eps_g, ntot, uact[0], uact[1],
-                                                   dim == 3 ? uact[2] : uact[1], vs[0], vs[1],
-                                                   dim == 3 ? vs[2] : vs[1], partials);
-    k_reduce_final<<<1, 32, 0, st>>>(partials, nb, 3, out);
-}
-
-// lattice mean of eps_g for the current particle positions: [0] sum over cells
-template <class Real>
-__global__ void __launch_bounds__(kRedThreads)
-k_reduce_voidage(int ncell, CellList cells, const Real *eps_g_tab, int ntab, double *partials)
-{
-    double acc[1] = {0.0};
-    const int stride = gridDim.x * blockDim.x;
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < ncell; x += stride) {
-        const int n = cells.begin(x + 1) - cells.begin(x);
-        acc[0] += (double)eps_g_tab[n < ntab ? n : ntab - 1];
-    }
-    block_sum_write<1>(acc, partials);
-}
-
-template <class Real>
-void launch_reduce_voidage(int ncell, CellList cells, const Real *eps_g_tab, int ntab,
-                           double *partials, double *out, cudaStream_t st)
-{
-    const int nb = reduce_block_count(ncell);
-    k_reduce_voidage<Real><<<nb, kRedThreads, 0, st>>>(ncell, cells, eps_g_tab, ntab, partials);
-    k_reduce_final<<<1, 32, 0, st>>>(partials, nb, 1, out);
-}
-template void launch_reduce_voidage<double>(int, CellList, const double *, int, double *, double *,
-                                            cudaStream_t);
-template void launch_reduce_voidage<float>(int, CellList, const float *, int, double *, double *,
-                                           cudaStream_t);
-
-#define LBDPS_INST_RED(L, R, S)                                                                   \
-    template void launch_reduce_state<L, R, S>(const PopLayout &, int, const S *, Particles<R>,    \
-                                               double, int, double *, double *, cudaStream_t);
+#define LBDPS_INST_RED(L, R, S)                                                                    \
+    template void launch_reduce_all<L, R, S>(const PopLayout &, int, const S *, Particles<R>,       \
+                                             double, int, CellList, const R *, int,                \
+                                             const Fields<R> *, double *, unsigned *, double *,     \
+                                             cudaStream_t);
 LBDPS_INST_RED(D2Q9, double, double)
 LBDPS_INST_RED(D2Q9, float, float)
 LBDPS_INST_RED(D2Q9, float, __half)
@@ -154,11 +163,5 @@ LBDPS_INST_RED(D3Q19, double, double)
 LBDPS_INST_RED(D3Q19, float, float)
 LBDPS_INST_RED(D3Q19, float, __half)
 LBDPS_INST_RED(D3Q19, float, __nv_bfloat16)
-template void launch_reduce_bed<double>(int, int, const double *, const int *,
-                                        const double *const *, const double *const *, double *,
-                                        double *, cudaStream_t);
-template void launch_reduce_bed<float>(int, int, const float *, const int *,
-                                       const float *const *, const float *const *, double *,
-                                       double *, cudaStream_t);
 
 }  // namespace lbdpsk
