@@ -119,6 +119,11 @@ typedef struct {
     double e;             /* restitution coefficient, Eq. 17-18                   */
     const double *pos;    /* n x dim centres, m, inside the domain, non-overlapping; copied */
     const double *vel;    /* n x dim velocities, m/s; copied                      */
+    int recirculate;      /* 1: a particle leaving through the outlet face of the vertical
+                             axis re-enters through the inlet face at the same lateral
+                             position and velocity (the solids loop of a circulating
+                             bed, §3.2 / Fig. 9); needs the inlet below and the outlet
+                             above.  0: particles reflect at every non-periodic face */
 } lbdps_particle_desc;
 
 /* Gas and run parameters. */
@@ -151,6 +156,9 @@ typedef struct {
                                     step (needs diagnostics, else NaN)                */
     int64_t steps;               /* steps taken so far                              */
     int health;                  /* bitmask: 1 diverged, 2 domain, 4 capacity       */
+    int64_t solids_out;          /* particles that left through the outlet since creation
+                                    (recirculate = 1; the solids flux of §3.2 is
+                                    solids_out m_p / (outlet area x time))            */
 } lbdps_stats_t;
 
 /* Create a bed (the paper's step 1, Fig. 4).  Validates the description:

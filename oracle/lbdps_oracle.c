@@ -81,6 +81,7 @@ typedef struct {
     double cs_smag;
     int superficial_mode;    /* 0: u / eps_2d, 1: u / eps_g, 2: no conversion */
     int pressure_plus;       /* 1: +V_p grad p as printed in Eq. 16 */
+    int recirculate;         /* 1: outlet -> inlet re-injection of particles (reading R21) */
 } ob_setup;
 
 /* ---- lattice-unit constants derived from an ob_setup ---- */
@@ -103,6 +104,8 @@ typedef struct {
     int bc[6];
     ob_consts k;
     int superficial_mode, pressure_plus;
+    int recirculate;         /* reading R21 */
+    int64_t solids_out;      /* particles that left through the outlet so far */
     int c[OB_MAXQ][3];
     double w[OB_MAXQ];
     int opp[OB_MAXQ];
@@ -348,6 +351,9 @@ ob_bed *ob_create(const ob_setup *s)
         if (s->bc[2 * a] == OB_PERIODIC && s->n[a] < 3) return NULL;
     }
     if (!(s->d_p <= s->h)) return NULL;
+    /* recirculation needs the inlet below and the outlet above (reading R21) */
+    if (s->recirculate && !(s->bc[2 * (s->dim - 1)] == OB_INLET && s->bc[2 * s->dim - 1] == OB_OUTLET))
+        return NULL;
     ob_bed *b = calloc(1, sizeof(ob_bed));
     if (!b) return NULL;
     b->dim = s->dim;
@@ -360,6 +366,8 @@ ob_bed *ob_create(const ob_setup *s)
     ob_units(s, &b->k);
     b->superficial_mode = s->superficial_mode;
     b->pressure_plus = s->pressure_plus;
+    b->recirculate = s->recirculate;
+    b->solids_out = 0;
     set_lattice(b);
 
     size_t nc = (size_t)b->ncell;
@@ -786,6 +794,10 @@ static void drag_and_integrate(ob_bed *b)
                         *pa += L;
                         if (*pa >= L) *pa = 0.0;
                     }
+                } else if (b->recirculate && a == dim - 1 && *pa >= L) {
+                    /* reading R21: through the outlet, back in at the inlet */
+                    *pa -= L;
+                    b->solids_out += 1;
                 } else {
                     if (*pa < 0.0) {
                         *pa = -*pa;
@@ -904,7 +916,9 @@ static void detect_and_resolve(ob_bed *b)
             if (b->bc[2 * a] == OB_PERIODIC) continue;
             double pa = b->P[p * 3 + a], va = b->v[p * 3 + a];
             if (pa < r && va < 0.0) b->wall_hit[p] |= 1 << (2 * a);
-            if ((double)b->n[a] - pa < r && va > 0.0) b->wall_hit[p] |= 1 << (2 * a + 1);
+            /* with the solids loop closed the outlet lets particles through (R21) */
+            const int open_top = b->recirculate && a == dim - 1;
+            if (!open_top && (double)b->n[a] - pa < r && va > 0.0) b->wall_hit[p] |= 1 << (2 * a + 1);
         }
     }
     qsort(b->pairs, (size_t)b->npairs, 2 * sizeof(int64_t), cmp_pair);
@@ -1128,6 +1142,8 @@ static void nsum(double *s, double *c, double x)
     else *c += (x - t) + *s;
     *s = t;
 }
+
+int64_t ob_solids_out(const ob_bed *b) { return b->solids_out; }
 
 void ob_stats(const ob_bed *b, double *out)
 {

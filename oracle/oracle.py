@@ -39,6 +39,7 @@ class Setup(ctypes.Structure):
         ("g", ctypes.c_double * 3), ("body_accel", ctypes.c_double * 3),
         ("u0", ctypes.c_double * 3), ("cs_smag", ctypes.c_double),
         ("superficial_mode", ctypes.c_int), ("pressure_plus", ctypes.c_int),
+        ("recirculate", ctypes.c_int),
     ]
 
 
@@ -60,7 +61,7 @@ def lib():
         for name in ("ob_dim", "ob_nq"):
             getattr(L, name).argtypes = [vp]
             getattr(L, name).restype = ctypes.c_int
-        for name in ("ob_ncell", "ob_np", "ob_npairs"):
+        for name in ("ob_ncell", "ob_np", "ob_npairs", "ob_solids_out"):
             getattr(L, name).argtypes = [vp]
             getattr(L, name).restype = ctypes.c_int64
         L.ob_constants.argtypes = [vp, dp]
@@ -134,6 +135,7 @@ def make_setup(w):
     s.cs_smag = float(w.cs_smag)
     s.superficial_mode = int(w.superficial_mode)
     s.pressure_plus = int(w.pressure_plus)
+    s.recirculate = int(getattr(w, "recirculate", False))
     return s, keep
 
 
@@ -252,5 +254,6 @@ class OracleBed:
     def stats(self) -> dict:
         out = np.zeros(9)
         lib().ob_stats(self._h, _dp(out))
-        return {"mass": out[0], "gas_momentum": out[1:4], "particle_momentum": out[4:7],
+        return {"solids_out": int(lib().ob_solids_out(self._h)),
+                "mass": out[0], "gas_momentum": out[1:4], "particle_momentum": out[4:7],
                 "mean_eps_g": out[7], "mean_slip": out[8]}

@@ -163,6 +163,7 @@ struct lbdps {
     int64_t steps = 0;
     int64_t since_check = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int recirculate = 0;               // outlet -> inlet re-injection of particles
     unsigned *health_host = nullptr;   // pinned: the health word, then 16 doubles of statistics
     double *stats_host = nullptr;      // inside the same pinned block
     std::vector<double> inlet_lat;     // face cells x dim
@@ -194,6 +195,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
     unsigned *health_dev = nullptr;
     double *red_partials = nullptr, *red_out = nullptr;
     unsigned *red_ticket = nullptr;
+    unsigned long long *solids_out = nullptr;   // particles through the outlet so far
     unsigned long long *npairs_dev = nullptr;
     StepParams<Real> sp{};
     PopLayout lay{};          // extended lattice of the population arrays
@@ -264,11 +266,12 @@ template <class L, class Real, class S> struct EngineT : Engine {
         red_partials = (double *)get(sizeof(double) * 16 * 512);   // values x blocks of the reduction
         red_out = (double *)get(sizeof(double) * 16);
         red_ticket = (unsigned *)get(sizeof(unsigned));
+        solids_out = (unsigned long long *)get(sizeof(unsigned long long));
         npairs_dev = (unsigned long long *)get(sizeof(unsigned long long));
         void *must[] = {f[0], f[1], cl_local[0], cl_local[1], cl_base[0], cl_base[1], fld.rho,
                         fld.beta, fld.solg, key, counts, slot, idslot, tile_total, ticket,
                         best, wall, tab_branch, inlet_dev, health_dev,
-                        red_partials, red_out, red_ticket, npairs_dev, part[0].id, part[1].id,
+                        red_partials, red_out, red_ticket, solids_out, npairs_dev, part[0].id, part[1].id,
                         part[0].cell, part[1].cell};
         for (void *p : must)
             if (!p) return fail(LBDPS_ERR_OOM, "device allocation failed");
@@ -349,6 +352,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
         for (int f6 = 0; f6 < 6; ++f6)
             if (H->bc[f6] == BC_INLET) p.inlet_face = f6;
         p.health = health_dev;
+        p.recirculate = H->recirculate;
+        p.solids_out = solids_out;
     }
 
     int upload_initial(const double *pos_lat, const double *vel_lat) override
@@ -371,6 +376,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
         CU(cudaMemsetAsync(counts, 0, sizeof(int) * (H->ncell + 1), st));
         CU(cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
         CU(cudaMemsetAsync(red_ticket, 0, sizeof(unsigned), st));
+        CU(cudaMemsetAsync(solids_out, 0, sizeof(unsigned long long), st));
         if (H->np == 0) {
             int rc = clear_cells(0);
             if (rc == LBDPS_OK) rc = clear_cells(1);
@@ -700,7 +706,12 @@ template <class L, class Real, class S> struct EngineT : Engine {
         CU(cudaMemcpyAsync(v, red_out, sizeof(double) * 11, cudaMemcpyDeviceToHost, H->stream));
         CU(cudaMemcpyAsync(H->health_host, health_word(), sizeof(unsigned), cudaMemcpyDeviceToHost,
                            H->stream));
+        CU(cudaMemcpyAsync(v + 12, solids_out, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           H->stream));
         CU(cudaStreamSynchronize(H->stream));
+        unsigned long long nout = 0;
+        std::memcpy(&nout, v + 12, sizeof(nout));
+        out->solids_out = (int64_t)nout;
         out->mass = v[0] + (double)H->ncell;
         for (int a = 0; a < 3; ++a) {
             out->gas_momentum[a] = a < D ? v[1 + a] : 0.0;
@@ -729,7 +740,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
         const size_t nc = (size_t)H->ncell, np = (size_t)H->np;
         return sizeof(S) * pop_slots() + (sizeof(double) + 2 * sizeof(Real)) * D * np +
                2 * sizeof(int) * np + sizeof(int) * (nc + 1) +
-               sizeof(int) * (cell_tiles(H->ncell) + 1);
+               sizeof(int) * (cell_tiles(H->ncell) + 1) + sizeof(unsigned long long);
     }
 
     int save(char *buf) override
@@ -756,6 +767,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
         o += sizeof(int) * (nc + 1);
         CU(cudaMemcpyAsync(buf + o, cl_base[cur], sizeof(int) * (cell_tiles(H->ncell) + 1),
                            cudaMemcpyDeviceToHost, st));
+        o += sizeof(int) * (cell_tiles(H->ncell) + 1);
+        CU(cudaMemcpyAsync(buf + o, solids_out, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
         return LBDPS_OK;
     }
@@ -784,6 +797,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
         o += sizeof(int) * (nc + 1);
         CU(cudaMemcpyAsync(cl_base[cur], buf + o, sizeof(int) * (cell_tiles(H->ncell) + 1),
                            cudaMemcpyHostToDevice, st));
+        o += sizeof(int) * (cell_tiles(H->ncell) + 1);
+        CU(cudaMemcpyAsync(solids_out, buf + o, sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
         CU(cudaMemsetAsync(counts, 0, sizeof(int) * (nc + 1), st));
         CU(cudaStreamSynchronize(st));
         return LBDPS_OK;
@@ -980,6 +995,9 @@ static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc 
     if (!(par->d_p > 0) || !(par->rho_s > 0) || !(par->e >= 0 && par->e <= 1))
         return fail(LBDPS_ERR_INVALID, "bad particle properties");
     if (!(par->d_p <= lat->h)) return fail(LBDPS_ERR_INVALID, "d_p must not exceed h");
+    if (par->recirculate != 0 && par->recirculate != 1) return fail(LBDPS_ERR_INVALID, "bad recirculate");
+    if (par->recirculate && !(bc[2 * (D - 1)] == BC_INLET && bc[2 * (D - 1) + 1] == BC_OUTLET))
+        return fail(LBDPS_ERR_INVALID, "recirculate needs the inlet below and the outlet above");
     if (!(prm->rho_g > 0) || !(prm->mu_g > 0)) return fail(LBDPS_ERR_INVALID, "bad gas properties");
     if (prm->storage < 0 || prm->storage > 3) return fail(LBDPS_ERR_INVALID, "bad storage");
     if (!(prm->cs_smag >= 0)) return fail(LBDPS_ERR_INVALID, "bad Smagorinsky constant");
@@ -996,6 +1014,7 @@ static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc 
     for (int f6 = 0; f6 < 6; ++f6) h->bc[f6] = bc[f6];
     h->h = lat->h;
     h->dt = lat->dt;
+    h->recirculate = par->recirculate;
     h->prm = *prm;
     h->k = derive(*lat, *par, *prm);
     const Derived &k = h->k;

@@ -141,6 +141,8 @@ template <class Real> struct StepParams {
     const Real *inlet_u;      // inlet face cells x dim
     int inlet_face;           // face index or -1
     unsigned *health;
+    int recirculate;          // 1: outlet -> inlet re-injection of particles
+    unsigned long long *solids_out;   // particles through the outlet so far
 };
 
 // Layout of the population arrays: the lattice plus one ghost layer on every

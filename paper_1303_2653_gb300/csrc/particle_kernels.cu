@@ -304,6 +304,10 @@ k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, Cell
                     P[a] += L;
                     if (P[a] >= L) P[a] = 0.0;
                 }
+            } else if (p.recirculate && a == D - 1 && P[a] >= L) {
+                // through the outlet, back in at the inlet (solids loop)
+                P[a] -= L;
+                atomicAdd(p.solids_out, 1ull);
             } else {
                 if (P[a] < 0.0) {
                     P[a] = -P[a];
@@ -755,7 +759,8 @@ k_detect(StepParams<Real> p, Particles<Real> parts, CellList cells, int *__restr
             const double Pa = parts.P[a][i];
             if (Pa < p.r64 && (double)parts.v[a][i] < 0.0) bits |= 1 << (2 * a);
         }
-        if (idx[a] == p.n[a] - 1) {
+        // with the solids loop closed the outlet lets particles through
+        if (idx[a] == p.n[a] - 1 && !(p.recirculate && a == D - 1)) {
             const double Pa = parts.P[a][i];
             if (__dsub_rn(p.len[a], Pa) < p.r64 && (double)parts.v[a][i] > 0.0)
                 bits |= 1 << (2 * a + 1);

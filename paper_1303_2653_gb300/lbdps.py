@@ -46,7 +46,8 @@ class LatticeDesc(ctypes.Structure):
 
 class ParticleDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d_p", ctypes.c_double), ("rho_s", ctypes.c_double),
-                ("e", ctypes.c_double), ("pos", _dp), ("vel", _dp)]
+                ("e", ctypes.c_double), ("pos", _dp), ("vel", _dp),
+                ("recirculate", ctypes.c_int)]
 
 
 class Params(ctypes.Structure):
@@ -64,7 +65,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("mass", ctypes.c_double), ("gas_momentum", ctypes.c_double * 3),
                 ("particle_momentum", ctypes.c_double * 3), ("mean_eps_g", ctypes.c_double),
                 ("mean_slip", ctypes.c_double), ("steps", ctypes.c_int64),
-                ("health", ctypes.c_int)]
+                ("health", ctypes.c_int), ("solids_out", ctypes.c_int64)]
 
 
 class DoneRec(ctypes.Structure):
@@ -184,7 +185,7 @@ def describe(w, storage: Optional[int] = None, diagnostics: bool = False,
     vel = np.ascontiguousarray(w.vel, dtype=np.float64)
     keep += [pos, vel]
     par = ParticleDesc(pos.shape[0], float(w.d_p), float(w.rho_s), float(w.e), _ptr(pos),
-                       _ptr(vel))
+                       _ptr(vel), int(w.recirculate))
     prm = Params()
     prm.rho_g, prm.mu_g = float(w.rho_g), float(w.mu_g)
     for a in range(3):
@@ -372,7 +373,7 @@ class Bed:
         return {"mass": s.mass, "gas_momentum": np.array(s.gas_momentum[:]),
                 "particle_momentum": np.array(s.particle_momentum[:]),
                 "mean_eps_g": s.mean_eps_g, "mean_slip": s.mean_slip, "steps": s.steps,
-                "health": s.health}
+                "health": s.health, "solids_out": s.solids_out}
 
     def health(self) -> int:
         hw = ctypes.c_int()

@@ -109,6 +109,7 @@ class Workload:
     cs_smag: float = 0.0
     superficial_mode: int = 0
     pressure_plus: int = 0
+    recirculate: bool = False     # outlet -> inlet re-injection of particles
     storage: int = STORE_F32
     steps: int = 1
     seed: int = 0
@@ -191,6 +192,34 @@ def riser2d(nx=256, ny=2048, n_particles=200000, seed=SEED_BASE + 1, storage=STO
         rho_s=rho_s, e=0.9, pos=pos, vel=vel, rho_g=rho_g, mu_g=mu_g,
         g=(0.0, -g, 0.0), body_accel=(0.0, a_body, 0.0), u0=(0.0, u_gas, 0.0),
         cs_smag=cs_smag, storage=storage, steps=steps, seed=seed)
+
+
+def cfb_riser2d(nx=60, ny=720, n_particles=123921, seed=SEED_BASE + 5, storage=STORE_F32,
+                steps=20000, cs_smag=0.1, h=2.7e-4, u_in=1.52, u_lat=0.0338) -> Workload:
+    """The riser of a circulating fluidized bed as in the paper's §3.2 (Table 2):
+    0.0162 m x 0.194 m at h = 2.7e-4 m (60 x 720 cells), 123,921 particles of
+    54 um and 930 kg/m^3 placed uniformly at rest (solids fraction 0.09),
+    gas 1.1795 kg/m^3, 1.8872e-5 Pa s entering at the bottom at 1.52 m/s
+    (0.0338 in lattice units, which sets dt = 6.0e-6 s), a pressure outlet at
+    the top, walls at the sides, gravity, and the solids loop closed: a
+    particle leaving through the outlet re-enters through the inlet.  The
+    Smagorinsky constant is a parameter (the paper prints none; tau is
+    0.5040).  Smaller lattices keep h and the solids fraction."""
+    d_p = 54e-6
+    r = 0.5 * d_p
+    rho_s, rho_g, mu_g, g = 930.0, 1.1795, 1.8872e-5, 9.81
+    dt = u_lat * h / u_in
+    W, H = nx * h, ny * h
+    pos = rsa(2, (W, H), (r, r), (W - r, H - r), (0, 0), d_p * (1 + 1e-9), n_particles, seed)
+    vel = np.zeros_like(pos)
+    inlet = np.zeros((nx, 2))
+    inlet[:, 1] = u_in
+    return Workload(
+        name=f"cfbriser2d-{nx}x{ny}-N{n_particles}", dim=2, n=(nx, ny),
+        bc=(WALL, WALL, INLET, OUTLET, PERIODIC, PERIODIC), h=h, dt=dt, d_p=d_p,
+        rho_s=rho_s, e=0.9, pos=pos, vel=vel, rho_g=rho_g, mu_g=mu_g,
+        g=(0.0, -g, 0.0), u0=(0.0, u_in, 0.0), inlet_u=inlet, cs_smag=cs_smag,
+        recirculate=True, storage=storage, steps=steps, seed=seed)
 
 
 def riser3d(nx=256, ny=256, nz=1024, n_particles=4000000, seed=SEED_BASE + 3,
