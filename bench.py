@@ -63,6 +63,12 @@ def parse():
                     help="circulating-bed riser of Table 2 with the solids loop closed: "
                          "solids flux through the outlet over time")
     ap.add_argument("--cfb-steps", type=int, default=60000)
+    ap.add_argument("--bubble", action="store_true",
+                    help="single-orifice bed of Table 1 with a 0.006 s jet pulse: equivalent "
+                         "bubble diameter over time")
+    ap.add_argument("--bubble-time", type=float, default=0.05)
+    ap.add_argument("--bubble-cs", type=float, default=0.1,
+                    help="Smagorinsky constant of the bubbling bed (Table 1's tau is 0.50089)")
     return ap.parse_args()
 
 
@@ -275,6 +281,10 @@ def main():
     if args.cfb:
         if rank == 0:
             cfb_main(args)
+        return
+    if args.bubble:
+        if rank == 0:
+            bubble_main(args)
         return
 
     import torch
@@ -620,6 +630,60 @@ def cfb_main(args):
             "mean_flux_second_half": float(np.mean(half)) if half else None,
             "series": series, "mlups": w.ncell * done / t_dev / 1e6,
             "note": "the paper reports 13.8 kg/(m^2 s) from its own (longer) run, §3.2; context only"}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ bubbling bed
+
+def bubble_main(args):
+    """The bed of Table 1 (25 x 100, 15,000 particles, background inlet
+    0.0025 m/s) with the jet of 0.8 m/s on the central three cells for
+    0.006 s (§3.1), then the background only; every 100 steps the equivalent
+    diameter D_e = 2 h sqrt(A / pi) of the largest region with eps_2d > 0.85
+    below the bed surface (lbdps_bubbles)."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1303_2653_gb300 import lbdps as L
+    from paper_1303_2653_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    # LES on: tau is 0.50089 in Table 1 (reading R20)
+    w = W.bubbling_table1(cs_smag=args.bubble_cs)
+    bed = L.Bed(w, check_every=100)
+    pulse = int(round(0.006 / w.dt))
+    total = int(round(args.bubble_time / w.dt))
+    every = 100
+    series, best = [], (0.0, 0.0)
+    st = bed.stream
+    t_dev, done = 0.0, 0
+    while done < total:
+        k = min(every, total - done)
+        if done < pulse <= done + k:        # end the pulse exactly at step `pulse`
+            k = pulse - done
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        try:
+            bed.step(k)
+        except L.LbdpsError as err:       # diverged: report how far it got
+            series.append({"t_s": done * w.dt, "stopped": str(err)})
+            break
+        b.record(st)
+        bub = bed.bubbles(0.85, L.VOIDAGE_2D)
+        t_dev += a.elapsed_time(b) / 1e3
+        done += k
+        if done == pulse:
+            bed.set_inlet(W.background_inlet(w))
+        de = 2.0 * w.h * math.sqrt(bub["largest"] / math.pi)
+        series.append({"t_s": done * w.dt, "de_m": de, "regions": bub["count"]})
+        if de > best[0]:
+            best = (de, done * w.dt)
+    line = {"metric": "maximum equivalent bubble diameter, single-orifice bed", "unit": "m",
+            "value": best[0], "at_s": best[1],
+            "workload": f"{w.name}, jet 0.8 m/s for 0.006 s, C_s = {w.cs_smag}",
+            "data": "synthetic", "steps": done, "health": bed.health(),
+            "mlups": w.ncell * done / t_dev / 1e6,
+            "series": series[::10] + series[-1:]}
     print(json.dumps(line), flush=True)
 
 

@@ -194,6 +194,28 @@ int lbdps_sync(lbdps_t *h);
  * LBDPS_UNITS_LATTICE or _SI. */
 int lbdps_fields(lbdps_t *h, int mask, int units, double *out, size_t cap);
 
+/* which voidage lbdps_bubbles thresholds */
+#define LBDPS_VOIDAGE_2D 0   /* eps_2d = 1 - eps_s of the cell, Eq. 10          */
+#define LBDPS_VOIDAGE_G  1   /* eps_g, the 3D voidage of Eq. 11 (= eps_2d in 3D) */
+
+/* Bubble regions of the current particle positions (§3.1): connected regions
+ * (neighbours along the axes, wrapping across periodic faces) of cells whose
+ * voidage (LBDPS_VOIDAGE_*, from the cell's particle count) exceeds
+ * threshold (0.85 in §3.1), leaving out the regions that reach the top row of
+ * the vertical axis (the freeboard above the bed).  out[0] = cells of the
+ * largest region, out[1] = number of regions, out[2] = cells in all regions.
+ * The equivalent bubble diameter of §3.1 (a circle of the same area) is
+ * 2 h sqrt(out[0] / pi) in 2D.  Device scratch of three ints per cell is
+ * allocated on the first call and kept.  LBDPS_ERR_INVALID for a threshold
+ * outside [0, 1) or an unknown voidage. */
+int lbdps_bubbles(lbdps_t *h, double threshold, int voidage, int64_t out[3]);
+
+/* Replace the inlet velocities (m/s, inlet-face cells x dim, x-fastest, as
+ * lbdps_lattice_desc.inlet_u), e.g. to end a jet pulse (§3.1: the injection
+ * lasts 0.006 s).  Takes effect from the next step, graphs included.
+ * LBDPS_ERR_INVALID if the bed has no inlet or |u| >= 0.3 in lattice units. */
+int lbdps_set_inlet(lbdps_t *h, const double *inlet_u);
+
 /* Copy the particle state (section 2.2: P, v) in id order, n x dim each.
  * cap is the capacity of each array in particles. */
 int lbdps_particles(lbdps_t *h, int units, double *pos, double *vel, int64_t cap);

@@ -106,6 +106,7 @@ typedef struct {
     int superficial_mode, pressure_plus;
     int recirculate;         /* reading R21 */
     int64_t solids_out;      /* particles that left through the outlet so far */
+    double uscale;           /* SI velocity -> lattice units: dt / h */
     int c[OB_MAXQ][3];
     double w[OB_MAXQ];
     int opp[OB_MAXQ];
@@ -368,6 +369,7 @@ ob_bed *ob_create(const ob_setup *s)
     b->pressure_plus = s->pressure_plus;
     b->recirculate = s->recirculate;
     b->solids_out = 0;
+    b->uscale = s->dt / s->h;
     set_lattice(b);
 
     size_t nc = (size_t)b->ncell;
@@ -1144,6 +1146,70 @@ static void nsum(double *s, double *c, double x)
 }
 
 int64_t ob_solids_out(const ob_bed *b) { return b->solids_out; }
+
+/* Replace the inlet velocities (SI, inlet-face cells x dim), e.g. at the end
+ * of the jet pulse of §3.1. */
+void ob_set_inlet(ob_bed *b, const double *inlet_si)
+{
+    int64_t nface = b->ncell / b->n[b->dim - 1];
+    for (int64_t j = 0; j < nface; ++j)
+        for (int a = 0; a < b->dim; ++a) b->inlet_u[j * 3 + a] = inlet_si[j * b->dim + a] * b->uscale;
+}
+
+/* Bubbles (§3.1): regions of cells whose voidage (eps_2d of Eq. 10 for
+ * voidage = 0, eps_g of Eq. 11 for 1, from the current particle counts)
+ * exceeds the threshold, neighbours along the axes
+ * (periodic faces wrap), without the regions that reach the top row of the
+ * vertical axis.  Breadth-first flood fill.  out: [0] cells of the largest
+ * region, [1] regions, [2] cells in all regions. */
+void ob_bubbles(const ob_bed *b, double threshold, int voidage, int64_t *out)
+{
+    int64_t nc = b->ncell;
+    char *in = calloc((size_t)nc, 1);
+    char *seen = calloc((size_t)nc, 1);
+    int64_t *queue = malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
+    for (int64_t x = 0; x < nc; ++x) {
+        double es, e2;
+        double eg = voidage_of_count(b, b->cell_start[x + 1] - b->cell_start[x], &es, &e2);
+        in[x] = (voidage == 0 ? e2 : eg) > threshold;
+    }
+    int64_t stride[3] = {1, b->n[0], (int64_t)b->n[0] * b->n[1]};
+    int vert = b->dim - 1;
+    out[0] = out[1] = out[2] = 0;
+    for (int64_t s0 = 0; s0 < nc; ++s0) {
+        if (!in[s0] || seen[s0]) continue;
+        int64_t head = 0, tail = 0, size = 0;
+        int top = 0;
+        queue[tail++] = s0;
+        seen[s0] = 1;
+        while (head < tail) {
+            int64_t x = queue[head++];
+            ++size;
+            int64_t q[3] = {x % b->n[0], (x / b->n[0]) % b->n[1], x / stride[2]};
+            if (q[vert] == b->n[vert] - 1) top = 1;
+            for (int a = 0; a < b->dim; ++a)
+                for (int sgn = -1; sgn <= 1; sgn += 2) {
+                    int64_t qa = q[a] + sgn;
+                    if (qa < 0 || qa >= b->n[a]) {
+                        if (b->bc[2 * a] != OB_PERIODIC) continue;
+                        qa = (qa + b->n[a]) % b->n[a];
+                    }
+                    int64_t y = x + (qa - q[a]) * stride[a];
+                    if (in[y] && !seen[y]) {
+                        seen[y] = 1;
+                        queue[tail++] = y;
+                    }
+                }
+        }
+        if (top) continue;
+        if (size > out[0]) out[0] = size;
+        out[1] += 1;
+        out[2] += size;
+    }
+    free(in);
+    free(seen);
+    free(queue);
+}
 
 void ob_stats(const ob_bed *b, double *out)
 {

@@ -65,6 +65,8 @@ def lib():
             getattr(L, name).argtypes = [vp]
             getattr(L, name).restype = ctypes.c_int64
         L.ob_constants.argtypes = [vp, dp]
+        L.ob_set_inlet.argtypes = [vp, dp]
+        L.ob_bubbles.argtypes = [vp, d, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
         L.ob_units_flat.argtypes = [ctypes.POINTER(Setup), dp]
         L.ob_get_populations.argtypes = [vp, dp]
         L.ob_set_populations.argtypes = [vp, dp]
@@ -250,6 +252,15 @@ class OracleBed:
         out = np.empty((max(n, 1), 2), dtype=np.int64)
         lib().ob_get_pairs(self._h, _i64p(out), n)
         return out[:n]
+
+    def set_inlet(self, inlet_u):
+        u = np.ascontiguousarray(inlet_u, dtype=np.float64)
+        lib().ob_set_inlet(self._h, _dp(u))
+
+    def bubbles(self, threshold: float = 0.85, voidage: int = 0) -> dict:
+        out = np.zeros(3, dtype=np.int64)
+        lib().ob_bubbles(self._h, float(threshold), int(voidage), _i64p(out))
+        return {"largest": int(out[0]), "count": int(out[1]), "cells": int(out[2])}
 
     def stats(self) -> dict:
         out = np.zeros(9)

@@ -36,7 +36,7 @@ def build_workloads(force: bool = False) -> str:
 
 
 CU_SOURCES = ["lbm_kernels.cu", "particle_kernels.cu", "stats_kernels.cu", "lbdps_api.cu",
-              "lbdps_server.cu", "noalloc_sort.cu"]
+              "lbdps_server.cu", "noalloc_sort.cu", "bubble_kernels.cu"]
 HEADERS = ["lbdps_internal.cuh"]
 
 

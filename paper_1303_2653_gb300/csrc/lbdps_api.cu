@@ -139,6 +139,8 @@ struct Engine {
     virtual int collide_particles(int64_t *pairs, int64_t cap, int64_t *npairs) = 0;
     virtual int stats(lbdps_stats_t *out) = 0;
     virtual int health(unsigned *out) = 0;
+    virtual int bubbles(double threshold, int voidage, int64_t *out) = 0;
+    virtual int set_inlet(const double *inlet_lat) = 0;
     virtual size_t checkpoint_bytes() const = 0;
     virtual int save(char *buf) = 0;
     virtual int load(const char *buf) = 0;
@@ -196,6 +198,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
     double *red_partials = nullptr, *red_out = nullptr;
     unsigned *red_ticket = nullptr;
     unsigned long long *solids_out = nullptr;   // particles through the outlet so far
+    BubbleScratch bub{};                         // allocated on the first lbdps_bubbles
     unsigned long long *npairs_dev = nullptr;
     StepParams<Real> sp{};
     PopLayout lay{};          // extended lattice of the population arrays
@@ -721,6 +724,48 @@ template <class L, class Real, class S> struct EngineT : Engine {
         out->mean_slip = bed ? (v[10] > 0 ? v[9] / v[10] : 0.0) : NAN;
         out->steps = H->steps;
         out->health = (int)*H->health_host;
+        return LBDPS_OK;
+    }
+
+    int bubbles(double threshold, int voidage, int64_t *out) override
+    {
+        const int nc = H->ncell;
+        if (!bub.parent) {
+            BubbleScratch b{};
+            b.parent = (int *)H->mem.get(sizeof(int) * nc);
+            b.size = (int *)H->mem.get(sizeof(int) * nc);
+            b.top = (int *)H->mem.get(sizeof(int) * nc);
+            b.nlim = (int *)H->mem.get(sizeof(int));
+            b.out = (unsigned long long *)H->mem.get(sizeof(unsigned long long) * 3);
+            b.err = (unsigned *)H->mem.get(sizeof(unsigned));
+            if (!b.parent || !b.size || !b.top || !b.nlim || !b.out || !b.err)
+                return fail(LBDPS_ERR_OOM, "device allocation failed");
+            bub = b;
+        }
+        int per_mask = 0;
+        for (int a = 0; a < D; ++a)
+            if (H->bc[2 * a] == BC_PERIODIC) per_mask |= 1 << a;
+        launch_bubbles(D, H->n, per_mask, H->k.r, H->k.vp, H->ntab, threshold, voidage,
+                       cells(H->parity), bub, H->stream);
+        CHECK_LAUNCH();
+        unsigned long long res[3] = {0, 0, 0};
+        unsigned err = 0;
+        CU(cudaMemcpyAsync(res, bub.out, sizeof(res), cudaMemcpyDeviceToHost, H->stream));
+        CU(cudaMemcpyAsync(&err, bub.err, sizeof(err), cudaMemcpyDeviceToHost, H->stream));
+        CU(cudaStreamSynchronize(H->stream));
+        if (err) return fail(LBDPS_ERR_TIMEOUT, "bubble labelling exceeded its iteration bound");
+        for (int k = 0; k < 3; ++k) out[k] = (int64_t)res[k];
+        return LBDPS_OK;
+    }
+
+    int set_inlet(const double *inlet_lat) override
+    {
+        const size_t n = H->inlet_lat.size();
+        std::vector<Real> tmp(n);
+        for (size_t i = 0; i < n; ++i) tmp[i] = (Real)inlet_lat[i];
+        CU(cudaMemcpyAsync(inlet_dev, tmp.data(), sizeof(Real) * n, cudaMemcpyHostToDevice, H->stream));
+        CU(cudaStreamSynchronize(H->stream));
+        H->inlet_lat.assign(inlet_lat, inlet_lat + n);
         return LBDPS_OK;
     }
 
@@ -1261,6 +1306,35 @@ int lbdps_health(lbdps_t *h, int *health)
     if (rc) return rc;
     *health = (int)hw;
     return LBDPS_OK;
+}
+
+int lbdps_bubbles(lbdps_t *h, double threshold, int voidage, int64_t *out)
+{
+    if (!h || !out) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    if (!(threshold >= 0.0 && threshold < 1.0)) return fail(LBDPS_ERR_INVALID, "threshold must be in [0, 1)");
+    if (voidage != LBDPS_VOIDAGE_2D && voidage != LBDPS_VOIDAGE_G)
+        return fail(LBDPS_ERR_INVALID, "unknown voidage");
+    return h->eng->bubbles(threshold, voidage, out);
+}
+
+int lbdps_set_inlet(lbdps_t *h, const double *inlet_u)
+{
+    if (!h || !inlet_u) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    if (h->inlet_lat.empty()) return fail(LBDPS_ERR_INVALID, "the bed has no inlet face");
+    const int D = h->dim;
+    const size_t nface = h->inlet_lat.size() / D;
+    const double us = h->dt / h->h;
+    std::vector<double> lat(h->inlet_lat.size());
+    for (size_t j = 0; j < nface; ++j) {
+        double s = 0.0;
+        for (int a = 0; a < D; ++a) {
+            const double u = inlet_u[j * D + a] * us;
+            lat[j * D + a] = u;
+            s += u * u;
+        }
+        if (!(s < 0.09)) return fail(LBDPS_ERR_INVALID, "inlet |u| must be below 0.3 in lattice units");
+    }
+    return h->eng->set_inlet(lat.data());
 }
 
 int lbdps_constants(lbdps_t *h, double *out, int cap)

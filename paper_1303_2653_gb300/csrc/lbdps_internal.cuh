@@ -95,7 +95,7 @@ template <> struct Store<__nv_bfloat16> {
 // ---------------------------------------------------------------------------
 template <class R> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
-template <> struct Vec4<double> { using type = double4; };
+template <> struct Vec4<double> { using type = double4_32a; };
 
 template <class Real> struct CountTables {
     // packed copies for the lattice kernel: pk0 = {og, gam, inv_div, beta_a},
@@ -191,6 +191,29 @@ inline PopLayout make_layout(int dim, const int *n)
     return l;
 }
 
+// Solid fraction (Eq. 10, capped at close packing) and gas voidage eps_g
+// (Eq. 11 in 2D, 1 - eps_s in 3D) of a cell holding n particle centres, in
+// FP64 (lattice units: r the particle radius, vp its volume).
+__host__ __device__ inline void cell_voidage(int dim, double r, double vp, int n, double *es_out,
+                                             double *eg_out, double *sg_out)
+{
+    const double pi = 3.141592653589793238462643383;
+    double es, sg;
+    if (dim == 2) {
+        const double cap = pi / (2.0 * sqrt(3.0));
+        es = fmin((double)n * pi * r * r, cap);
+        const double s = 1.0 - (1.0 - es);                        // 1 - eps_2d
+        sg = sqrt(2.0) / sqrt(pi * sqrt(3.0)) * (s * sqrt(s));   // eps_3d = 1 - sg
+    } else {
+        const double cap = pi / (3.0 * sqrt(2.0));
+        es = fmin((double)n * vp, cap);
+        sg = es;
+    }
+    *es_out = es;
+    *sg_out = sg;
+    *eg_out = 1.0 - sg;
+}
+
 // Device buffers of one bed.
 template <class Real> struct Fields {
     Real *rho, *uact[3], *fpg[3], *beta, *solg;         // node outputs of the collision
@@ -232,6 +255,23 @@ struct CellListOut {
     unsigned *ticket;   // zero between launches
 };
 inline int cell_tiles(int ncell) { return (ncell + 1 + kCellTile - 1) / kCellTile; }
+
+// Scratch of the bubble labelling (one int per cell for parent, size and
+// top flags; three counters; the count limit; an error word).
+struct BubbleScratch {
+    int *parent, *size, *top, *nlim;
+    unsigned long long *out;   // largest region, regions, cells in regions
+    unsigned *err;
+};
+
+// Bubble regions of the current cell list (§3.1): cells whose voidage
+// (voidage 0: eps_2d, Eq. 10; 1: eps_g, Eq. 11) exceeds threshold, connected
+// along the axes (periodic faces wrap), without the regions that reach the
+// top row of the vertical axis.  per_mask bit a: axis a is periodic.
+void launch_bubbles(int dim, const int *n, int per_mask, double r, double vp, int ntab,
+                    double threshold, int voidage, CellList cells, BubbleScratch s,
+                    cudaStream_t st);
+
 
 template <class L, class Real, class S>
 void launch_collide_stream(const StepParams<Real> &p, const PopLayout &lay, const S *fin, S *fout,

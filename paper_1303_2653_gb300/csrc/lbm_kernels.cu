@@ -40,21 +40,9 @@ __global__ void k_build_tables(int dim, double tau, double r, double vp, double 
 {
     const double pi = 3.141592653589793238462643383;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < ntab; n += gridDim.x * blockDim.x) {
-        double es, e2, eg, sg;
-        if (dim == 2) {
-            const double cap = pi / (2.0 * sqrt(3.0));
-            es = fmin((double)n * pi * r * r, cap);                 // Eq. 10 with h = 1
-            e2 = 1.0 - es;
-            double s = 1.0 - e2;
-            sg = sqrt(2.0) / sqrt(pi * sqrt(3.0)) * (s * sqrt(s));  // Eq. 11: eps_3d = 1 - sg
-            eg = 1.0 - sg;
-        } else {
-            const double cap = pi / (3.0 * sqrt(2.0));
-            es = fmin((double)n * vp, cap);
-            e2 = 1.0 - es;
-            sg = es;
-            eg = 1.0 - es;
-        }
+        double es, eg, sg;
+        cell_voidage(dim, r, vp, n, &es, &eg, &sg);   // Eq. 10-11
+        const double e2 = 1.0 - es;
         double div = (mode == 0) ? e2 : (mode == 1) ? eg : 1.0;
         double om = emms_omega(eg);
         double gm = es * (tau - 0.5) / ((1.0 - es) + (tau - 0.5));      // Eq. 9

@@ -25,6 +25,7 @@ UNITS_LATTICE, UNITS_SI = 0, 1
 
 FIELD_RHO, FIELD_U, FIELD_FPG, FIELD_BETA = 1, 2, 4, 8
 FIELD_VS, FIELD_NTOT, FIELD_TAU_T, FIELD_UACT, FIELD_EPS_G = 16, 32, 64, 128, 256
+VOIDAGE_2D, VOIDAGE_G = 0, 1
 FIELD_NAMES = ["rho", "u", "fpg", "beta", "vs", "ntot", "tau_t", "uact", "eps_g"]
 VECTOR_FIELDS = {"u", "fpg", "vs", "uact"}
 PDIAG_FPRE, PDIAG_FD, PDIAG_BEST, PDIAG_WALL, PDIAG_CELL, PDIAG_ORDER = 0, 1, 2, 3, 4, 5
@@ -115,6 +116,8 @@ def lib():
             "lbdps_memory_estimate": ([ctypes.POINTER(LatticeDesc), ctypes.POINTER(ParticleDesc),
                                        ctypes.POINTER(Params), ctypes.POINTER(sz)], i),
             "lbdps_record_event": ([vp, vp], i),
+            "lbdps_bubbles": ([vp, ctypes.c_double, i, ctypes.POINTER(ctypes.c_int64)], i),
+            "lbdps_set_inlet": ([vp, _dp], i),
             "lbdps_server_create": ([sz, i, i, ctypes.POINTER(vp)], i),
             "lbdps_server_submit": ([vp, ctypes.POINTER(LatticeDesc), ctypes.POINTER(ParticleDesc),
                                      ctypes.POINTER(Params), i64, i, ctypes.POINTER(ctypes.c_uint64)], i),
@@ -374,6 +377,16 @@ class Bed:
                 "particle_momentum": np.array(s.particle_momentum[:]),
                 "mean_eps_g": s.mean_eps_g, "mean_slip": s.mean_slip, "steps": s.steps,
                 "health": s.health, "solids_out": s.solids_out}
+
+    def bubbles(self, threshold: float = 0.85, voidage: int = 0) -> dict:
+        """voidage: VOIDAGE_2D (Eq. 10) or VOIDAGE_G (Eq. 11)."""
+        out = (ctypes.c_int64 * 3)()
+        _check(lib().lbdps_bubbles(self._h, float(threshold), int(voidage), out), "lbdps_bubbles")
+        return {"largest": int(out[0]), "count": int(out[1]), "cells": int(out[2])}
+
+    def set_inlet(self, inlet_u) -> None:
+        u = np.ascontiguousarray(inlet_u, dtype=np.float64)
+        _check(lib().lbdps_set_inlet(self._h, _ptr(u)), "lbdps_set_inlet")
 
     def health(self) -> int:
         hw = ctypes.c_int()

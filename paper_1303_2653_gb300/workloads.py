@@ -162,6 +162,45 @@ def bubbling2d(nx=64, ny=128, n_particles=2000, seed=SEED_BASE + 0, storage=STOR
         storage=storage, steps=steps, seed=seed)
 
 
+def bubbling_table1(nx=25, ny=100, n_particles=15000, seed=SEED_BASE + 6, storage=STORE_F32,
+                    steps=26000, cs_smag=0.0, jet_cells=3, v_mf=0.0025, v_inj=0.8,
+                    bed_rows=45) -> Workload:
+    """The single-orifice bubbling bed of the paper's §3.1 (Table 1):
+    0.00675 m x 0.027 m at h = 2.7e-4 m (25 x 100 cells), dt = 1.35e-6 s,
+    15,000 particles of 54 um and 930 kg/m^3 placed at rest by random
+    sequential addition in the lower ``bed_rows`` rows (2D area fraction 0.42
+    at 45 rows), gas 1.1795 kg/m^3, 1.8872e-5 Pa s, a bottom inlet at the
+    minimum fluidization velocity 0.0025 m/s with the central ``jet_cells``
+    cells (the 0.00081 m orifice) injecting at 0.8 m/s, a pressure outlet at
+    the top and walls at the sides.  The pulse length (0.006 s in §3.1) is
+    applied by the caller with lbdps_set_inlet (``background_inlet``)."""
+    h, dt = 2.7e-4, 1.35e-6
+    d_p = 54e-6
+    r = 0.5 * d_p
+    W = nx * h
+    pos = rsa(2, (W, ny * h), (r, r), (W - r, bed_rows * h), (0, 0), d_p * (1 + 1e-9),
+              n_particles, seed)
+    vel = np.zeros_like(pos)
+    inlet = np.zeros((nx, 2))
+    inlet[:, 1] = v_mf
+    j0 = nx // 2 - jet_cells // 2
+    inlet[j0:j0 + jet_cells, 1] = v_inj
+    return Workload(
+        name=f"bubbling-table1-{nx}x{ny}-N{n_particles}", dim=2, n=(nx, ny),
+        bc=(WALL, WALL, INLET, OUTLET, PERIODIC, PERIODIC), h=h, dt=dt, d_p=d_p,
+        rho_s=930.0, e=0.9, pos=pos, vel=vel, rho_g=1.1795, mu_g=1.8872e-5,
+        g=(0.0, -9.81, 0.0), u0=(0.0, v_mf, 0.0), inlet_u=inlet, cs_smag=cs_smag,
+        storage=storage, steps=steps, seed=seed)
+
+
+def background_inlet(w: Workload) -> np.ndarray:
+    """The inlet of a bubbling bed with the jet switched off: every inlet cell
+    at the background (minimum fluidization) velocity of its edge cells."""
+    u = np.array(w.inlet_u, dtype=np.float64)
+    u[:, :] = u[0, :]
+    return u
+
+
 def riser2d(nx=256, ny=2048, n_particles=200000, seed=SEED_BASE + 1, storage=STORE_F32,
             steps=10000, cs_smag=0.0, solid_fraction=0.05, u_gas=1.5, u_lat=0.0338,
             sigma_v=0.1, h=None) -> Workload:

@@ -776,3 +776,53 @@ def test_recirculation_needs_inlet_below_and_outlet_above():
     w = _cfb_column()
     with pytest.raises(Exception):
         O.OracleBed(w.with_(bc=(W.WALL, W.WALL, W.OUTLET, W.INLET, W.PERIODIC, W.PERIODIC)))
+
+
+def _counted_bed(counts, storage=W.STORE_F64):
+    """A Table 1 bed whose cell (x, y) holds counts[y, x] particles on a 4 x 4
+    sub-grid of the cell (spacing 0.25 > d = 0.2, so no two overlap)."""
+    ny, nx = counts.shape
+    w = W.bubbling_table1(nx=nx, ny=ny, n_particles=1, storage=storage)
+    pts = []
+    for y in range(ny):
+        for x in range(nx):
+            for k in range(int(counts[y, x])):
+                pts.append((x + 0.125 + 0.25 * (k % 4), y + 0.125 + 0.25 * (k // 4)))
+    pos = np.array(pts, dtype=np.float64).reshape(-1, 2) * w.h
+    return w.with_(pos=pos, vel=np.zeros_like(pos))
+
+
+def _scipy_bubbles(mask):
+    # independent reference: scipy's 4-connected labelling, regions touching
+    # the top row left out
+    ndimage = pytest.importorskip("scipy.ndimage")
+    lab, n = ndimage.label(mask)
+    top = set(lab[-1][lab[-1] > 0].tolist())
+    sizes = [int((lab == k).sum()) for k in range(1, n + 1) if k not in top]
+    return {"largest": max(sizes, default=0), "count": len(sizes), "cells": sum(sizes)}
+
+
+def test_bubbles_of_a_designed_bed():
+    # §3.1: regions with voidage above 0.85; two holes in a packed bed, the
+    # empty freeboard above it is not a bubble
+    counts = np.full((24, 12), 16)
+    counts[-5:, :] = 0                 # freeboard
+    counts[6:9, 4:7] = 0               # 3 x 3 hole
+    counts[0, 9:11] = 0                # 2 x 1 hole on the bottom row
+    bed = O.OracleBed(_counted_bed(counts))
+    assert bed.bubbles(0.85) == {"largest": 9, "count": 2, "cells": 11}
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_bubbles_match_scipy_labelling(seed):
+    rng = np.random.default_rng(seed)
+    counts = rng.integers(0, 17, size=(30, 14))
+    counts[rng.random(counts.shape) < 0.35] = 0
+    w = _counted_bed(counts)
+    bed = O.OracleBed(w)
+    r = 0.5 * w.d_p / w.h
+    eps2d = 1.0 - np.minimum(counts * math.pi * r * r, math.pi / (2 * math.sqrt(3)))
+    assert bed.bubbles(0.85, 0) == _scipy_bubbles(eps2d > 0.85)
+    # Eq. 11 voidage, written out independently
+    epsg = 1.0 - math.sqrt(2.0) / math.sqrt(math.pi * math.sqrt(3.0)) * (1.0 - eps2d) ** 1.5
+    assert bed.bubbles(0.97, 1) == _scipy_bubbles(epsg > 0.97)
