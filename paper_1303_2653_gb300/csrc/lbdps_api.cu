@@ -703,18 +703,15 @@ template <class L, class Real, class S> struct EngineT : Engine {
         const bool bed = H->prm.diagnostics && H->steps > 0;
         launch_reduce_all<L, Real, S>(lay, H->ncell, f[cur], part[cur], H->k.mp, H->np, cells(cur),
                                       sp.tab.eps_g, H->ntab, bed ? &fld : nullptr, red_partials,
-                                      red_ticket, red_out, H->stream);
+                                      red_ticket, health_dev, solids_out, red_out, H->stream);
         CHECK_LAUNCH();
         double *v = H->stats_host;
-        CU(cudaMemcpyAsync(v, red_out, sizeof(double) * 11, cudaMemcpyDeviceToHost, H->stream));
-        CU(cudaMemcpyAsync(H->health_host, health_word(), sizeof(unsigned), cudaMemcpyDeviceToHost,
-                           H->stream));
-        CU(cudaMemcpyAsync(v + 12, solids_out, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                           H->stream));
+        CU(cudaMemcpyAsync(v, red_out, sizeof(double) * 13, cudaMemcpyDeviceToHost, H->stream));
         CU(cudaStreamSynchronize(H->stream));
-        unsigned long long nout = 0;
-        std::memcpy(&nout, v + 12, sizeof(nout));
-        out->solids_out = (int64_t)nout;
+        unsigned long long raw[2] = {0, 0};
+        std::memcpy(raw, v + 11, sizeof(raw));
+        *H->health_host = (unsigned)raw[0];
+        out->solids_out = (int64_t)raw[1];
         out->mass = v[0] + (double)H->ncell;
         for (int a = 0; a < 3; ++a) {
             out->gas_momentum[a] = a < D ? v[1 + a] : 0.0;

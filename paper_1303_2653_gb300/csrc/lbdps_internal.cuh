@@ -332,7 +332,8 @@ void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int 
 template <class L, class Real, class S>
 void launch_reduce_all(const PopLayout &lay, int ncell, const S *f, Particles<Real> parts, double mp,
                        int np, CellList cells, const Real *eps_tab, int ntab,
-                       const Fields<Real> *bed, double *partials, unsigned *ticket, double *out,
+                       const Fields<Real> *bed, double *partials, unsigned *ticket,
+                       const unsigned *health, const unsigned long long *solids_out, double *out,
                        cudaStream_t st);
 
 int reduce_block_count(int n);

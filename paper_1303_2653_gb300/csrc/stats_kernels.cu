@@ -4,22 +4,22 @@
 //
 // Each thread accumulates over a grid-stride range of cells and particles (in
 // FP64 in the FP64 engine; in FP32 with Kahan compensation otherwise, since
-// FP64 arithmetic is slow on this part), the blocks reduce in a fixed order
-// to FP64 partials, and the block that finishes last (ticket counter, nothing
-// waits) sums the partials in a fixed tree.  The result does not depend on
-// scheduling.
+// FP64 arithmetic is slow on this part), each warp sums its lanes in the
+// arithmetic type, each block adds its warp totals in FP64 in a fixed order,
+// and the block that finishes last (ticket counter, nothing waits) adds the
+// block partials in block order.  The result does not depend on scheduling.
 #include "lbdps_internal.cuh"
 
 namespace lbdpsk {
 
 constexpr int kRedThreads = 256;
-constexpr int kRedMaxBlocks = 512;
+constexpr int kRedMaxBlocks = 1024;
 
 template <class Real> struct Acc;
 template <> struct Acc<double> {
     double s = 0.0;
     __device__ void add(double x) { s += x; }
-    __device__ double get() const { return s; }
+    __device__ double value() const { return s; }
 };
 // Kahan-compensated FP32 sum (Kahan 1965)
 template <> struct Acc<float> {
@@ -31,23 +31,16 @@ template <> struct Acc<float> {
         c = (t - s) - y;
         s = t;
     }
-    __device__ double get() const { return (double)s - (double)c; }
+    __device__ float value() const { return s - c; }
 };
 
-// Block sum of v in a fixed order (warp shuffles, then the warp totals);
-// the result is valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double *sh)
+// Sum over a warp in a fixed order (butterfly of shuffles): every lane
+// holds the total.
+template <class T> __device__ __forceinline__ T warp_sum(T v)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < kRedThreads / 32; ++w) t += sh[w];
-    return t;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // out: [0] sum of deviations f_i - w_i, [1..3] sum c_i f_i, [4..6] m_p sum v,
@@ -59,7 +52,8 @@ template <class L, class Real, class S, bool BED>
 __global__ void __launch_bounds__(kRedThreads)
 k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> parts, double mp,
              int np, CellList cells, const Real *__restrict__ eps_tab, int ntab, Fields<Real> fld,
-             double *partials, unsigned *ticket, double *out)
+             double *partials, unsigned *ticket, const unsigned *health,
+             const unsigned long long *solids_out, double *out)
 {
     constexpr int D = L::D, Q = L::Q;
     Acc<Real> acc[kStatValues];
@@ -107,13 +101,24 @@ k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> 
         for (int a = 0; a < D; ++a) acc[4 + a].add(parts.v[a][k]);
     }
 
-    __shared__ double sh[kRedThreads / 32];
+    // block partials: warp sums in the arithmetic type, then the eight warp
+    // totals of each value added in FP64 in warp order (one barrier)
+    constexpr int kWarps = kRedThreads / 32;
+    __shared__ double sh[kWarps][kStatValues];
     __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kStatValues; ++k) {
-        const double t = block_sum(acc[k].get(), sh);
-        if (threadIdx.x == 0) partials[blockIdx.x * kStatValues + k] = t;
+        const Real t = warp_sum<Real>(acc[k].value());
+        if (lane == 0) sh[warp][k] = (double)t;
     }
+    __syncthreads();
+    if (threadIdx.x < kStatValues) {
+        double t = 0.0;
+        for (int w = 0; w < kWarps; ++w) t += sh[w][threadIdx.x];
+        partials[blockIdx.x * kStatValues + threadIdx.x] = t;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         last = atomicAdd(ticket, 1u) == gridDim.x - 1;
@@ -121,40 +126,59 @@ k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    const int nb = gridDim.x;
-#pragma unroll 1
+    // the last block: each thread adds the partials of a fixed subset of
+    // blocks (b = thread, thread + 256, ...), then warps and the block add
+    // those in a fixed order, value by value
     for (int k = 0; k < kStatValues; ++k) {
-        double v = 0.0;
-        for (int b = threadIdx.x; b < nb; b += kRedThreads)
-            v += __ldcg(partials + b * kStatValues + k);
-        const double t = block_sum(v, sh);
-        if (threadIdx.x == 0) out[k] = (k >= 4 && k < 7) ? mp * t : t;
+        double t = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += kRedThreads)
+            t += __ldcg(partials + b * kStatValues + k);
+        t = warp_sum<double>(t);
+        __syncthreads();
+        if (lane == 0) sh[warp][0] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double u = 0.0;
+            for (int w = 0; w < kWarps; ++w) u += sh[w][0];
+            out[k] = (k >= 4 && k < 7) ? mp * u : u;
+        }
     }
-    if (threadIdx.x == 0) *ticket = 0u;
+    if (threadIdx.x == 0) {
+        // the health word and the outlet count travel with the values, so
+        // that the host reads everything with one copy
+        unsigned long long *raw = reinterpret_cast<unsigned long long *>(out);
+        raw[kStatValues] = *health;
+        raw[kStatValues + 1] = *solids_out;
+        *ticket = 0u;
+    }
 }
 
 template <class L, class Real, class S>
 void launch_reduce_all(const PopLayout &lay, int ncell, const S *f, Particles<Real> parts, double mp,
                        int np, CellList cells, const Real *eps_tab, int ntab,
-                       const Fields<Real> *bed, double *partials, unsigned *ticket, double *out,
+                       const Fields<Real> *bed, double *partials, unsigned *ticket,
+                       const unsigned *health, const unsigned long long *solids_out, double *out,
                        cudaStream_t st)
 {
     const int n = ncell > np ? ncell : np;
-    int nb = (n + kRedThreads * 4 - 1) / (kRedThreads * 4);
+    int nb = (n + kRedThreads - 1) / kRedThreads;
     nb = nb < 1 ? 1 : (nb > kRedMaxBlocks ? kRedMaxBlocks : nb);
     if (bed)
         k_reduce_all<L, Real, S, true><<<nb, kRedThreads, 0, st>>>(
-            lay, ncell, f, parts, mp, np, cells, eps_tab, ntab, *bed, partials, ticket, out);
+            lay, ncell, f, parts, mp, np, cells, eps_tab, ntab, *bed, partials, ticket, health,
+            solids_out, out);
     else
         k_reduce_all<L, Real, S, false><<<nb, kRedThreads, 0, st>>>(
-            lay, ncell, f, parts, mp, np, cells, eps_tab, ntab, Fields<Real>{}, partials, ticket, out);
+            lay, ncell, f, parts, mp, np, cells, eps_tab, ntab, Fields<Real>{}, partials, ticket,
+            health, solids_out, out);
 }
 
 #define LBDPS_INST_RED(L, R, S)                                                                    \
     template void launch_reduce_all<L, R, S>(const PopLayout &, int, const S *, Particles<R>,       \
                                              double, int, CellList, const R *, int,                \
-                                             const Fields<R> *, double *, unsigned *, double *,     \
-                                             cudaStream_t);
+                                             const Fields<R> *, double *, unsigned *,               \
+                                             const unsigned *, const unsigned long long *,          \
+                                             double *, cudaStream_t);
 LBDPS_INST_RED(D2Q9, double, double)
 LBDPS_INST_RED(D2Q9, float, float)
 LBDPS_INST_RED(D2Q9, float, __half)
