@@ -104,22 +104,6 @@ __device__ __forceinline__ double sep_axis(double pi, double pj, bool periodic, 
 // p = rho/3 (one-sided next to non-periodic faces).  1 - eps is interpolated
 // from the tabulated solid fraction so that it needs no cancellation.
 // ---------------------------------------------------------------------------
-template <class Real>
-__device__ __forceinline__ Real node_gradp(const StepParams<Real> &p, const Real *rho, const int *q,
-                                           int a)
-{
-    if (p.n[a] == 1) return Real(0);
-    const int stride = (a == 0) ? 1 : (a == 1) ? p.n[0] : p.n[0] * p.n[1];
-    const int x = q[0] + p.n[0] * (q[1] + p.n[1] * q[2]);
-    int lo = q[a] - 1, hi = q[a] + 1;
-    Real scale = Real(1) / Real(6);        // (1/3) / 2: central difference of rho/3
-    const bool per = (p.bc[2 * a] == BC_PERIODIC);
-    if (lo < 0) { if (per) lo += p.n[a]; else { lo = q[a]; scale = Real(1) / Real(3); } }
-    if (hi >= p.n[a]) { if (per) hi -= p.n[a]; else { hi = q[a]; scale = Real(1) / Real(3); } }
-    const int xl = x + (lo - q[a]) * stride, xh = x + (hi - q[a]) * stride;
-    return (__ldg(rho + xh) - __ldg(rho + xl)) * scale;
-}
-
 template <int D, class Real>
 __device__ __forceinline__ void drag_pre_one(const StepParams<Real> &p, const Particles<Real> &parts,
                                              const Fields<Real> &fld, const int *idx,
@@ -147,24 +131,58 @@ __device__ __forceinline__ void drag_pre_one(const StepParams<Real> &p, const Pa
     }
     Real uk[3] = {Real(0), Real(0), Real(0)}, gk[3] = {Real(0), Real(0), Real(0)};
     Real sk = Real(0), bk = Real(0);     // interpolated 1 - eps and beta
+    constexpr int NC = 1 << D;
+    int node[NC];
+    Real R[NC], wt[NC];
 #pragma unroll
-    for (int corner = 0; corner < (1 << D); ++corner) {
+    for (int corner = 0; corner < NC; ++corner) {
         int q[3] = {0, 0, 0};
-        Real wt = Real(1);
+        Real w = Real(1);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             const int bit = (corner >> a) & 1;
             q[a] = bit ? i1[a] : i0[a];
-            wt *= bit ? w1[a] : (Real(1) - w1[a]);
+            w *= bit ? w1[a] : (Real(1) - w1[a]);
         }
-        const int node = q[0] + p.n[0] * (q[1] + p.n[1] * q[2]);
+        wt[corner] = w;
+        node[corner] = q[0] + p.n[0] * (q[1] + p.n[1] * q[2]);
+        R[corner] = __ldg(fld.rho + node[corner]);
+#pragma unroll
+        for (int a = 0; a < D; ++a) uk[a] += w * __ldg(fld.uact[a] + node[corner]);
+        sk += w * __ldg(fld.solg + node[corner]);
+        bk += w * __ldg(fld.beta + node[corner]);
+    }
+    // grad p at each node: central differences of rho/3 (one-sided next to a
+    // non-periodic face); in 3D a neighbour that is itself a stencil node is
+    // taken from R instead of being loaded again
+#pragma unroll
+    for (int corner = 0; corner < NC; ++corner) {
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            uk[a] += wt * __ldg(fld.uact[a] + node);
-            gk[a] += wt * node_gradp<Real>(p, fld.rho, q, a);
+            if (p.n[a] == 1) continue;
+            const int bit = (corner >> a) & 1;
+            const int q = bit ? i1[a] : i0[a];
+            const int stride = (a == 0) ? 1 : (a == 1) ? p.n[0] : p.n[0] * p.n[1];
+            int lo = q - 1, hi = q + 1;
+            Real scale = Real(1) / Real(6);    // (1/3) / 2: central difference of rho/3
+            const bool per = (p.bc[2 * a] == BC_PERIODIC);
+            if (lo < 0) { if (per) lo += p.n[a]; else { lo = q; scale = Real(1) / Real(3); } }
+            if (hi >= p.n[a]) { if (per) hi -= p.n[a]; else { hi = q; scale = Real(1) / Real(3); } }
+            const int x = node[corner];
+            Real rh, rl;
+            if (D == 2) {   // 2D: the plain loads schedule better than the selects
+                rh = __ldg(fld.rho + x + (hi - q) * stride);
+                rl = __ldg(fld.rho + x + (lo - q) * stride);
+            } else {
+                if (hi == q) rh = R[corner];
+                else if (!bit && hi == i1[a]) rh = R[corner | (1 << a)];
+                else rh = __ldg(fld.rho + x + (hi - q) * stride);
+                if (lo == q) rl = R[corner];
+                else if (bit && lo == i0[a]) rl = R[corner & ~(1 << a)];
+                else rl = __ldg(fld.rho + x + (lo - q) * stride);
+            }
+            gk[a] += wt[corner] * ((rh - rl) * scale);
         }
-        sk += wt * __ldg(fld.solg + node);
-        bk += wt * __ldg(fld.beta + node);
     }
     const Real coef = p.vp * bk / sk;   // V_p beta_k / (1 - eps_k), Eq. 26
 #pragma unroll
