@@ -234,12 +234,9 @@ template <class L, class Real, class S> struct EngineT : Engine {
                 return fail(LBDPS_ERR_OOM, "device allocation failed");
         }
         fld.rho = (Real *)get(sizeof(Real) * nc);
-        fld.beta = (Real *)get(sizeof(Real) * nc);
-        fld.solg = (Real *)get(sizeof(Real) * nc);
-        for (int a = 0; a < D; ++a) {
-            fld.uact[a] = (Real *)get(sizeof(Real) * nc);
-            fld.fpg[a] = (Real *)get(sizeof(Real) * nc);
-        }
+        fld.node4 = (typename Vec4<Real>::type *)get(sizeof(typename Vec4<Real>::type) * nc);
+        fld.solg = D == 3 ? (Real *)get(sizeof(Real) * nc) : nullptr;
+        for (int a = 0; a < D; ++a) fld.fpg[a] = (Real *)get(sizeof(Real) * nc);
         if (H->prm.diagnostics) {
             fld.tau_t = (Real *)get(sizeof(Real) * nc);
             fld.eps_g = (Real *)get(sizeof(Real) * nc);
@@ -272,16 +269,17 @@ template <class L, class Real, class S> struct EngineT : Engine {
         solids_out = (unsigned long long *)get(sizeof(unsigned long long));
         npairs_dev = (unsigned long long *)get(sizeof(unsigned long long));
         void *must[] = {f[0], f[1], cl_local[0], cl_local[1], cl_base[0], cl_base[1], fld.rho,
-                        fld.beta, fld.solg, key, counts, slot, idslot, tile_total, ticket,
+                        fld.node4, key, counts, slot, idslot, tile_total, ticket,
                         best, wall, tab_branch, inlet_dev, health_dev,
                         red_partials, red_out, red_ticket, solids_out, npairs_dev, part[0].id, part[1].id,
                         part[0].cell, part[1].cell};
         for (void *p : must)
             if (!p) return fail(LBDPS_ERR_OOM, "device allocation failed");
         for (int a = 0; a < D; ++a)
-            if (!fld.uact[a] || !fld.fpg[a] || !part[0].P[a] || !part[1].P[a] || !part[0].v[a] ||
+            if (!fld.fpg[a] || !part[0].P[a] || !part[1].P[a] || !part[0].v[a] ||
                 !part[1].v[a] || !part[0].off[a] || !part[1].off[a])
                 return fail(LBDPS_ERR_OOM, "device allocation failed");
+        if (D == 3 && !fld.solg) return fail(LBDPS_ERR_OOM, "device allocation failed");
         for (int t = 0; t < 10; ++t)
             if (!tabs[t]) return fail(LBDPS_ERR_OOM, "device allocation failed");
         if (!tab_pk[0] || !tab_pk[1]) return fail(LBDPS_ERR_OOM, "device allocation failed");
@@ -582,11 +580,28 @@ template <class L, class Real, class S> struct EngineT : Engine {
             o += nc * D;
             return LBDPS_OK;
         };
+        // components of the node record: beta is .w, u_act is .x, .y (, .z)
+        using V4 = typename Vec4<Real>::type;
+        std::vector<V4> h4;
+        auto put_node = [&](int first, int count, double scale) -> int {
+            if (h4.empty()) {
+                h4.resize(nc);
+                CU(cudaMemcpyAsync(h4.data(), fld.node4, sizeof(V4) * nc, cudaMemcpyDeviceToHost,
+                                   H->stream));
+                CU(cudaStreamSynchronize(H->stream));
+            }
+            for (size_t x = 0; x < nc; ++x) {
+                const Real c4[4] = {h4[x].x, h4[x].y, h4[x].z, h4[x].w};
+                for (int a = 0; a < count; ++a) out[o + x * count + a] = (double)c4[first + a] * scale;
+            }
+            o += nc * count;
+            return LBDPS_OK;
+        };
         int rc = LBDPS_OK;
         if (mask & LBDPS_FIELD_RHO) if ((rc = put_scalar(fld.rho, rs))) return rc;
         if (mask & LBDPS_FIELD_U) if ((rc = put_vec(fld.u, us))) return rc;
         if (mask & LBDPS_FIELD_FPG) if ((rc = put_vec(fld.fpg, fs))) return rc;
-        if (mask & LBDPS_FIELD_BETA) if ((rc = put_scalar(fld.beta, bs))) return rc;
+        if (mask & LBDPS_FIELD_BETA) if ((rc = put_node(3, 1, bs))) return rc;
         if (mask & LBDPS_FIELD_VS) if ((rc = put_vec(fld.vs, us))) return rc;
         if (mask & LBDPS_FIELD_NTOT) {
             if ((rc = d2h(hi, fld.ntot, nc))) return rc;
@@ -594,7 +609,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
             o += nc;
         }
         if (mask & LBDPS_FIELD_TAU_T) if ((rc = put_scalar(fld.tau_t, ts))) return rc;
-        if (mask & LBDPS_FIELD_UACT) if ((rc = put_vec(fld.uact, us))) return rc;
+        if (mask & LBDPS_FIELD_UACT) if ((rc = put_node(0, D, us))) return rc;
         if (mask & LBDPS_FIELD_EPS_G) if ((rc = put_scalar(fld.eps_g, 1.0))) return rc;
         return LBDPS_OK;
     }

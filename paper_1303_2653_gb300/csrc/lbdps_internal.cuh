@@ -215,8 +215,13 @@ __host__ __device__ inline void cell_voidage(int dim, double r, double vp, int n
 }
 
 // Device buffers of one bed.
+// node4 is the record the drag reads at each stencil node, one 16-byte (FP32)
+// load: {u_act,x, u_act,y, 1 - eps, beta} in 2D and {u_act,x, u_act,y,
+// u_act,z, beta} in 3D, where 1 - eps is in solg.
 template <class Real> struct Fields {
-    Real *rho, *uact[3], *fpg[3], *beta, *solg;         // node outputs of the collision
+    Real *rho, *fpg[3];                                 // node outputs of the collision
+    typename Vec4<Real>::type *node4;
+    Real *solg;                                         // 3D only (null in 2D)
     Real *vs[3], *tau_t, *u[3], *eps_g;                 // diagnostics (may be null)
     int *ntot;                                          // diagnostics (may be null)
 };

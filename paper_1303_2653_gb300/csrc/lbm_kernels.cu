@@ -347,17 +347,16 @@ k_collide_stream(StepParams<Real> p, PopLayout lay, PopPtrs<S> pp, CellList cell
     // interpolation reads u_act, beta and 1 - eps of each stencil node from
     // these arrays alone (no cell-list or table lookups).
     const Real inv_div = t0.z;
-    Real slip2 = Real(0);
+    Real slip2 = Real(0), ua[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         fld.fpg[a][x] = og * (rho * u[a] + rho * vs[a] - Real(2) * m[a]);
-        const Real ua = u[a] * inv_div;
-        fld.uact[a][x] = ua;
-        const Real sl = ua - vs[a];
+        ua[a] = u[a] * inv_div;
+        const Real sl = ua[a] - vs[a];
         slip2 += sl * sl;
     }
     fld.rho[x] = rho;
-    fld.solg[x] = p.tab.sol_g[nn];
+    const Real solg = p.tab.sol_g[nn];
     const Real slip = sqrt_pos(slip2);
     Real beta;
     if (t1.w == Real(0)) {
@@ -367,7 +366,12 @@ k_collide_stream(StepParams<Real> p, PopLayout lay, PopPtrs<S> pp, CellList cell
         beta = (re < Real(1000)) ? t0.w * (Real(1) + Real(0.15) * re_pow(re))   // Eq. 19, 21
                                  : t1.y * slip;
     }
-    fld.beta[x] = beta;
+    if (D == 2) {
+        fld.node4[x] = {ua[0], ua[1], solg, beta};
+    } else {
+        fld.node4[x] = {ua[0], ua[1], ua[2], beta};
+        fld.solg[x] = solg;
+    }
 
     // ---- LES (Eq. 13-15) ----
     Real inv_tau_t = p.inv_tau, gam_t = t0.y, tau_t = p.tau;

@@ -147,10 +147,16 @@ __device__ __forceinline__ void drag_pre_one(const StepParams<Real> &p, const Pa
         wt[corner] = w;
         node[corner] = q[0] + p.n[0] * (q[1] + p.n[1] * q[2]);
         R[corner] = __ldg(fld.rho + node[corner]);
-#pragma unroll
-        for (int a = 0; a < D; ++a) uk[a] += w * __ldg(fld.uact[a] + node[corner]);
-        sk += w * __ldg(fld.solg + node[corner]);
-        bk += w * __ldg(fld.beta + node[corner]);
+        const auto r4 = fld.node4[node[corner]];   // u_act, 1 - eps, beta of the node
+        uk[0] += w * r4.x;
+        uk[1] += w * r4.y;
+        if (D == 3) {
+            uk[2] += w * r4.z;
+            sk += w * __ldg(fld.solg + node[corner]);
+        } else {
+            sk += w * r4.z;
+        }
+        bk += w * r4.w;
     }
     // grad p at each node: central differences of rho/3 (one-sided next to a
     // non-periodic face); in 3D a neighbour that is itself a stencil node is

@@ -85,10 +85,12 @@ k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> 
             acc[8].add(fld.eps_g[x]);
             const int nt = fld.ntot[x];
             if (nt > 0) {
+                const auto r4 = fld.node4[x];
+                const Real ua[3] = {r4.x, r4.y, D == 3 ? r4.z : Real(0)};
                 Real s2 = Real(0);
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
-                    const Real d = fld.uact[a][x] - fld.vs[a][x];
+                    const Real d = ua[a] - fld.vs[a][x];
                     s2 += d * d;
                 }
                 acc[9].add(Real(nt) * sqrt(s2));
