@@ -164,7 +164,8 @@ struct lbdps {
     int parity = 0;
     int64_t steps = 0;
     int64_t since_check = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step, per starting parity
+    cudaGraphExec_t chunk[2] = {nullptr, nullptr};   // kChunkSteps steps, per starting parity
     int recirculate = 0;               // outlet -> inlet re-injection of particles
     unsigned *health_host = nullptr;   // pinned: the health word, then 16 doubles of statistics
     double *stats_host = nullptr;      // inside the same pinned block
@@ -263,8 +264,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
         const int nface = (int)(H->inlet_lat.size() / D);
         inlet_dev = (Real *)get(sizeof(Real) * D * std::max(nface, 1));
         health_dev = (unsigned *)get(sizeof(unsigned));
-        red_partials = (double *)get(sizeof(double) * 16 * 512);   // values x blocks of the reduction
-        red_out = (double *)get(sizeof(double) * 16);
+        red_partials = (double *)get(sizeof(double) * kStatPartials);
+        red_out = (double *)get(sizeof(double) * kStatOut);
         red_ticket = (unsigned *)get(sizeof(unsigned));
         solids_out = (unsigned long long *)get(sizeof(unsigned long long));
         npairs_dev = (unsigned long long *)get(sizeof(unsigned long long));
@@ -721,7 +722,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
                                       red_ticket, health_dev, solids_out, red_out, H->stream);
         CHECK_LAUNCH();
         double *v = H->stats_host;
-        CU(cudaMemcpyAsync(v, red_out, sizeof(double) * 13, cudaMemcpyDeviceToHost, H->stream));
+        CU(cudaMemcpyAsync(v, red_out, sizeof(double) * kStatOut, cudaMemcpyDeviceToHost, H->stream));
         CU(cudaStreamSynchronize(H->stream));
         unsigned long long raw[2] = {0, 0};
         std::memcpy(raw, v + 11, sizeof(raw));
@@ -936,40 +937,74 @@ int validate_positions(const lbdps *h, const double *pos, bool check_overlap)
     return LBDPS_OK;
 }
 
+// Steps replayed by one launch of a chunk graph when a call asks for at least
+// as many (an even count, so a chunk ends on the parity it started from).
+constexpr int kChunkSteps = 16;
+
+int capture_steps(lbdps *h, int nsteps, cudaGraphExec_t *out)
+{
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = LBDPS_OK;
+    for (int s = 0; s < nsteps && rc == LBDPS_OK; ++s) rc = h->eng->enqueue_step((h->parity + s) & 1, nullptr);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(LBDPS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(LBDPS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return LBDPS_OK;
+}
+
+int check_health(lbdps *h)
+{
+    int hw = 0;
+    int rc = lbdps_health(h, &hw);
+    if (rc) return rc;
+    if (hw & HEALTH_DIVERGED) return fail(LBDPS_ERR_DIVERGED, "gas state diverged by step %lld", (long long)h->steps);
+    if (hw & HEALTH_DOMAIN) return fail(LBDPS_ERR_DOMAIN, "a particle left the domain by step %lld", (long long)h->steps);
+    return LBDPS_OK;
+}
+
 int run_steps(lbdps *h, int64_t nsteps)
 {
-    for (int64_t s = 0; s < nsteps; ++s) {
-        if (h->prm.use_graph) {
-            if (!h->graph[h->parity]) {
-                cudaGraph_t g = nullptr;
-                CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-                int rc = h->eng->enqueue_step(h->parity, nullptr);
-                cudaError_t e = cudaStreamEndCapture(h->stream, &g);
-                if (rc) {
-                    if (g) cudaGraphDestroy(g);
-                    return rc;
-                }
-                if (e != cudaSuccess)
-                    return fail(LBDPS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-                e = cudaGraphInstantiate(&h->graph[h->parity], g, 0);
-                cudaGraphDestroy(g);
-                if (e != cudaSuccess)
-                    return fail(LBDPS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    const int ce = h->prm.check_every;
+    for (int64_t s = 0; s < nsteps;) {
+        // a chunk when the call and the next health check leave room for one
+        const bool chunk = h->prm.use_graph && nsteps - s >= kChunkSteps &&
+                           (ce <= 0 || ce - h->since_check >= kChunkSteps);
+        if (chunk) {
+            if (!h->chunk[h->parity]) {
+                int rc = capture_steps(h, kChunkSteps, &h->chunk[h->parity]);
+                if (rc) return rc;
             }
-            CU(cudaGraphLaunch(h->graph[h->parity], h->stream));
+            CU(cudaGraphLaunch(h->chunk[h->parity], h->stream));
+            s += kChunkSteps;
+            h->steps += kChunkSteps;
+            if (ce > 0) h->since_check += kChunkSteps;
         } else {
-            int rc = h->eng->enqueue_step(h->parity, nullptr);
-            if (rc) return rc;
+            if (h->prm.use_graph) {
+                if (!h->graph[h->parity]) {
+                    int rc = capture_steps(h, 1, &h->graph[h->parity]);
+                    if (rc) return rc;
+                }
+                CU(cudaGraphLaunch(h->graph[h->parity], h->stream));
+            } else {
+                int rc = h->eng->enqueue_step(h->parity, nullptr);
+                if (rc) return rc;
+            }
+            h->parity ^= 1;
+            s += 1;
+            h->steps++;
+            if (ce > 0) h->since_check += 1;
         }
-        h->parity ^= 1;
-        h->steps++;
-        if (h->prm.check_every > 0 && ++h->since_check >= h->prm.check_every) {
+        if (ce > 0 && h->since_check >= ce) {
             h->since_check = 0;
-            int hw = 0;
-            int rc = lbdps_health(h, &hw);
+            int rc = check_health(h);
             if (rc) return rc;
-            if (hw & HEALTH_DIVERGED) return fail(LBDPS_ERR_DIVERGED, "gas state diverged by step %lld", (long long)h->steps);
-            if (hw & HEALTH_DOMAIN) return fail(LBDPS_ERR_DOMAIN, "a particle left the domain by step %lld", (long long)h->steps);
         }
     }
     return LBDPS_OK;
@@ -977,11 +1012,16 @@ int run_steps(lbdps *h, int64_t nsteps)
 
 void free_graphs(lbdps *h)
 {
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < 2; ++p) {
         if (h->graph[p]) {
             cudaGraphExecDestroy(h->graph[p]);
             h->graph[p] = nullptr;
         }
+        if (h->chunk[p]) {
+            cudaGraphExecDestroy(h->chunk[p]);
+            h->chunk[p] = nullptr;
+        }
+    }
 }
 
 }  // namespace
@@ -1175,6 +1215,7 @@ int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
         cudaGetLastError();
         return cleanup(fail(LBDPS_ERR_OOM, "pinned allocation failed"));
     }
+    static_assert(sizeof(double) * kStatOut <= 128, "statistics fit the pinned block");
     h->stats_host = reinterpret_cast<double *>(reinterpret_cast<char *>(h->health_host) + 128);
     if ((rc = h->eng->upload_initial(pos.data(), vel.data()))) {
         cudaFreeHost(h->health_host);

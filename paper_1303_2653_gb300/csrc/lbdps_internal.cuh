@@ -331,6 +331,14 @@ template <int D, class Real>
 void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int *best,
                     const int *wall, int np, cudaStream_t st);
 
+// Sizes of the statistics buffers: the reduction runs at most
+// kStatMaxBlocks blocks, each writing kStatValues partials; out holds
+// kStatValues values plus the health word and the outlet count.
+constexpr int kStatValues = 11;
+constexpr int kStatMaxBlocks = 1024;
+constexpr int kStatPartials = kStatValues * kStatMaxBlocks;
+constexpr int kStatOut = kStatValues + 2;
+
 // All bed statistics in one launch (values listed in stats_kernels.cu); bed
 // = the diagnostic fields or null; ticket must be zero on entry and is zero
 // again on exit.

@@ -13,7 +13,7 @@
 namespace lbdpsk {
 
 constexpr int kRedThreads = 256;
-constexpr int kRedMaxBlocks = 1024;
+constexpr int kRedMaxBlocks = kStatMaxBlocks;
 
 template <class Real> struct Acc;
 template <> struct Acc<double> {
@@ -45,8 +45,7 @@ template <class T> __device__ __forceinline__ T warp_sum(T v)
 
 // out: [0] sum of deviations f_i - w_i, [1..3] sum c_i f_i, [4..6] m_p sum v,
 // [7] sum of eps_g of the current counts, [8] sum of the diagnostic eps_g,
-// [9] sum n |u_act - v_s|, [10] sum n
-constexpr int kStatValues = 11;
+// [9] sum n |u_act - v_s|, [10] sum n (kStatValues = 11)
 
 template <class L, class Real, class S, bool BED>
 __global__ void __launch_bounds__(kRedThreads)

@@ -351,6 +351,27 @@ def test_no_particles_and_graph_vs_eager():
     e.close()
 
 
+@pytest.mark.parametrize("check_every", [0, 24])
+def test_chunked_steps_equal_single_steps(check_every):
+    # lbdps_step replays 16-step chunk graphs when it can; the state must be
+    # that of the same steps launched one at a time (eager)
+    L = _lb()
+    w = W.scaled_riser2d(nx=32, ny=64, seed=41)
+    a = L.Bed(w, check_every=check_every)
+    b = L.Bed(w, use_graph=False)
+    a.step(53)
+    for _ in range(53):
+        b.step(1)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    Pa, va = a.particles()
+    Pb, vb = b.particles()
+    np.testing.assert_array_equal(Pa, Pb)
+    np.testing.assert_array_equal(va, vb)
+    assert a.stats()["steps"] == 53
+    a.close()
+    b.close()
+
+
 def test_create_rejects_invalid():
     L = _lb()
     w = W.scaled_riser2d(nx=32, ny=64)
