@@ -216,6 +216,13 @@ int lbdps_bubbles(lbdps_t *h, double threshold, int voidage, int64_t out[3]);
  * LBDPS_ERR_INVALID if the bed has no inlet or |u| >= 0.3 in lattice units. */
 int lbdps_set_inlet(lbdps_t *h, const double *inlet_u);
 
+/* Self-check of the handle's device memory (not in the paper): every block
+ * the handle allocated is followed by a 256-byte guard zone written with a
+ * fixed pattern at creation; *damaged receives the number of blocks whose
+ * guard no longer holds it (a kernel wrote past the end of a buffer).  For
+ * tests; waits for the handle's stream. */
+int lbdps_check_guards(lbdps_t *h, int *damaged);
+
 /* Copy the particle state (section 2.2: P, v) in id order, n x dim each.
  * cap is the capacity of each array in particles. */
 int lbdps_particles(lbdps_t *h, int units, double *pos, double *vel, int64_t cap);

@@ -81,19 +81,27 @@ Derived derive(const lbdps_lattice_desc &L, const lbdps_particle_desc &Pd, const
     return k;
 }
 
+// Every block carries a guard zone of kGuardBytes right after the bytes that
+// were asked for, filled with kGuardByte at allocation; lbdps_check_guards
+// reports blocks whose guard was overwritten (a kernel that wrote past the
+// end of its buffer).
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+
 struct DeviceAlloc {
     void *(*alloc)(size_t, void *) = nullptr;
     void (*release)(void *, void *) = nullptr;
     void *ctx = nullptr;
     std::vector<void *> owned;
+    std::vector<std::pair<char *, size_t>> guards;   // guard start, bytes asked for
     bool count_only = false;     // only add up the sizes (memory estimate)
     bool misaligned = false;     // params.alloc returned a block off a 256-byte boundary
     size_t counted = 0;
+    cudaStream_t stream = nullptr;   // the handle's stream: guards are written on it
 
-    void *get(size_t bytes)
+    void *get(size_t asked)
     {
-        bytes = (bytes + 255) & ~size_t(255);
-        if (bytes == 0) bytes = 256;
+        size_t bytes = ((asked + kGuardBytes) + 255) & ~size_t(255);
         if (count_only) {
             counted += bytes;
             return (void *)(uintptr_t)256;   // never dereferenced
@@ -110,8 +118,36 @@ struct DeviceAlloc {
             cudaGetLastError();
             p = nullptr;
         }
-        if (p) owned.push_back(p);
+        if (p) {
+            owned.push_back(p);
+            char *g = static_cast<char *>(p) + asked;
+            if (cudaMemsetAsync(g, kGuardByte, kGuardBytes, stream) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            guards.emplace_back(g, asked);
+        }
         return p;
+    }
+    // number of blocks whose guard zone no longer holds kGuardByte
+    int damaged(cudaStream_t st, int *bad) const
+    {
+        std::vector<unsigned char> h(kGuardBytes);
+        int n = 0;
+        for (const auto &g : guards) {
+            if (cudaMemcpyAsync(h.data(), g.first, kGuardBytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                cudaGetLastError();
+                return -1;
+            }
+            for (unsigned char c : h)
+                if (c != kGuardByte) {
+                    ++n;
+                    break;
+                }
+        }
+        *bad = n;
+        return 0;
     }
     void release_all()
     {
@@ -121,6 +157,7 @@ struct DeviceAlloc {
             else cudaFree(p);
         }
         owned.clear();
+        guards.clear();
     }
 };
 
@@ -1198,6 +1235,7 @@ int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
     h->mem.alloc = prm->alloc;
     h->mem.release = prm->free;
     h->mem.ctx = prm->alloc_ctx;
+    h->mem.stream = h->stream;
     h->eng.reset(D == 2 ? make_engine_l<D2Q9>(h.get()) : make_engine_l<D3Q19>(h.get()));
     if (!h->eng) return fail(LBDPS_ERR_OOM, "engine allocation failed");
     auto cleanup = [&](int code) {
@@ -1358,6 +1396,13 @@ int lbdps_health(lbdps_t *h, int *health)
     int rc = h->eng->health(&hw);
     if (rc) return rc;
     *health = (int)hw;
+    return LBDPS_OK;
+}
+
+int lbdps_check_guards(lbdps_t *h, int *damaged)
+{
+    if (!h || !damaged) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    if (h->mem.damaged(h->stream, damaged)) return fail(LBDPS_ERR_CUDA, "guard read-back failed");
     return LBDPS_OK;
 }
 

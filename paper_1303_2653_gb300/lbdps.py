@@ -118,6 +118,7 @@ def lib():
             "lbdps_record_event": ([vp, vp], i),
             "lbdps_bubbles": ([vp, ctypes.c_double, i, ctypes.POINTER(ctypes.c_int64)], i),
             "lbdps_set_inlet": ([vp, _dp], i),
+            "lbdps_check_guards": ([vp, ctypes.POINTER(i)], i),
             "lbdps_server_create": ([sz, i, i, ctypes.POINTER(vp)], i),
             "lbdps_server_submit": ([vp, ctypes.POINTER(LatticeDesc), ctypes.POINTER(ParticleDesc),
                                      ctypes.POINTER(Params), i64, i, ctypes.POINTER(ctypes.c_uint64)], i),
@@ -383,6 +384,12 @@ class Bed:
         out = (ctypes.c_int64 * 3)()
         _check(lib().lbdps_bubbles(self._h, float(threshold), int(voidage), out), "lbdps_bubbles")
         return {"largest": int(out[0]), "count": int(out[1]), "cells": int(out[2])}
+
+    def check_guards(self) -> int:
+        """Number of device buffers written past their end (0 when sound)."""
+        n = ctypes.c_int()
+        _check(lib().lbdps_check_guards(self._h, ctypes.byref(n)), "lbdps_check_guards")
+        return n.value
 
     def set_inlet(self, inlet_u) -> None:
         u = np.ascontiguousarray(inlet_u, dtype=np.float64)

@@ -212,6 +212,7 @@ def test_one_step_parity(name, storage):
         if mism.any():
             frac = np.abs(Po[mism] - np.round(Po[mism]))
             assert frac.min(axis=1).max() < 1e-4
+    assert bed.check_guards() == 0
     bed.close()
 
 
@@ -370,6 +371,29 @@ def test_chunked_steps_equal_single_steps(check_every):
     assert a.stats()["steps"] == 53
     a.close()
     b.close()
+
+
+def test_no_kernel_writes_past_its_buffers():
+    # every device block carries a guard zone; run each entry point that
+    # launches kernels on beds large enough for the multi-block paths (the
+    # statistics reduction runs its maximum of 1,024 blocks above 262,144
+    # cells) and check that no guard was touched
+    L = _lb()
+    for w, st in [(W.riser2d(nx=256, ny=1536, n_particles=100000), W.STORE_F32),
+                  (W.scaled_riser3d(nx=48, ny=48, nz=128), W.STORE_F16),
+                  (W.bubbling_table1(nx=25, ny=100, n_particles=3000, bed_rows=40), W.STORE_F64)]:
+        bed = L.Bed(w, storage=st, diagnostics=True)
+        bed.step(3)
+        bed.stats()
+        bed.fields(L.FIELD_RHO | L.FIELD_UACT | L.FIELD_BETA | L.FIELD_FPG | L.FIELD_U)
+        bed.populations()
+        bed.particles()
+        bed.bubbles(0.85)
+        bed.collide_particles()
+        bed.step(17)
+        bed.stats()
+        assert bed.check_guards() == 0
+        bed.close()
 
 
 def test_create_rejects_invalid():
