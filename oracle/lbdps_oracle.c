@@ -82,6 +82,8 @@ typedef struct {
     int superficial_mode;    /* 0: u / eps_2d, 1: u / eps_g, 2: no conversion */
     int pressure_plus;       /* 1: +V_p grad p as printed in Eq. 16 */
     int recirculate;         /* 1: outlet -> inlet re-injection of particles (reading R21) */
+    int collision_model;     /* 0: time-driven hard spheres (§2.2); 1: soft spheres (R25) */
+    double dem_kn;           /* soft-sphere normal stiffness, N/m */
 } ob_setup;
 
 /* ---- lattice-unit constants derived from an ob_setup ---- */
@@ -95,6 +97,7 @@ typedef struct {
     double u0[3];
     double wall_u[6][3];
     double cs_smag;
+    double kn, eta, eta_w;   /* soft spheres: stiffness, pair and wall damping */
 } ob_consts;
 
 typedef struct {
@@ -125,7 +128,10 @@ typedef struct {
     int64_t *id, *cell;
     int64_t *cell_start;     /* ncell + 1 */
     double *fpre, *fd;       /* np * 3, sorted order, last step */
+    double *fc;              /* np * 3, sorted order: soft-sphere contact forces */
+    int model;               /* collision model (0 hard, 1 soft spheres) */
     double *diag_fpre, *diag_fd;   /* np * 3, id order, last step */
+    double *diag_fc;               /* np * 3, id order, last step */
     int64_t *best;           /* chosen partner (id) or -1 */
     int *wall_hit;           /* bitmask of faces contacted */
     int64_t *pairs;          /* approaching contact pairs (id_i < id_j) */
@@ -291,6 +297,17 @@ void ob_units(const ob_setup *s, ob_consts *k)
     for (int f = 0; f < 6; ++f)
         for (int a = 0; a < 3; ++a) k->wall_u[f][a] = s->wall_u[f][a] * uscale;
     k->cs_smag = s->cs_smag;
+    /* soft spheres (R25): F = k_n delta - eta v_n; the damping that gives the
+     * restitution e to a linear spring-dashpot pair of reduced mass m/2 (and
+     * to a particle against a wall, reduced mass m) */
+    k->kn = s->dem_kn * s->dt * s->dt / (s->rho_g * s->h * s->h * s->h);
+    k->eta = k->eta_w = 0.0;
+    if (s->e > 0.0 && s->e < 1.0 && k->kn > 0.0) {
+        double le = log(s->e);
+        double z = -le / sqrt(M_PI * M_PI + le * le);
+        k->eta = 2.0 * z * sqrt(0.5 * k->mp * k->kn);
+        k->eta_w = 2.0 * z * sqrt(k->mp * k->kn);
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -325,7 +342,8 @@ void ob_destroy(ob_bed *b)
 static int alloc_particles(ob_bed *b, int64_t np)
 {
     free(b->P); free(b->v); free(b->id); free(b->cell); free(b->fpre); free(b->fd);
-    free(b->best); free(b->wall_hit); free(b->diag_fpre); free(b->diag_fd);
+    free(b->best); free(b->wall_hit); free(b->diag_fpre); free(b->diag_fd); free(b->fc);
+    free(b->diag_fc);
     size_t m = (size_t)(np > 0 ? np : 1);
     b->np = np;
     b->P = calloc(m * 3, sizeof(double));
@@ -338,8 +356,10 @@ static int alloc_particles(ob_bed *b, int64_t np)
     b->wall_hit = calloc(m, sizeof(int));
     b->diag_fpre = calloc(m * 3, sizeof(double));
     b->diag_fd = calloc(m * 3, sizeof(double));
+    b->fc = calloc(m * 3, sizeof(double));
+    b->diag_fc = calloc(m * 3, sizeof(double));
     return (b->P && b->v && b->id && b->cell && b->fpre && b->fd && b->best && b->wall_hit &&
-            b->diag_fpre && b->diag_fd);
+            b->diag_fpre && b->diag_fd && b->fc && b->diag_fc);
 }
 
 ob_bed *ob_create(const ob_setup *s)
@@ -352,6 +372,9 @@ ob_bed *ob_create(const ob_setup *s)
         if (s->bc[2 * a] == OB_PERIODIC && s->n[a] < 3) return NULL;
     }
     if (!(s->d_p <= s->h)) return NULL;
+    /* soft spheres need a stiffness and 0 < e <= 1 (R25) */
+    if (s->collision_model != 0 && s->collision_model != 1) return NULL;
+    if (s->collision_model == 1 && !(s->dem_kn > 0.0 && s->e > 0.0 && s->e <= 1.0)) return NULL;
     /* recirculation needs the inlet below and the outlet above (reading R21) */
     if (s->recirculate && !(s->bc[2 * (s->dim - 1)] == OB_INLET && s->bc[2 * s->dim - 1] == OB_OUTLET))
         return NULL;
@@ -368,6 +391,7 @@ ob_bed *ob_create(const ob_setup *s)
     b->superficial_mode = s->superficial_mode;
     b->pressure_plus = s->pressure_plus;
     b->recirculate = s->recirculate;
+    b->model = s->collision_model;
     b->solids_out = 0;
     b->uscale = s->dt / s->h;
     set_lattice(b);
@@ -782,7 +806,9 @@ static void drag_and_integrate(ob_bed *b)
             /* Step 5: Eq. 16, symplectic Euler (reading R13) */
             double sgn = b->pressure_plus ? 1.0 : -1.0;
             for (int a = 0; a < dim; ++a) {
-                double acc = b->k.g_eff[a] + (b->fd[p * 3 + a] + sgn * vp * gk[a]) / mp;
+                double fa = b->fd[p * 3 + a] + sgn * vp * gk[a];
+                if (b->model == 1) fa += b->fc[p * 3 + a];   /* soft-sphere contacts (R25) */
+                double acc = b->k.g_eff[a] + fa / mp;
                 b->v[p * 3 + a] += acc;
                 b->P[p * 3 + a] += b->v[p * 3 + a];
             }
@@ -965,14 +991,79 @@ static void detect_and_resolve(ob_bed *b)
 /* ------------------------------------------------------------------------ */
 /* One coupled step (Fig. 4, steps 2-6).                                       */
 /* ------------------------------------------------------------------------ */
+/* ------------------------------------------------------------------------ */
+/* Soft-sphere contacts (reading R25, the paper's §2.2 outlook on DEM for     */
+/* dense beds): every overlapping pair and every wall overlap pushes with a  */
+/* linear spring-dashpot normal force F = k_n delta - eta (v_rel . n),       */
+/* never pulling.  Forces from the positions and velocities at the start of  */
+/* the step, sorted order.                                                    */
+/* ------------------------------------------------------------------------ */
+static void contact_forces(ob_bed *b)
+{
+    const int dim = b->dim;
+    const double d = b->k.d, r = b->k.r, kn = b->k.kn;
+    for (int64_t p = 0; p < b->np; ++p) {
+        double F[3] = {0, 0, 0};
+        int64_t x = b->cell[p];
+        int64_t idx[3] = {x % b->n[0], (x / b->n[0]) % b->n[1], x / ((int64_t)b->n[0] * b->n[1])};
+        int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        for (int a = 0; a < dim; ++a) { lo[a] = -1; hi[a] = 1; }
+        for (int64_t oz = lo[2]; oz <= hi[2]; ++oz)
+        for (int64_t oy = lo[1]; oy <= hi[1]; ++oy)
+        for (int64_t ox = lo[0]; ox <= hi[0]; ++ox) {
+            int64_t q[3] = {idx[0] + ox, idx[1] + oy, idx[2] + oz};
+            int skip = 0;
+            for (int a = 0; a < dim; ++a)
+                if (q[a] < 0 || q[a] >= b->n[a]) {
+                    if (b->bc[2 * a] == OB_PERIODIC) q[a] = (q[a] + b->n[a]) % b->n[a];
+                    else skip = 1;
+                }
+            if (skip) continue;
+            int64_t y = q[0] + (int64_t)b->n[0] * (q[1] + (int64_t)b->n[1] * q[2]);
+            for (int64_t j = b->cell_start[y]; j < b->cell_start[y + 1]; ++j) {
+                if (j == p) continue;
+                double dx[3] = {0, 0, 0}, d2 = 0.0;
+                for (int a = 0; a < dim; ++a) {
+                    dx[a] = sep_axis(b, a, b->P[p * 3 + a], b->P[j * 3 + a]);
+                    d2 += dx[a] * dx[a];
+                }
+                if (!(d2 < d * d)) continue;
+                double dist = sqrt(d2), vn = 0.0;
+                for (int a = 0; a < dim; ++a) vn += (b->v[p * 3 + a] - b->v[j * 3 + a]) * (dx[a] / dist);
+                double f = kn * (d - dist) - b->k.eta * vn;
+                if (f < 0.0) f = 0.0;
+                for (int a = 0; a < dim; ++a) F[a] += f * (dx[a] / dist);
+            }
+        }
+        /* walls (an open outlet of a circulating bed is not one, R21) */
+        for (int a = 0; a < dim; ++a) {
+            if (b->bc[2 * a] == OB_PERIODIC) continue;
+            double pa = b->P[p * 3 + a], va = b->v[p * 3 + a];
+            if (pa < r) {
+                double f = kn * (r - pa) - b->k.eta_w * va;
+                if (f > 0.0) F[a] += f;
+            }
+            if (!(b->recirculate && a == dim - 1) && (double)b->n[a] - pa < r) {
+                double f = kn * (r - ((double)b->n[a] - pa)) + b->k.eta_w * va;
+                if (f > 0.0) F[a] -= f;
+            }
+        }
+        for (int a = 0; a < 3; ++a) {
+            b->fc[p * 3 + a] = F[a];
+            b->diag_fc[b->id[p] * 3 + a] = F[a];
+        }
+    }
+}
+
 void ob_step(ob_bed *b)
 {
     deposit(b);
     collide_and_stream(b);
     pressure_gradient(b);
+    if (b->model == 1) contact_forces(b);
     drag_and_integrate(b);
     sort_particles(b);
-    detect_and_resolve(b);
+    if (b->model == 0) detect_and_resolve(b);
     b->steps++;
 }
 
@@ -1000,11 +1091,11 @@ int64_t ob_npairs(const ob_bed *b) { return b->npairs; }
 
 void ob_constants(const ob_bed *b, double *out)
 {
-    /* tau nu mu rho_s d r vp mp e g_eff[3] fb[3] u0[3] cs */
+    /* tau nu mu rho_s d r vp mp e g_eff[3] fb[3] u0[3] cs kn eta eta_w */
     const ob_consts *k = &b->k;
     double v[] = {k->tau, k->nu, k->mu, k->rho_s, k->d, k->r, k->vp, k->mp, k->e,
                   k->g_eff[0], k->g_eff[1], k->g_eff[2], k->fb[0], k->fb[1], k->fb[2],
-                  k->u0[0], k->u0[1], k->u0[2], k->cs_smag};
+                  k->u0[0], k->u0[1], k->u0[2], k->cs_smag, k->kn, k->eta, k->eta_w};
     memcpy(out, v, sizeof(v));
 }
 
@@ -1014,7 +1105,7 @@ void ob_units_flat(const ob_setup *s, double *out)
     ob_units(s, &k);
     double v[] = {k.tau, k.nu, k.mu, k.rho_s, k.d, k.r, k.vp, k.mp, k.e,
                   k.g_eff[0], k.g_eff[1], k.g_eff[2], k.fb[0], k.fb[1], k.fb[2],
-                  k.u0[0], k.u0[1], k.u0[2], k.cs_smag};
+                  k.u0[0], k.u0[1], k.u0[2], k.cs_smag, k.kn, k.eta, k.eta_w};
     memcpy(out, v, sizeof(v));
 }
 
@@ -1100,7 +1191,7 @@ int ob_get_field(const ob_bed *b, int which, double *out)
     return 0;
 }
 
-enum { OB_P_FPRE = 0, OB_P_FD = 1, OB_P_CELL = 2, OB_P_BEST = 3, OB_P_WALL = 4 };
+enum { OB_P_FPRE = 0, OB_P_FD = 1, OB_P_CELL = 2, OB_P_BEST = 3, OB_P_WALL = 4, OB_P_FC = 5 };
 
 /* per-particle diagnostics of the last step, id order */
 int ob_get_particle_diag(const ob_bed *b, int which, double *out)
@@ -1117,6 +1208,9 @@ int ob_get_particle_diag(const ob_bed *b, int which, double *out)
         case OB_P_CELL: out[id] = (double)b->cell[p]; break;
         case OB_P_BEST: out[id] = (double)b->best[p]; break;
         case OB_P_WALL: out[id] = (double)b->wall_hit[p]; break;
+        case OB_P_FC:
+            for (int a = 0; a < b->dim; ++a) out[id * b->dim + a] = b->diag_fc[id * 3 + a];
+            break;
         default: return -1;
         }
     }

@@ -21,9 +21,10 @@ _LIB = None
 F_RHO, F_U, F_UACT, F_VS, F_EPS_S, F_EPS_G, F_OMEGA, F_BETA, F_FPG, F_GRADP, F_TAU_T, \
     F_NTOT, F_SUM_PRE, F_SUM_ABS_PRE, F_EPS_2D = range(15)
 VECTOR_FIELDS = {F_U, F_UACT, F_VS, F_FPG, F_GRADP, F_SUM_PRE, F_SUM_ABS_PRE}
-P_FPRE, P_FD, P_CELL, P_BEST, P_WALL = range(5)
+P_FPRE, P_FD, P_CELL, P_BEST, P_WALL, P_FC = range(6)
 CONST_NAMES = ["tau", "nu", "mu", "rho_s", "d", "r", "vp", "mp", "e", "g_eff_x", "g_eff_y",
-               "g_eff_z", "fb_x", "fb_y", "fb_z", "u0_x", "u0_y", "u0_z", "cs_smag"]
+               "g_eff_z", "fb_x", "fb_y", "fb_z", "u0_x", "u0_y", "u0_z", "cs_smag",
+               "kn", "eta", "eta_w"]
 
 
 class Setup(ctypes.Structure):
@@ -39,7 +40,8 @@ class Setup(ctypes.Structure):
         ("g", ctypes.c_double * 3), ("body_accel", ctypes.c_double * 3),
         ("u0", ctypes.c_double * 3), ("cs_smag", ctypes.c_double),
         ("superficial_mode", ctypes.c_int), ("pressure_plus", ctypes.c_int),
-        ("recirculate", ctypes.c_int),
+        ("recirculate", ctypes.c_int), ("collision_model", ctypes.c_int),
+        ("dem_kn", ctypes.c_double),
     ]
 
 
@@ -138,6 +140,8 @@ def make_setup(w):
     s.superficial_mode = int(w.superficial_mode)
     s.pressure_plus = int(w.pressure_plus)
     s.recirculate = int(getattr(w, "recirculate", False))
+    s.collision_model = int(getattr(w, "collision_model", 0))
+    s.dem_kn = float(getattr(w, "dem_kn", 0.0))
     return s, keep
 
 
@@ -241,7 +245,7 @@ class OracleBed:
         return out.reshape(self.ncell, self.dim) if vec else out
 
     def particle_diag(self, which: int) -> np.ndarray:
-        vec = which in (P_FPRE, P_FD)
+        vec = which in (P_FPRE, P_FD, P_FC)
         out = np.empty(max(self.np, 1) * (self.dim if vec else 1))
         lib().ob_get_particle_diag(self._h, which, _dp(out))
         out = out[: self.np * (self.dim if vec else 1)]

@@ -110,6 +110,8 @@ class Workload:
     superficial_mode: int = 0
     pressure_plus: int = 0
     recirculate: bool = False     # outlet -> inlet re-injection of particles
+    collision_model: int = 0      # 0: time-driven hard spheres, 1: soft spheres
+    dem_kn: float = 0.0           # soft-sphere normal stiffness (N/m)
     storage: int = STORE_F32
     steps: int = 1
     seed: int = 0
@@ -191,6 +193,58 @@ def bubbling_table1(nx=25, ny=100, n_particles=15000, seed=SEED_BASE + 6, storag
         rho_s=930.0, e=0.9, pos=pos, vel=vel, rho_g=1.1795, mu_g=1.8872e-5,
         g=(0.0, -9.81, 0.0), u0=(0.0, v_mf, 0.0), inlet_u=inlet, cs_smag=cs_smag,
         storage=storage, steps=steps, seed=seed)
+
+
+def dem_stiffness(w: Workload, contact_steps: float = 20.0) -> float:
+    """Normal stiffness k_n (N/m) that makes an undamped pair contact last
+    ``contact_steps`` time steps: half a period pi sqrt(m_eff / k_n) of the
+    spring with the reduced mass m_eff = m_p / 2."""
+    m_p = w.rho_s * math.pi * w.d_p ** 3 / 6.0
+    t_c = contact_steps * w.dt
+    return 0.5 * m_p * (math.pi / t_c) ** 2
+
+
+def soft_spheres(w: Workload, contact_steps: float = 20.0, e: Optional[float] = None) -> Workload:
+    """The same bed with the soft-sphere contact model in place of the
+    time-driven hard spheres."""
+    w2 = w.with_(collision_model=1, name=w.name + "-dem")
+    if e is not None:
+        w2 = w2.with_(e=e)
+    return w2.with_(dem_kn=dem_stiffness(w2, contact_steps))
+
+
+def packed_bed(dim=2, n=(32, 64), fill_rows=None, gap=0.9, n_particles=None,
+               seed=SEED_BASE + 7, storage=STORE_F64, contact_steps=20.0, e=0.7,
+               sigma_v=0.05) -> Workload:
+    """A dense soft-sphere bed of Table 1 particles (54 um, 930 kg/m^3, h =
+    2.7e-4 m, dt = 1.35e-6 s) whose centres are only ``gap`` d_p apart at
+    least, so that many pairs start in contact: random sequential addition in
+    the lower ``fill_rows`` rows of a closed box (walls on every face), gas at
+    rest, gravity, Maxwellian velocities of ``sigma_v`` m/s."""
+    h, dt, d_p = 2.7e-4, 1.35e-6, 54e-6
+    r = 0.5 * d_p
+    n = tuple(n)
+    if fill_rows is None:
+        fill_rows = n[-1] // 2
+    lo = [r] * dim
+    hi = [n[a] * h - r for a in range(dim)]
+    hi[-1] = fill_rows * h
+    box = [n[a] * h for a in range(dim)]
+    if n_particles is None:
+        # about 0.35 of the filled area (2D) or volume (3D) in particles
+        if dim == 2:
+            n_particles = int(0.35 * box[0] * fill_rows * h / (math.pi * r * r))
+        else:
+            n_particles = int(0.35 * box[0] * box[1] * fill_rows * h / (math.pi * d_p ** 3 / 6))
+    pos = rsa(dim, box, lo, hi, (0, 0, 0), gap * d_p, n_particles, seed)
+    vel = maxwellian(dim, n_particles, (0.0,) * dim, sigma_v, seed ^ 0x5DEECE66D)
+    bc = _bc(dim, (WALL, WALL), (WALL, WALL), (WALL, WALL))
+    g = (0.0, -9.81, 0.0) if dim == 2 else (0.0, 0.0, -9.81)
+    w = Workload(
+        name=f"packed{dim}d-{'x'.join(map(str, n))}-N{n_particles}", dim=dim, n=n, bc=bc, h=h,
+        dt=dt, d_p=d_p, rho_s=930.0, e=e, pos=pos, vel=vel, rho_g=1.1795, mu_g=1.8872e-5, g=g,
+        storage=storage, seed=seed, collision_model=1)
+    return w.with_(dem_kn=dem_stiffness(w, contact_steps))
 
 
 def background_inlet(w: Workload) -> np.ndarray:

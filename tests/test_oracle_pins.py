@@ -826,3 +826,166 @@ def test_bubbles_match_scipy_labelling(seed):
     # Eq. 11 voidage, written out independently
     epsg = 1.0 - math.sqrt(2.0) / math.sqrt(math.pi * math.sqrt(3.0)) * (1.0 - eps2d) ** 1.5
     assert bed.bubbles(0.97, 1) == _scipy_bubbles(epsg > 0.97)
+
+
+# ------------------------------------------------------- soft spheres (R25)
+
+def _soft(dim=2, n=(16, 8), e=0.9, contact_steps=40.0, rho_s=1e6, **kw):
+    """Lattice-unit bed (h = dt = rho_g = 1) with the soft-sphere model; the
+    solid density is high so that the gas drag on the particles is negligible
+    beside the contact forces (drag acceleration ~ 18 mu slip / (rho_s d^2))."""
+    d = kw.pop("d_p", 0.5)
+    mp = rho_s * math.pi * d ** 3 / 6.0
+    kn = 0.5 * mp * (math.pi / contact_steps) ** 2
+    base = dict(dim=dim, n=n, bc=(W.PERIODIC,) * 6, d_p=d, rho_s=rho_s, e=e, mu_g=0.1,
+                collision_model=1, dem_kn=kn)
+    base.update(kw)
+    return _bed(**base), mp, kn
+
+
+def _clipped_restitution(e):
+    """Restitution and peak overlap of a continuous-time linear spring-dashpot
+    contact whose force never pulls (F = max(0, k s + eta s')), integrated by
+    scipy at tight tolerance: units m_eff = k = 1, approach speed 1."""
+    integrate = pytest.importorskip("scipy.integrate")
+    le = math.log(e)
+    c = 2.0 * (-le / math.sqrt(math.pi ** 2 + le * le))
+
+    def rhs(t, y):
+        return [y[1], -max(0.0, y[0] + c * y[1])]
+
+    def out(t, y):
+        return y[0]
+    out.terminal, out.direction = True, -1
+    sol = integrate.solve_ivp(rhs, [0.0, 20.0], [0.0, 1.0], events=out, rtol=1e-12, atol=1e-14,
+                              max_step=1e-3, dense_output=True)
+    t_end = sol.t_events[0][0]
+    ts = np.linspace(0.0, t_end, 4001)
+    return -sol.y_events[0][0][1], sol.sol(ts)[0].max()
+
+
+@pytest.mark.parametrize("e", [0.9, 0.5, 1.0])
+def test_soft_sphere_pair_restitution(e):
+    # A head-on pair with the damping that gives restitution e to a linear
+    # spring-dashpot contact of reduced mass m/2: the separation speed and the
+    # peak overlap match the continuous-time contact (no pulling force) up to
+    # the time discretisation, and the error shrinks as the contact is
+    # resolved by more steps.
+    e_ref, s_ref = _clipped_restitution(e)
+    errs = []
+    for steps in (40.0, 160.0):
+        w, mp, kn = _soft(e=e, contact_steps=steps)
+        v = 1e-3
+        P = np.array([[8 - 0.25 - 0.02, 4.3], [8 + 0.25 + 0.02, 4.3]])
+        V = np.array([[v, 0.0], [-v, 0.0]])
+        bed = O.OracleBed(w.__class__(**{**vars(w), "pos": P, "vel": V}))
+        gap_min = np.inf
+        for _ in range(int(3 * steps) + 60):
+            bed.step(1)
+            Pn, Vn = bed.particles()
+            gap_min = min(gap_min, Pn[1, 0] - Pn[0, 0])
+        e_num = (Vn[1, 0] - Vn[0, 0]) / (2 * v)
+        overlap_ref = 2 * v * math.sqrt(0.5 * mp / kn) * s_ref
+        assert abs((0.5 - gap_min) - overlap_ref) <= 0.05 * overlap_ref
+        errs.append(abs(e_num - e_ref))
+        # no lateral motion beyond what the disturbed gas gives; total
+        # momentum kept up to the (negligible) drag
+        assert np.abs(Vn[:, 1]).max() < 1e-6 * v
+        assert abs(Vn[0, 0] + Vn[1, 0]) < 1e-3 * v
+    assert errs[0] <= 0.015
+    assert errs[1] <= 0.3 * errs[0] + 1e-4
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_soft_sphere_rests_on_the_floor(dim):
+    # A particle settles on the bottom wall where the spring carries its
+    # effective weight: overlap = m_p g_eff / k_n.
+    n = (8, 8) if dim == 2 else (6, 6, 8)
+    g = 1e-5
+    grav = (0.0, -g, 0.0) if dim == 2 else (0.0, 0.0, -g)
+    P = np.full((1, dim), 3.4)
+    P[0, -1] = 0.5
+    w, mp, kn = _soft(dim=dim, n=n, e=0.3, contact_steps=40.0, bc=(W.WALL,) * 6, g=grav,
+                      pos=P, vel=np.zeros((1, dim)))
+    bed = O.OracleBed(w)
+    bed.step(3000)
+    Pn, Vn = bed.particles()
+    g_eff = (1.0 - 1.0 / w.rho_s) * g
+    assert Pn[0, -1] == pytest.approx(0.25 - mp * g_eff / kn, rel=1e-9)
+    assert np.abs(Vn).max() < 1e-5 * g
+    assert bed.particle_diag(O.P_FC)[0, -1] == pytest.approx(mp * g_eff, rel=1e-9)
+
+
+def _soft_forces_bruteforce(P, v, n, per, d, kn, eta, eta_w, top_open=False):
+    """All pairs (minimum image on periodic axes) and every face."""
+    N, dim = P.shape
+    r = 0.5 * d
+    F = np.zeros((N, dim))
+    for i in range(N):
+        for j in range(N):
+            if i == j:
+                continue
+            dx = P[i] - P[j]
+            for a in range(dim):
+                if per[a]:
+                    dx[a] -= n[a] * round(dx[a] / n[a])
+            dist = math.sqrt(dx @ dx)
+            if dist >= d:
+                continue
+            nrm = dx / dist
+            f = kn * (d - dist) - eta * ((v[i] - v[j]) @ nrm)
+            F[i] += max(f, 0.0) * nrm
+        for a in range(dim):
+            if per[a]:
+                continue
+            if P[i, a] < r:
+                F[i, a] += max(kn * (r - P[i, a]) - eta_w * v[i, a], 0.0)
+            if not (top_open and a == dim - 1) and n[a] - P[i, a] < r:
+                F[i, a] -= max(kn * (r - (n[a] - P[i, a])) + eta_w * v[i, a], 0.0)
+    return F
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("walls", [False, True])
+def test_soft_sphere_forces_match_all_pairs(dim, walls):
+    # The contact forces from the cell neighbourhood equal those of an
+    # all-pairs search; in a periodic box they sum to zero (third law).
+    n = (7, 6) if dim == 2 else (5, 4, 6)
+    rng = np.random.default_rng(11 + dim)
+    d = 0.7
+    box = np.array(n, dtype=float)
+    pos = W.rsa(dim, box, [0.36] * dim, box - 0.36, (0, 0, 0) if walls else (1, 1, 1), 0.8 * d,
+                60 if dim == 2 else 120, 5 + dim)
+    vel = rng.normal(scale=2e-3, size=pos.shape)
+    bc = (W.WALL,) * 6 if walls else (W.PERIODIC,) * 6
+    w, mp, kn = _soft(dim=dim, n=n, d_p=d, rho_s=50.0, e=0.6, contact_steps=12.0, bc=bc,
+                      pos=pos, vel=vel)
+    bed = O.OracleBed(w)
+    P0, v0 = bed.particles()
+    k = bed.constants()
+    bed.step(1)
+    fc = bed.particle_diag(O.P_FC)
+    ref = _soft_forces_bruteforce(P0, v0, n, [not walls] * dim, d, k["kn"], k["eta"], k["eta_w"])
+    assert (np.abs(ref).sum(axis=1) > 0).mean() > 0.4
+    np.testing.assert_allclose(fc, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    if not walls:
+        assert np.abs(fc.sum(axis=0)).max() <= 1e-12 * np.abs(fc).sum()
+    # and the force enters Eq. 16 like the drag: the particle momentum
+    # changes by the contact, drag, pressure and gravity forces of the step
+    assert k["eta"] == pytest.approx(k["eta_w"] / math.sqrt(2.0), rel=1e-14)
+
+
+def test_soft_sphere_outlet_of_circulating_bed_is_open():
+    # With the solids loop closed (R21) the outlet lets particles through, so
+    # it exerts no contact force; the inlet face below still does.
+    w = _cfb_column()
+    r = 0.5 * w.d_p / w.h
+    P = np.array([[4.5, w.n[1] - 0.5 * r], [8.5, 0.5 * r]])
+    v = np.array([[0.0, 0.08], [0.0, -0.01]])
+    w = W.soft_spheres(w, contact_steps=20.0).with_(pos=P * w.h, vel=v * w.h / w.dt)
+    bed = O.OracleBed(w)
+    bed.step(1)
+    fc = bed.particle_diag(O.P_FC)
+    assert fc[0, 1] == 0.0 and fc[0, 0] == 0.0
+    assert fc[1, 1] > 0.0
+    assert bed.stats()["solids_out"] == 1
