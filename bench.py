@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--bubble-time", type=float, default=0.05)
     ap.add_argument("--bubble-cs", type=float, default=0.1,
                     help="Smagorinsky constant of the bubbling bed (Table 1's tau is 0.50089)")
+    ap.add_argument("--dem", action="store_true",
+                    help="dense soft-sphere bed (Table 1 particles, 256 x 1024 cells, lower half "
+                         "packed): step time, kernel split and the contact kernel's roofline")
+    ap.add_argument("--dem-steps", type=int, default=400)
     return ap.parse_args()
 
 
@@ -285,6 +289,10 @@ def main():
     if args.bubble:
         if rank == 0:
             bubble_main(args)
+        return
+    if args.dem:
+        if rank == 0:
+            dem_main(args)
         return
 
     import torch
@@ -685,6 +693,75 @@ def bubble_main(args):
             "mlups": w.ncell * done / t_dev / 1e6,
             "series": series[::10] + series[-1:]}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- soft spheres
+
+def contact_bytes(w, storage):
+    """Algorithmic bytes of one soft-sphere contact launch, per particle: its
+    cell index, in-cell offset, velocity and FP64 position read once, the
+    contact force written once, and the cell-list entries of its 3 (2D) or 9
+    (3D) neighbour rows (two ints each).  Reads of the neighbours' state are
+    re-reads of the same arrays (served by L1/L2) and are not counted."""
+    r = 8 if storage == "f64" else 4
+    d = w.dim
+    rows = 3 if d == 2 else 9
+    per_particle = 4 + d * r + d * r + d * 8 + d * r + rows * 2 * 4
+    return per_particle * len(w.pos)
+
+
+def dem_main(args):
+    """Dense soft-sphere bed: Table 1 particles (54 um, 930 kg/m^3, h = 2.7e-4
+    m, dt = 1.35e-6 s) packed to an area fraction of 0.35 in the lower half of
+    a closed 256 x 1024 box, centres at least 0.9 d_p apart (many start in
+    contact), pair contacts 20 steps long, e = 0.7."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1303_2653_gb300 import lbdps as L
+    from paper_1303_2653_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    storage = args.storage
+    st_code = {"f32": W.STORE_F32, "f16": W.STORE_F16, "bf16": W.STORE_BF16,
+               "f64": W.STORE_F64}[storage]
+    w = W.packed_bed(dim=2, n=(256, 1024), storage=st_code, cs_smag=0.1)
+    bed = L.Bed(w, check_every=0)
+    st = bed.stream
+    bed.step(max(args.warmup, 3))
+    bed.sync()
+    clocks = ClockSampler(0)
+    clocks.start()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    bed.step(args.dem_steps)
+    b.record(st)
+    b.synchronize()
+    clk = clocks.stop()
+    t = a.elapsed_time(b) / 1e3
+    prof_steps = 50
+    ms = bed.step_profiled(prof_steps)
+    peak, peak_kind = measured_peaks()
+    t_contact = ms["collide_particles"] / 1e3 / prof_steps
+    nb = contact_bytes(w, storage)
+    ach = nb / t_contact / 1e9
+    s = bed.stats()
+    line = {"metric": "dense soft-sphere bed: coupled step throughput", "unit": "MLUPS",
+            "value": w.ncell * args.dem_steps / t / 1e6,
+            "particle_updates_per_s": len(w.pos) * args.dem_steps / t,
+            "ms_per_step": 1e3 * t / args.dem_steps, "steps": args.dem_steps,
+            "warmup": max(args.warmup, 3), "dtype": {"f64": "f64"}.get(storage, "f32"),
+            "storage": storage, "data": "synthetic",
+            "config": {"workload": w.name, "cells": w.ncell, "particles": len(w.pos),
+                       "contact_steps": 20, "e": w.e, "cs_smag": w.cs_smag},
+            "kernel_ms_per_step": {k: v / prof_steps for k, v in ms.items()},
+            "roofline_contacts": {"bound": "hbm", "achieved": ach, "peak": peak,
+                                  "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                                  "bytes_per_launch": nb},
+            "health": s["health"], "clocks": clk}
+    print(json.dumps(line), flush=True)
+    bed.close()
 
 
 if __name__ == "__main__":

@@ -94,6 +94,8 @@ extern "C" {
 #define LBDPS_PDIAG_CELL   4  /* cell index of the particle (1)                     */
 #define LBDPS_PDIAG_ORDER  5  /* ids in cell-sorted order: entry k is the id held
                                  in sorted slot k (1)                               */
+#define LBDPS_PDIAG_FC     6  /* soft-sphere contact force of the last step (dim,
+                                 LBDPS_COLLIDE_SOFT, needs diagnostics)               */
 
 typedef struct lbdps lbdps_t;
 
@@ -124,7 +126,20 @@ typedef struct {
                              position and velocity (the solids loop of a circulating
                              bed, §3.2 / Fig. 9); needs the inlet below and the outlet
                              above.  0: particles reflect at every non-periodic face */
+    int collision_model;  /* LBDPS_COLLIDE_HARD (0): time-driven hard spheres of §2.2,
+                             Eq. 17-18.  LBDPS_COLLIDE_SOFT (1): soft spheres, the DEM
+                             alternative §2.2 names for dense beds: each pair closer than
+                             d_p and each face closer than d_p/2 pushes with
+                             max(0, k_n overlap - eta v_n) along the line of centres, eta
+                             giving the restitution e (which must then be > 0); the force
+                             joins the drag of Eq. 16.  Positions may then overlap */
+    double dem_kn;        /* soft-sphere normal stiffness k_n, N/m (> 0 with
+                             LBDPS_COLLIDE_SOFT; a pair contact must last at least
+                             4 steps: pi sqrt(m_p / (2 k_n)) >= 4 dt) */
 } lbdps_particle_desc;
+
+#define LBDPS_COLLIDE_HARD 0
+#define LBDPS_COLLIDE_SOFT 1
 
 /* Gas and run parameters. */
 typedef struct {
@@ -257,7 +272,8 @@ int lbdps_stats(lbdps_t *h, lbdps_stats_t *out);
 int lbdps_health(lbdps_t *h, int *health);
 
 /* Lattice-unit constants derived at create, in this order: tau, nu, mu,
- * rho_s/rho_g, d, r, V_p, m_p, e, g_eff[3], F_b[3], u0[3], C_s. */
+ * rho_s/rho_g, d, r, V_p, m_p, e, g_eff[3], F_b[3], u0[3], C_s, and the
+ * soft-sphere k_n, eta (pair) and eta (wall), 0 with hard spheres. */
 int lbdps_constants(lbdps_t *h, double *out, int cap);
 
 /* Shape queries. */

@@ -20,10 +20,12 @@
  *             gamma (Eq. 9), F_p->g (Eq. 25), node beta (Eq. 19, 21, 22)
  *   stream    Eq. 2 (push), half-way bounce-back walls, velocity inlet,
  *             pressure outlet, periodic faces
+ *   contacts  soft spheres only (R25): spring-dashpot contact forces
  *   drag      bilinear interpolation (step 4), Eq. 26-28
  *   integrate Eq. 16 (symplectic Euler), specular walls, periodic wrap
  *   sort      by (cell, id)
- *   collide   TDHS detection (contact + approach, §2.2) and Eq. 17-18
+ *   collide   hard spheres only: TDHS detection (contact + approach, §2.2)
+ *             and Eq. 17-18
  *
  * Readings of passages that are silent, ambiguous or garbled (each is listed
  * with its reason in the design notes):
@@ -54,6 +56,18 @@
  *       smallest distance (ties to the smaller id); mutual picks collide by
  *       Eq. 17-18 on pre-collision velocities; wall contacts (the wall is an
  *       infinitely heavy particle at rest) apply to the rest.
+ *   R19 The bed-mean voidage is that of the current positions (Eq. 10-11
+ *       from a fresh count), not of the last deposition.
+ *   R21 Solids loop of the circulating bed (§3.2): a particle that crosses
+ *       the outlet re-enters through the inlet face at the same lateral
+ *       position and velocity and is counted; the outlet makes no contact.
+ *   R23 Bubble regions (§3.1): cells whose voidage exceeds the threshold,
+ *       connected along the axes; a region reaching the top row is freeboard.
+ *   R25 Soft spheres, the DEM option of §2.2 for dense beds: each pair closer
+ *       than d and each face closer than r pushes with max(0, k_n delta -
+ *       eta v_n) along the line of centres, eta = 2 zeta sqrt(m_eff k_n),
+ *       zeta = -ln e / sqrt(pi^2 + ln^2 e), m_eff = m/2 (pair) or m (wall);
+ *       forces from the state at the start of the step, added in Eq. 16.
  */
 #include <math.h>
 #include <stdint.h>

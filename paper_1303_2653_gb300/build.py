@@ -36,8 +36,8 @@ def build_workloads(force: bool = False) -> str:
 
 
 CU_SOURCES = ["lbm_kernels.cu", "particle_kernels.cu", "stats_kernels.cu", "lbdps_api.cu",
-              "lbdps_server.cu", "noalloc_sort.cu", "bubble_kernels.cu"]
-HEADERS = ["lbdps_internal.cuh"]
+              "lbdps_server.cu", "noalloc_sort.cu", "bubble_kernels.cu", "contact_kernels.cu"]
+HEADERS = ["lbdps_internal.cuh", "particle_common.cuh"]
 
 
 def nvcc_flags(extra=()):

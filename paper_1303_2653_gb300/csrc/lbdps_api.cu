@@ -48,10 +48,18 @@ int fail(int code, const char *fmt, ...)
     } while (0)
 
 // Lattice-unit constants (h = 1, dt = 1, reference gas density 1).
+// Profiling events of one step: the intervals between them are collide_stream,
+// soft-sphere contacts, drag, sort and hard-sphere collisions; the classes
+// reported are collide_stream (0), drag (1), sort (2) and particle-particle
+// contacts of either model (3).
+constexpr int kStepEvents = 6;
+constexpr int kStepEventClass[kStepEvents - 1] = {0, 3, 1, 2, 3};
+
 struct Derived {
     double nu, mu, tau, rho_s, d, r, vp, mp, e;
     double geff[3], fb[3], u0[3], wall_u[6][3];
     double cs;
+    double kn, eta, eta_w;     // soft spheres: stiffness, pair and wall damping
 };
 
 constexpr double kPi = 3.141592653589793238462643383;
@@ -78,6 +86,19 @@ Derived derive(const lbdps_lattice_desc &L, const lbdps_particle_desc &Pd, const
     for (int f = 0; f < 6; ++f)
         for (int a = 0; a < 3; ++a) k.wall_u[f][a] = L.wall_u[f][a] * uscale;
     k.cs = P.cs_smag;
+    // soft spheres: the damping that gives a linear spring-dashpot contact
+    // the restitution e, for the reduced mass m_p / 2 of a pair and m_p
+    // against a wall (an infinitely heavy body)
+    k.kn = k.eta = k.eta_w = 0.0;
+    if (Pd.collision_model == LBDPS_COLLIDE_SOFT) {
+        k.kn = Pd.dem_kn * L.dt * L.dt / (P.rho_g * L.h * L.h * L.h);
+        if (k.e > 0.0 && k.e < 1.0 && k.kn > 0.0) {
+            const double le = std::log(k.e);
+            const double z = -le / std::sqrt(kPi * kPi + le * le);
+            k.eta = 2.0 * z * std::sqrt(0.5 * k.mp * k.kn);
+            k.eta_w = 2.0 * z * std::sqrt(k.mp * k.kn);
+        }
+    }
     return k;
 }
 
@@ -204,6 +225,7 @@ struct lbdps {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step, per starting parity
     cudaGraphExec_t chunk[2] = {nullptr, nullptr};   // kChunkSteps steps, per starting parity
     int recirculate = 0;               // outlet -> inlet re-injection of particles
+    bool soft = false;                 // soft-sphere contacts in place of hard spheres
     unsigned *health_host = nullptr;   // pinned: the health word, then 16 doubles of statistics
     double *stats_host = nullptr;      // inside the same pinned block
     std::vector<double> inlet_lat;     // face cells x dim
@@ -228,6 +250,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
     int2 *slot = nullptr;     // (source index, cell) of each sorted slot
     Real *diag_fpre = nullptr, *diag_fd = nullptr;
     int *best = nullptr, *wall = nullptr;
+    Real *fc[3] = {nullptr, nullptr, nullptr};   // soft-sphere contact forces (sorted slots)
+    Real *diag_fc = nullptr;                     // the same in id order (diagnostics)
     Real *tabs[10] = {};
     int *tab_branch = nullptr;
     typename Vec4<Real>::type *tab_pk[2] = {nullptr, nullptr};
@@ -285,6 +309,16 @@ template <class L, class Real, class S> struct EngineT : Engine {
             }
             diag_fpre = (Real *)get(sizeof(Real) * D * np);
             diag_fd = (Real *)get(sizeof(Real) * D * np);
+        }
+        if (H->soft) {
+            for (int a = 0; a < D; ++a) {
+                fc[a] = (Real *)get(sizeof(Real) * np);
+                if (!fc[a]) return fail(LBDPS_ERR_OOM, "device allocation failed");
+            }
+            if (H->prm.diagnostics) {
+                diag_fc = (Real *)get(sizeof(Real) * D * np);
+                if (!diag_fc) return fail(LBDPS_ERR_OOM, "device allocation failed");
+            }
         }
         key = (int *)get(sizeof(int) * np);
         counts = (int *)get(sizeof(int) * (nc + 1));
@@ -393,6 +427,10 @@ template <class L, class Real, class S> struct EngineT : Engine {
         p.health = health_dev;
         p.recirculate = H->recirculate;
         p.solids_out = solids_out;
+        for (int a = 0; a < 3; ++a) p.fc[a] = a < D ? fc[a] : nullptr;
+        p.kn = (Real)k.kn;
+        p.eta = (Real)k.eta;
+        p.eta_w = (Real)k.eta_w;
     }
 
     int upload_initial(const double *pos_lat, const double *vel_lat) override
@@ -467,8 +505,9 @@ template <class L, class Real, class S> struct EngineT : Engine {
     }
 
     // One coupled step from buffers `parity` into buffers `1 - parity`.
-    // ev (optional, 5 events) brackets the kernel classes for profiling:
-    // collide_stream, drag, sort, collide_particles.
+    // ev (optional, kStepEvents events) brackets the kernels for profiling:
+    // collide_stream, soft-sphere contacts, drag, sort, hard-sphere
+    // collisions (kStepEventClass maps each interval to its class).
     int enqueue_step(int parity, cudaEvent_t *ev) override
     {
         cudaStream_t st = H->stream;
@@ -478,10 +517,16 @@ template <class L, class Real, class S> struct EngineT : Engine {
         launch_collide_stream<L, Real, S>(sp, lay, f[a], f[b], cells(a), part[a], fld, st);
         CHECK_LAUNCH();
         if (ev) CU(cudaEventRecord(ev[1], st));
+        if (H->soft) {
+            // contact forces of the start-of-step state, used by the drag kernel
+            launch_contacts<D, Real>(sp, part[a], cells(a), diag_fc, np, st);
+            CHECK_LAUNCH();
+        }
+        if (ev) CU(cudaEventRecord(ev[2], st));
         launch_drag_step<D, Real>(sp, part[a], stage, cells(a), fld, key, counts, diag_fpre,
                                   diag_fd, np, st);
         CHECK_LAUNCH();
-        if (ev) CU(cudaEventRecord(ev[2], st));
+        if (ev) CU(cudaEventRecord(ev[3], st));
         if (np > 0) {
             launch_cell_scan(counts, cells_out(b), H->ncell, st);
             CHECK_LAUNCH();
@@ -493,12 +538,14 @@ template <class L, class Real, class S> struct EngineT : Engine {
             int rc = clear_cells(b);
             if (rc) return rc;
         }
-        if (ev) CU(cudaEventRecord(ev[3], st));
-        launch_detect<D, Real>(sp, part[b], cells(b), best, wall, nullptr, nullptr, 0, np, st);
-        CHECK_LAUNCH();
-        launch_resolve<D, Real>(sp, part[b], best, wall, np, st);
-        CHECK_LAUNCH();
         if (ev) CU(cudaEventRecord(ev[4], st));
+        if (!H->soft) {
+            launch_detect<D, Real>(sp, part[b], cells(b), best, wall, nullptr, nullptr, 0, np, st);
+            CHECK_LAUNCH();
+            launch_resolve<D, Real>(sp, part[b], best, wall, np, st);
+            CHECK_LAUNCH();
+        }
+        if (ev) CU(cudaEventRecord(ev[5], st));
         return LBDPS_OK;
     }
 
@@ -711,15 +758,19 @@ template <class L, class Real, class S> struct EngineT : Engine {
     int particle_diag(int which, double *out, size_t cap) override
     {
         const int np = H->np, cur = H->parity;
-        const bool vec = (which == LBDPS_PDIAG_FPRE || which == LBDPS_PDIAG_FD);
+        const bool vec = (which == LBDPS_PDIAG_FPRE || which == LBDPS_PDIAG_FD ||
+                          which == LBDPS_PDIAG_FC);
         const size_t need = (size_t)np * (vec ? D : 1);
         if (cap < need) return fail(LBDPS_ERR_CAPACITY, "need %zu doubles", need);
         if (np == 0) return LBDPS_OK;
         int rc;
         if (vec) {
             if (!H->prm.diagnostics) return fail(LBDPS_ERR_INVALID, "needs params.diagnostics = 1");
+            if (which == LBDPS_PDIAG_FC && !H->soft)
+                return fail(LBDPS_ERR_INVALID, "contact forces need collision_model = LBDPS_COLLIDE_SOFT");
             std::vector<Real> hb;
-            const Real *src = which == LBDPS_PDIAG_FPRE ? diag_fpre : diag_fd;
+            const Real *src = which == LBDPS_PDIAG_FPRE ? diag_fpre
+                              : which == LBDPS_PDIAG_FD ? diag_fd : diag_fc;
             if ((rc = d2h(hb, src, (size_t)D * np))) return rc;
             for (int a = 0; a < D; ++a)
                 for (int i = 0; i < np; ++i) out[(size_t)i * D + a] = (double)hb[(size_t)a * np + i];
@@ -1130,6 +1181,12 @@ static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc 
         return fail(LBDPS_ERR_INVALID, "bad particle properties");
     if (!(par->d_p <= lat->h)) return fail(LBDPS_ERR_INVALID, "d_p must not exceed h");
     if (par->recirculate != 0 && par->recirculate != 1) return fail(LBDPS_ERR_INVALID, "bad recirculate");
+    if (par->collision_model != LBDPS_COLLIDE_HARD && par->collision_model != LBDPS_COLLIDE_SOFT)
+        return fail(LBDPS_ERR_INVALID, "bad collision_model");
+    const bool soft = par->collision_model == LBDPS_COLLIDE_SOFT;
+    if (soft && !(par->dem_kn > 0 && std::isfinite(par->dem_kn)))
+        return fail(LBDPS_ERR_INVALID, "soft spheres need dem_kn > 0");
+    if (soft && !(par->e > 0)) return fail(LBDPS_ERR_INVALID, "soft spheres need e > 0");
     if (par->recirculate && !(bc[2 * (D - 1)] == BC_INLET && bc[2 * (D - 1) + 1] == BC_OUTLET))
         return fail(LBDPS_ERR_INVALID, "recirculate needs the inlet below and the outlet above");
     if (!(prm->rho_g > 0) || !(prm->mu_g > 0)) return fail(LBDPS_ERR_INVALID, "bad gas properties");
@@ -1149,10 +1206,16 @@ static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc 
     h->h = lat->h;
     h->dt = lat->dt;
     h->recirculate = par->recirculate;
+    h->soft = soft;
     h->prm = *prm;
     h->k = derive(*lat, *par, *prm);
     const Derived &k = h->k;
     if (!(k.tau > 0.5) || !std::isfinite(k.tau)) return fail(LBDPS_ERR_INVALID, "tau must exceed 1/2");
+    // a pair contact (half a period of the undamped spring with the reduced
+    // mass m_p / 2) must span a few steps for the explicit update to hold it
+    if (soft && !(kPi * std::sqrt(0.5 * k.mp / k.kn) >= 4.0))
+        return fail(LBDPS_ERR_INVALID, "dem_kn too stiff: a pair contact lasts %.3g steps (at least 4)",
+                    kPi * std::sqrt(0.5 * k.mp / k.kn));
     double u0s = 0;
     for (int a = 0; a < D; ++a) u0s += k.u0[a] * k.u0[a];
     if (!(u0s < 0.09)) return fail(LBDPS_ERR_INVALID, "|u0| must be below 0.3 in lattice units");
@@ -1190,7 +1253,8 @@ static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc 
         pos[i] = par->pos[i] / lat->h;
         vel[i] = par->vel[i] * vscale;
     }
-    int rc = validate_positions(h.get(), pos.data(), check_overlap);
+    // soft spheres may start in contact
+    int rc = validate_positions(h.get(), pos.data(), check_overlap && !soft);
     if (rc) return rc;
     hout = std::move(h);
     return LBDPS_OK;
@@ -1290,26 +1354,26 @@ int lbdps_step_profiled(lbdps_t *h, int64_t nsteps, double *kernel_ms, int cap, 
     if (!h || nsteps < 0 || (!kernel_ms && cap > 0)) return fail(LBDPS_ERR_INVALID, "bad arguments");
     constexpr int kClasses = 4;
     if (nclass) *nclass = kClasses;
-    cudaEvent_t ev[kClasses + 1];
-    for (int e = 0; e <= kClasses; ++e) CU(cudaEventCreate(&ev[e]));
+    cudaEvent_t ev[kStepEvents];
+    for (int e = 0; e < kStepEvents; ++e) CU(cudaEventCreate(&ev[e]));
     double acc[kClasses] = {0, 0, 0, 0};
     int rc = LBDPS_OK;
     for (int64_t s = 0; s < nsteps && rc == LBDPS_OK; ++s) {
         rc = h->eng->enqueue_step(h->parity, ev);
         if (rc) break;
-        if (cudaEventSynchronize(ev[kClasses]) != cudaSuccess) {
+        if (cudaEventSynchronize(ev[kStepEvents - 1]) != cudaSuccess) {
             rc = fail(LBDPS_ERR_CUDA, "profiling: %s", cudaGetErrorString(cudaGetLastError()));
             break;
         }
-        for (int c = 0; c < kClasses; ++c) {
+        for (int c = 0; c + 1 < kStepEvents; ++c) {
             float ms = 0;
             cudaEventElapsedTime(&ms, ev[c], ev[c + 1]);
-            acc[c] += ms;
+            acc[kStepEventClass[c]] += ms;
         }
         h->parity ^= 1;
         h->steps++;
     }
-    for (int e = 0; e <= kClasses; ++e) cudaEventDestroy(ev[e]);
+    for (int e = 0; e < kStepEvents; ++e) cudaEventDestroy(ev[e]);
     for (int c = 0; c < kClasses && c < cap; ++c) kernel_ms[c] = acc[c];
     return rc;
 }
@@ -1439,11 +1503,13 @@ int lbdps_constants(lbdps_t *h, double *out, int cap)
 {
     if (!h || !out) return fail(LBDPS_ERR_INVALID, "bad arguments");
     const Derived &k = h->k;
-    const double v[19] = {k.tau, k.nu, k.mu, k.rho_s, k.d, k.r, k.vp, k.mp, k.e,
+    const double v[22] = {k.tau, k.nu, k.mu, k.rho_s, k.d, k.r, k.vp, k.mp, k.e,
                           k.geff[0], k.geff[1], k.geff[2], k.fb[0], k.fb[1], k.fb[2],
-                          k.u0[0], k.u0[1], k.u0[2], k.cs};
+                          k.u0[0], k.u0[1], k.u0[2], k.cs, k.kn, k.eta, k.eta_w};
+    // the first 19 are always there; the soft-sphere constants follow when
+    // there is room
     if (cap < 19) return fail(LBDPS_ERR_CAPACITY, "need 19 doubles");
-    std::memcpy(out, v, sizeof(v));
+    std::memcpy(out, v, sizeof(double) * (size_t)std::min(cap, 22));
     return LBDPS_OK;
 }
 

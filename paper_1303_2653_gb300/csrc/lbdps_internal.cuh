@@ -143,6 +143,10 @@ template <class Real> struct StepParams {
     unsigned *health;
     int recirculate;          // 1: outlet -> inlet re-injection of particles
     unsigned long long *solids_out;   // particles through the outlet so far
+    // soft spheres: contact forces of the step in sorted slot order (null
+    // with hard spheres), stiffness and pair / wall damping
+    Real *fc[3];
+    Real kn, eta, eta_w;
 };
 
 // Layout of the population arrays: the lattice plus one ghost layer on every
@@ -326,6 +330,11 @@ void launch_detect(const StepParams<Real> &p, Particles<Real> parts, CellList ce
 // allocation-free binning entry point)
 void launch_scan(const int *counts, int *cell_start, int *block_sums, int ncell, cudaStream_t st);
 int scan_block_count(int ncell);
+
+// soft-sphere contact forces of the step into p.fc (sorted slot order)
+template <int D, class Real>
+void launch_contacts(const StepParams<Real> &p, Particles<Real> parts, CellList cells,
+                     Real *diag_fc, int np, cudaStream_t st);
 
 template <int D, class Real>
 void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int *best,

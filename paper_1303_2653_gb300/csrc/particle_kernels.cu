@@ -7,66 +7,9 @@
 // everything per pair or per stencil node uses the cell index and the in-cell
 // offset carried with each particle, and the exact FP64 contact test runs
 // only for pairs that an FP32 test with a safety margin cannot exclude.
-#include "lbdps_internal.cuh"
-
-#include <climits>
-#include <map>
-#include <mutex>
+#include "particle_common.cuh"
 
 namespace lbdpsk {
-
-// Block size for a kernel with one thread per item: the candidate that covers
-// n items in the fewest waves of co-resident blocks (the largest candidate on
-// a tie).  A grid a little larger than one wave pays a whole second wave for
-// its last blocks, which dominates short particle kernels.
-template <class K>
-int wave_block(K kern, long long n)
-{
-    static std::mutex mu;
-    static std::map<std::pair<const void *, int>, int> fit;   // (kernel, block) -> blocks per SM
-    static int nsm = 0;
-    constexpr int cand[3] = {256, 128, 64};
-    std::lock_guard<std::mutex> lock(mu);
-    if (nsm == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-            cudaGetLastError();
-            nsm = 0;
-            return 256;
-        }
-    }
-    int best = 256;
-    long long best_waves = LLONG_MAX;
-    for (int b : cand) {
-        const auto key = std::make_pair((const void *)kern, b);
-        auto it = fit.find(key);
-        if (it == fit.end()) {
-            int per_sm = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b, 0) != cudaSuccess) {
-                cudaGetLastError();
-                per_sm = 0;
-            }
-            it = fit.emplace(key, per_sm).first;
-        }
-        if (it->second <= 0) continue;
-        const long long blocks = (n + b - 1) / b;
-        const long long slots = (long long)it->second * nsm;
-        const long long waves = (blocks + slots - 1) / slots;
-        if (waves < best_waves) {
-            best_waves = waves;
-            best = b;
-        }
-    }
-    return best;
-}
-
-__device__ __forceinline__ void cell_coords(int D, const int *n, int c, int *idx)
-{
-    idx[0] = c % n[0];
-    idx[1] = (D == 3) ? (c / n[0]) % n[1] : c / n[0];
-    idx[2] = (D == 3) ? c / (n[0] * n[1]) : 0;
-}
 
 // Cell of an FP64 position and the offset inside it (floor in FP64, clamped
 // to the lattice; positions are kept inside [0, n) by the integrator).
@@ -82,18 +25,6 @@ __device__ __forceinline__ int cell_and_offset(int D, const int *n, const double
         off[a] = (Real)(P[a] - (double)v);
     }
     return q[0] + n[0] * (q[1] + n[1] * q[2]);
-}
-
-// Minimum-image separation along one axis (periodic faces wrap), FP64 with
-// explicit rounding so that no multiply-add is fused.
-__device__ __forceinline__ double sep_axis(double pi, double pj, bool periodic, double L)
-{
-    double d = __dsub_rn(pi, pj);
-    if (periodic) {
-        if (d > 0.5 * L) d = __dsub_rn(d, L);
-        else if (d < -0.5 * L) d = __dadd_rn(d, L);
-    }
-    return d;
 }
 
 // ---------------------------------------------------------------------------
@@ -231,7 +162,8 @@ template <int D, class Real> struct DetectOccupancy { static constexpr int value
 template <> struct DetectOccupancy<2, float> { static constexpr int value = 6; };
 template <> struct DetectOccupancy<3, float> { static constexpr int value = 3; };
 
-template <int D, class Real>
+// SOFT: add the soft-sphere contact force of the step (p.fc) in Eq. 16
+template <int D, class Real, bool SOFT>
 __global__ void __launch_bounds__(256, DragOccupancy<D, Real>::value)
 k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, CellList cells,
             Fields<Real> fld, int *__restrict__ key, int *__restrict__ counts, Real *diag_fpre,
@@ -307,7 +239,9 @@ k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, Cell
             diag_fd[(size_t)a * np + id] = fd;
             diag_fpre[(size_t)a * np + id] = fp[a];
         }
-        v[a] = v0[a] + (p.geff[a] + (fd + p.psign * p.vp * gp[a]) / p.mp);
+        Real fa = fd + p.psign * p.vp * gp[a];
+        if (SOFT) fa += p.fc[a][k];
+        v[a] = v0[a] + (p.geff[a] + fa / p.mp);
         P[a] = P[a] + (double)v[a];
         const Real on = o0[a] + v[a];
         if (on > Real(1e-3) && on < Real(1) - Real(1e-3)) {
@@ -371,9 +305,15 @@ void launch_drag_step(const StepParams<Real> &p, Particles<Real> parts, Particle
                       Real *diag_fd, int np, cudaStream_t st)
 {
     if (np == 0) return;
-    const int b = wave_block(k_drag_step<D, Real>, np);
-    k_drag_step<D, Real><<<(np + b - 1) / b, b, 0, st>>>(p, parts, out, cells, fld, key, counts,
-                                                         diag_fpre, diag_fd, np);
+    if (p.fc[0]) {
+        const int b = wave_block(k_drag_step<D, Real, true>, np);
+        k_drag_step<D, Real, true><<<(np + b - 1) / b, b, 0, st>>>(p, parts, out, cells, fld, key,
+                                                                   counts, diag_fpre, diag_fd, np);
+    } else {
+        const int b = wave_block(k_drag_step<D, Real, false>, np);
+        k_drag_step<D, Real, false><<<(np + b - 1) / b, b, 0, st>>>(p, parts, out, cells, fld, key,
+                                                                    counts, diag_fpre, diag_fd, np);
+    }
 }
 
 // Keys, offsets and counts of the current positions (used when a particle
@@ -674,21 +614,7 @@ k_detect(StepParams<Real> p, Particles<Real> parts, CellList cells, int *__restr
     // and whose y (z) cell offset from particle i is sy (sz)
     auto test = [&](int j, int rowbase, float sy, float sz) {
         if (j == i) return;
-        // coarse test: P_i - P_j = (o_i - o_j) - (cell_j - cell_i), minimum
-        // image on periodic axes
-        const float shift[3] = {(float)(__ldg(parts.cell + j) - rowbase - idx[0]), sy, sz};
-        float d2f = 0.f;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            float dx = oi[a] - (float)__ldg(parts.off[a] + j) - shift[a];
-            if (per[a]) {
-                const float L = (float)p.n[a];
-                if (dx > 0.5f * L) dx -= L;
-                else if (dx < -0.5f * L) dx += L;
-            }
-            d2f += dx * dx;
-        }
-        if (d2f > cut2) return;
+        if (coarse_d2<D, Real>(p, parts, idx, oi, per, j, rowbase, sy, sz) > cut2) return;
         // exact test in FP64, as written in section 2.2
         double dx[3] = {0.0, 0.0, 0.0};
         double d2 = 0.0;
@@ -718,62 +644,7 @@ k_detect(StepParams<Real> p, Particles<Real> parts, CellList cells, int *__restr
             best_d2 = d2;
         }
     };
-    // The neighbourhood is visited one lattice row (along x) at a time: the
-    // cells x-1, x, x+1 of a row are consecutive in the cell list, so a row
-    // is one range of slots.  The slot ranges of the three rows of a plane
-    // are read together.  Where a periodic x face wraps, the cell across it
-    // is visited separately.
-    int x0 = idx[0] - 1, x1 = idx[0] + 1, xw = -1;
-    if (x0 < 0) {
-        x0 = 0;
-        if (per[0]) xw = p.n[0] - 1;
-    }
-    if (x1 >= p.n[0]) {
-        x1 = p.n[0] - 1;
-        if (per[0]) xw = 0;
-    }
-    const int oz0 = (D == 3) ? -1 : 0, oz1 = (D == 3) ? 1 : 0;
-#pragma unroll 1
-    for (int oz = oz0; oz <= oz1; ++oz) {
-        int qz = idx[2] + oz;
-        if (D == 3 && (qz < 0 || qz >= p.n[2])) {
-            if (!per[2]) continue;
-            qz = qz < 0 ? qz + p.n[2] : qz - p.n[2];
-        }
-        int rb[3], j0[3], j1[3];
-        unsigned rows_ok = 0;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            int qy = idx[1] + r - 1;
-            bool ok = true;
-            if (qy < 0 || qy >= p.n[1]) {
-                ok = per[1];
-                qy = qy < 0 ? qy + p.n[1] : qy - p.n[1];
-            }
-            rows_ok |= ok ? 1u << r : 0u;
-            rb[r] = p.n[0] * (qy + p.n[1] * qz);
-            j0[r] = ok ? cells.begin(rb[r] + x0) : 0;
-            j1[r] = ok ? cells.begin(rb[r] + x1 + 1) : 0;
-        }
-        const float sz = (float)oz;
-        // the three ranges as one loop, so that a warp iterates max over its
-        // threads of the total rather than the sum of per-row maxima
-        const int n0 = j1[0] - j0[0], n01 = n0 + (j1[1] - j0[1]);
-        const int ntot = n01 + (j1[2] - j0[2]);
-        for (int t = 0; t < ntot; ++t) {
-            const int r = t < n0 ? 0 : (t < n01 ? 1 : 2);
-            const int j = r == 0 ? j0[0] + t : (r == 1 ? j0[1] + (t - n0) : j0[2] + (t - n01));
-            test(j, r == 0 ? rb[0] : (r == 1 ? rb[1] : rb[2]), (float)(r - 1), sz);
-        }
-        if (xw >= 0) {
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                if (!((rows_ok >> r) & 1u)) continue;
-                const int w0 = cells.begin(rb[r] + xw), w1 = cells.begin(rb[r] + xw + 1);
-                for (int j = w0; j < w1; ++j) test(j, rb[r], (float)(r - 1), sz);
-            }
-        }
-    }
+    visit_neighbours<D, Real>(p, cells, idx, per, oi, cut, test);
     int bits = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) {

@@ -28,9 +28,11 @@ FIELD_VS, FIELD_NTOT, FIELD_TAU_T, FIELD_UACT, FIELD_EPS_G = 16, 32, 64, 128, 25
 VOIDAGE_2D, VOIDAGE_G = 0, 1
 FIELD_NAMES = ["rho", "u", "fpg", "beta", "vs", "ntot", "tau_t", "uact", "eps_g"]
 VECTOR_FIELDS = {"u", "fpg", "vs", "uact"}
-PDIAG_FPRE, PDIAG_FD, PDIAG_BEST, PDIAG_WALL, PDIAG_CELL, PDIAG_ORDER = 0, 1, 2, 3, 4, 5
+PDIAG_FPRE, PDIAG_FD, PDIAG_BEST, PDIAG_WALL, PDIAG_CELL, PDIAG_ORDER, PDIAG_FC = range(7)
+COLLIDE_HARD, COLLIDE_SOFT = 0, 1
 CONST_NAMES = ["tau", "nu", "mu", "rho_s", "d", "r", "vp", "mp", "e", "g_eff_x", "g_eff_y",
-               "g_eff_z", "fb_x", "fb_y", "fb_z", "u0_x", "u0_y", "u0_z", "cs_smag"]
+               "g_eff_z", "fb_x", "fb_y", "fb_z", "u0_x", "u0_y", "u0_z", "cs_smag",
+               "kn", "eta", "eta_w"]
 KERNEL_CLASSES = ["collide_stream", "drag", "sort", "collide_particles"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -48,7 +50,8 @@ class LatticeDesc(ctypes.Structure):
 class ParticleDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d_p", ctypes.c_double), ("rho_s", ctypes.c_double),
                 ("e", ctypes.c_double), ("pos", _dp), ("vel", _dp),
-                ("recirculate", ctypes.c_int)]
+                ("recirculate", ctypes.c_int), ("collision_model", ctypes.c_int),
+                ("dem_kn", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):
@@ -189,7 +192,8 @@ def describe(w, storage: Optional[int] = None, diagnostics: bool = False,
     vel = np.ascontiguousarray(w.vel, dtype=np.float64)
     keep += [pos, vel]
     par = ParticleDesc(pos.shape[0], float(w.d_p), float(w.rho_s), float(w.e), _ptr(pos),
-                       _ptr(vel), int(w.recirculate))
+                       _ptr(vel), int(w.recirculate), int(getattr(w, "collision_model", 0)),
+                       float(getattr(w, "dem_kn", 0.0)))
     prm = Params()
     prm.rho_g, prm.mu_g = float(w.rho_g), float(w.mu_g)
     for a in range(3):
@@ -352,7 +356,7 @@ class Bed:
         _check(lib().lbdps_set_populations(self._h, _ptr(f), f.size), "lbdps_set_populations")
 
     def particle_diag(self, which: int) -> np.ndarray:
-        vec = which in (PDIAG_FPRE, PDIAG_FD)
+        vec = which in (PDIAG_FPRE, PDIAG_FD, PDIAG_FC)
         n = self.np * (self.dim if vec else 1)
         out = np.empty(max(n, 1))
         _check(lib().lbdps_particle_diag(self._h, int(which), _ptr(out), n), "lbdps_particle_diag")

@@ -215,7 +215,7 @@ def soft_spheres(w: Workload, contact_steps: float = 20.0, e: Optional[float] = 
 
 def packed_bed(dim=2, n=(32, 64), fill_rows=None, gap=0.9, n_particles=None,
                seed=SEED_BASE + 7, storage=STORE_F64, contact_steps=20.0, e=0.7,
-               sigma_v=0.05) -> Workload:
+               sigma_v=0.05, cs_smag=0.0) -> Workload:
     """A dense soft-sphere bed of Table 1 particles (54 um, 930 kg/m^3, h =
     2.7e-4 m, dt = 1.35e-6 s) whose centres are only ``gap`` d_p apart at
     least, so that many pairs start in contact: random sequential addition in
@@ -243,7 +243,7 @@ def packed_bed(dim=2, n=(32, 64), fill_rows=None, gap=0.9, n_particles=None,
     w = Workload(
         name=f"packed{dim}d-{'x'.join(map(str, n))}-N{n_particles}", dim=dim, n=n, bc=bc, h=h,
         dt=dt, d_p=d_p, rho_s=930.0, e=e, pos=pos, vel=vel, rho_g=1.1795, mu_g=1.8872e-5, g=g,
-        storage=storage, seed=seed, collision_model=1)
+        storage=storage, seed=seed, collision_model=1, cs_smag=cs_smag)
     return w.with_(dem_kn=dem_stiffness(w, contact_steps))
 
 

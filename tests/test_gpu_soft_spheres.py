@@ -1,0 +1,298 @@
+"""GPU vs oracle: soft-sphere contacts (the DEM option for dense beds).
+
+Both sides start from the same state (the GPU bed's populations and
+particles loaded into the oracle).  The contact forces of a step come from
+that common state, so they are compared per particle: FP64 to 1e-11 and FP32
+to 1e-5 of the largest force (the overlap is formed from an exact FP64
+difference, so FP32 keeps its relative precision; normals, approach speeds
+and up to a dozen contacts per particle are summed in FP32).  The integrated
+state then follows the drag bounds of the hard-sphere parity tests.
+"""
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+sys.path.insert(0, HERE)
+
+from oracle import oracle as O                      # noqa: E402
+from paper_1303_2653_gb300 import workloads as W    # noqa: E402
+from test_gpu_parity import TOL_DERIVED, _compare_step, _pair, _particle_compare   # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1303_2653_gb300 import build
+    build.build_all()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _lb():
+    from paper_1303_2653_gb300 import lbdps as L
+    return L
+
+
+def _packed(name, storage):
+    if name == "packed2d":
+        return W.packed_bed(dim=2, n=(24, 48), storage=storage)
+    return W.packed_bed(dim=3, n=(8, 8, 12), storage=storage, seed=W.SEED_BASE + 8)
+
+
+def _lattice_pair(e, contact_steps, storage, v=1e-3):
+    """Head-on pair in a periodic 16 x 8 box, h = dt = rho_g = 1 (lattice
+    units), heavy particles so that the gas barely acts on them."""
+    d, rho_s = 0.5, 1e6
+    mp = rho_s * math.pi * d ** 3 / 6.0
+    kn = 0.5 * mp * (math.pi / contact_steps) ** 2
+    # the gap closes in 21.3 steps: no step ends near the contact threshold,
+    # so that both sides start the contact in the same step
+    P = np.array([[8 - 0.25 - 0.0213, 4.3], [8 + 0.25 + 0.0213, 4.3]])
+    V = np.array([[v, 0.0], [-v, 0.0]])
+    return W.Workload(name="pair", dim=2, n=(16, 8), bc=(W.PERIODIC,) * 6, h=1.0, dt=1.0, d_p=d,
+                      rho_s=rho_s, e=e, pos=P, vel=V, rho_g=1.0, mu_g=0.1, storage=storage,
+                      collision_model=1, dem_kn=kn)
+
+
+def test_soft_constants_match_oracle():
+    L = _lb()
+    w = _packed("packed2d", W.STORE_F32)
+    bed, ob = _pair(w, W.STORE_F32)
+    g, o = bed.constants(), ob.constants()
+    for k in ("kn", "eta", "eta_w", "mp", "d", "r"):
+        assert g[k] == pytest.approx(o[k], rel=1e-15), k
+    assert g["kn"] > 0 and g["eta"] > 0
+    bed.close()
+
+
+@pytest.mark.parametrize("name", ["packed2d", "packed3d"])
+@pytest.mark.parametrize("storage", [W.STORE_F64, W.STORE_F32])
+def test_soft_one_step_parity(name, storage):
+    L = _lb()
+    w = _packed(name, storage)
+    bed, ob = _pair(w, storage)
+    Pg0, _ = bed.particles()
+    n = w.n
+    c0 = np.floor(Pg0).astype(np.int64)
+    cell0 = c0[:, 0] + n[0] * c0[:, 1] + (n[0] * n[1] * c0[:, 2] if w.dim == 3 else 0)
+    _compare_step(bed, ob, storage)
+    fc_g = bed.particle_diag(L.PDIAG_FC)
+    fc_o = ob.particle_diag(O.P_FC)
+    in_contact = np.abs(fc_o).sum(axis=1) > 0
+    assert in_contact.mean() > 0.2
+    tol_f = 1e-11 if storage == W.STORE_F64 else 1e-5
+    fmax = np.abs(fc_o).max()
+    err = np.abs(fc_g - fc_o).max(axis=1) / fmax
+    worst = int(np.argmax(err))
+    assert err.max() <= tol_f, (worst, fc_g[worst].tolist(), fc_o[worst].tolist())
+    np.testing.assert_array_equal(np.abs(fc_g).sum(axis=1) > 0, in_contact)
+    # integrated state: the drag bound of the hard-sphere parity tests
+    # (amplified where the Eq. 28 rescale is ill-conditioned) plus the
+    # contact-force bound, each divided by m_p
+    Pg, vg, Po, vo, fd_g, fd_o, kappa_cell = _particle_compare(bed, ob, storage)
+    kappa = kappa_cell[cell0]
+    good = kappa < 1e3
+    assert good.mean() > 0.9
+    tol_d = TOL_DERIVED[storage]
+    amp = np.maximum(1.0, kappa / 100.0)[good][:, None]
+    mp = ob.constants()["mp"]
+    bound = tol_d * np.abs(fd_o).max() * amp / mp + tol_f * fmax / mp
+    vmax = np.abs(vo).max()
+    assert np.all(np.abs(vg[good] - vo[good]) <= bound + tol_d * vmax * amp)
+    assert np.all(np.abs(Pg[good] - Po[good]) <= 4 * (bound + tol_d * vmax * amp) + 1e-13)
+    assert bed.check_guards() == 0
+    bed.close()
+
+
+def test_soft_twenty_steps_fp64():
+    # The gas here is nearly at rest (|u| ~ 1e-7) while the populations are
+    # O(1), so u carries an absolute rounding floor of a few 1e-16 per step
+    # on top of the relative bound
+    L = _lb()
+    w = _packed("packed2d", W.STORE_F64)
+    bed, ob = _pair(w, W.STORE_F64)
+    bed.step(20)
+    ob.step(20)
+    gf = bed.fields(L.FIELD_RHO | L.FIELD_U)
+    u_o = ob.field(O.F_U)
+    assert np.abs(gf["u"] - u_o).max() <= 1e-12 * np.abs(u_o).max() + 20 * 1e-15
+    assert np.abs(gf["rho"] - ob.field(O.F_RHO)).max() <= 20 * 1e-15
+    Pg, vg = bed.particles()
+    Po, vo = ob.particles()
+    assert np.abs(vg - vo).max() <= 1e-9 * np.abs(vo).max()
+    assert np.abs(Pg - Po).max() <= 1e-10
+    bed.close()
+
+
+@pytest.mark.parametrize("storage", [W.STORE_F64, W.STORE_F32])
+@pytest.mark.parametrize("e", [0.9, 0.5])
+def test_soft_pair_collision_on_gpu(storage, e):
+    # the whole contact of a head-on pair, step by step against the oracle
+    L = _lb()
+    w = _lattice_pair(e, 40.0, storage)
+    bed = L.Bed(w, storage=storage)
+    ob = O.OracleBed(w)
+    ob.set_populations(bed.populations())
+    vmax = 2e-3
+    for _ in range(12):
+        bed.step(10)
+        ob.step(10)
+        Pg, vg = bed.particles()
+        Po, vo = ob.particles()
+        tol = 1e-12 if storage == W.STORE_F64 else 2e-5
+        assert np.abs(vg - vo).max() <= tol * vmax
+        assert np.abs(Pg - Po).max() <= 1e-12 + 10 * tol * vmax * 10
+    # separated again with the oracle's restitution
+    e_g = (vg[1, 0] - vg[0, 0]) / vmax
+    e_o = (vo[1, 0] - vo[0, 0]) / vmax
+    assert e_g == pytest.approx(e_o, abs=1e-4)
+    assert Pg[1, 0] - Pg[0, 0] > 0.5
+    bed.close()
+
+
+@pytest.mark.parametrize("storage", [W.STORE_F64, W.STORE_F32])
+def test_soft_sphere_rests_on_the_floor_on_gpu(storage):
+    # overlap on the floor = m_p g_eff / k_n once the bounce has died out
+    L = _lb()
+    g = 1e-5
+    d, rho_s = 0.5, 1e6
+    mp = rho_s * math.pi * d ** 3 / 6.0
+    kn = 0.5 * mp * (math.pi / 40.0) ** 2
+    w = W.Workload(name="floor", dim=2, n=(8, 8), bc=(W.WALL,) * 6, h=1.0, dt=1.0, d_p=d,
+                   rho_s=rho_s, e=0.3, pos=np.array([[3.4, 0.5]]), vel=np.zeros((1, 2)),
+                   rho_g=1.0, mu_g=0.1, g=(0.0, -g, 0.0), storage=storage, collision_model=1,
+                   dem_kn=kn)
+    bed = L.Bed(w, storage=storage)
+    bed.step(3000)
+    P, v = bed.particles()
+    g_eff = (1.0 - 1.0 / rho_s) * g
+    tol = 1e-9 if storage == W.STORE_F64 else 2e-5
+    assert P[0, 1] == pytest.approx(0.25 - mp * g_eff / kn, rel=tol)
+    bed.close()
+
+
+def test_soft_chunked_steps_equal_single_steps():
+    L = _lb()
+    w = _packed("packed2d", W.STORE_F32)
+    a = L.Bed(w, check_every=24)
+    b = L.Bed(w, use_graph=False)
+    a.step(37)
+    for _ in range(37):
+        b.step(1)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    Pa, va = a.particles()
+    Pb, vb = b.particles()
+    np.testing.assert_array_equal(Pa, Pb)
+    np.testing.assert_array_equal(va, vb)
+    assert a.check_guards() == 0 and b.check_guards() == 0
+    a.close()
+    b.close()
+
+
+def test_soft_profiled_classes_and_outlet():
+    # the profiled step reports the contact kernel under the particle class;
+    # with the solids loop closed, a particle leaves through the outlet
+    L = _lb()
+    w = W.cfb_riser2d(nx=16, ny=40, n_particles=60, seed=9, storage=W.STORE_F32, cs_smag=0.0)
+    r = 0.5 * w.d_p / w.h
+    P = np.array([[4.5, w.n[1] - 0.5 * r], [8.5, 0.5 * r]])
+    v = np.array([[0.0, 0.08], [0.0, -0.01]])
+    w = W.soft_spheres(w, contact_steps=20.0).with_(pos=P * w.h, vel=v * w.h / w.dt)
+    bed = L.Bed(w, diagnostics=True)
+    ob = O.OracleBed(w)
+    ob.set_populations(bed.populations())
+    ms = list(bed.step_profiled(1).values())
+    ob.step(1)
+    assert len(ms) == 4 and ms[3] > 0
+    fc = bed.particle_diag(L.PDIAG_FC)
+    np.testing.assert_allclose(fc, ob.particle_diag(O.P_FC), rtol=1e-5, atol=0)
+    assert fc[0, 1] == 0.0 and fc[1, 1] > 0.0
+    assert bed.stats()["solids_out"] == 1
+    bed.close()
+
+
+def test_soft_create_rules():
+    L = _lb()
+    w = _packed("packed2d", W.STORE_F32)
+    # soft spheres may start in contact; hard spheres may not
+    P = w.pos.copy()
+    P[1] = P[0] + np.array([0.5 * w.d_p, 0.0])
+    L.Bed(w.with_(pos=P)).close()
+    with pytest.raises(L.LbdpsError):
+        L.Bed(w.with_(pos=P, collision_model=0))
+    for bad in (dict(dem_kn=0.0), dict(e=0.0), dict(collision_model=2),
+                dict(dem_kn=W.dem_stiffness(w, 3.0))):
+        with pytest.raises(L.LbdpsError) as ei:
+            L.Bed(w.with_(**bad))
+        assert ei.value.code == L.ERR_INVALID
+    # 4 steps per contact is the stiffest accepted
+    L.Bed(w.with_(dem_kn=W.dem_stiffness(w, 4.01))).close()
+    # the contact diagnostic needs the soft model
+    hb = L.Bed(W.scaled_riser2d(nx=32, ny=64), diagnostics=True)
+    with pytest.raises(L.LbdpsError):
+        hb.particle_diag(L.PDIAG_FC)
+    hb.close()
+
+
+def _wide_periodic(collision_model, storage, nx=2050):
+    """Pairs straddling the periodic x face of a 2050-cell-wide box (lattice
+    units): the x separation of a pair across the face is formed from cell
+    offsets of nx - 1, where an FP32 intermediate of that size would round
+    by about 1e-4."""
+    rng = np.random.default_rng(3)
+    d = 0.5
+    P, V = [], []
+    for k in range(12):
+        y = 0.5 + k * 0.9
+        gap = rng.uniform(0.38, 0.52)          # some overlap, some do not touch
+        xa = rng.uniform(0.0, gap)
+        P += [[xa, y], [nx - (gap - xa), y]]
+        V += [[-1e-3, 0.0], [1e-3, 0.0]]       # approaching across the face
+    P, V = np.array(P), np.array(V)
+    return W.Workload(name="wide", dim=2, n=(nx, 12), bc=(W.PERIODIC,) * 6, h=1.0, dt=1.0, d_p=d,
+                      rho_s=1e6, e=0.8, pos=P, vel=V, rho_g=1.0, mu_g=0.1, storage=storage,
+                      collision_model=collision_model,
+                      dem_kn=0.5 * 1e6 * math.pi * d ** 3 / 6.0 * (math.pi / 30.0) ** 2)
+
+
+@pytest.mark.parametrize("storage", [W.STORE_F64, W.STORE_F32])
+def test_contacts_across_a_wide_periodic_face(storage):
+    L = _lb()
+    # soft spheres: forces against the oracle
+    w = _wide_periodic(1, storage)
+    bed = L.Bed(w, storage=storage, diagnostics=True)
+    ob = O.OracleBed(w)
+    ob.set_populations(bed.populations())
+    bed.step(1)
+    ob.step(1)
+    fo = ob.particle_diag(O.P_FC)
+    fg = bed.particle_diag(L.PDIAG_FC)
+    assert (np.abs(fo).sum(axis=1) > 0).sum() >= 8
+    tol = 1e-11 if storage == W.STORE_F64 else 1e-5
+    assert np.abs(fg - fo).max() <= tol * np.abs(fo).max()
+    bed.close()
+    # hard spheres: the same contact pairs as the oracle
+    w = _wide_periodic(0, storage)
+    touching = np.abs(w.pos[0::2, 0] + w.n[0] - w.pos[1::2, 0]) < w.d_p
+    w = w.with_(pos=np.concatenate([w.pos[0::2][~touching], w.pos[1::2][~touching]]),
+                vel=np.concatenate([w.vel[0::2][~touching], w.vel[1::2][~touching]]))
+    bed = L.Bed(w, storage=storage)
+    P, v = bed.particles()
+    # bring each pair into contact across the face, then detect
+    m = len(P) // 2
+    P[m:, 0] = w.n[0] - (0.45 - P[:m, 0])
+    bed.set_particles(P, v)
+    ob = O.OracleBed(w)
+    ob.set_particles(P, v)
+    ob.collide_particles()
+    pg = bed.collide_particles()
+    np.testing.assert_array_equal(pg, ob.pairs())
+    assert len(pg) == m
+    bed.close()
