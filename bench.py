@@ -699,14 +699,16 @@ def bubble_main(args):
 
 def contact_bytes(w, storage):
     """Algorithmic bytes of one soft-sphere contact launch, per particle: its
-    cell index, in-cell offset, velocity and FP64 position read once, the
-    contact force written once, and the cell-list entries of its 3 (2D) or 9
-    (3D) neighbour rows (two ints each).  Reads of the neighbours' state are
-    re-reads of the same arrays (served by L1/L2) and are not counted."""
+    cell index, in-cell offsets and velocity read once, the contact force
+    written once, and the cell-list entries of its 3 (2D) or 9 (3D)
+    neighbour rows (two ints each).  Reads of the neighbours' state are
+    re-reads of the same arrays (served by L1/L2) and are not counted, nor
+    are the FP64 positions, which only pairs within the exact-test band and
+    particles next to a face read."""
     r = 8 if storage == "f64" else 4
     d = w.dim
     rows = 3 if d == 2 else 9
-    per_particle = 4 + d * r + d * r + d * 8 + d * r + rows * 2 * 4
+    per_particle = 4 + d * r + d * r + d * r + rows * 2 * 4
     return per_particle * len(w.pos)
 
 
@@ -758,7 +760,9 @@ def dem_main(args):
             "kernel_ms_per_step": {k: v / prof_steps for k, v in ms.items()},
             "roofline_contacts": {"bound": "hbm", "achieved": ach, "peak": peak,
                                   "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
-                                  "bytes_per_launch": nb},
+                                  "bytes_per_launch": nb,
+                                  "limiter": "instruction issue: the walk over the candidates "
+                                             "of the cells within reach"},
             "health": s["health"], "clocks": clk}
     print(json.dumps(line), flush=True)
     bed.close()
