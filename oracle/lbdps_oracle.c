@@ -68,6 +68,12 @@
  *       eta v_n) along the line of centres, eta = 2 zeta sqrt(m_eff k_n),
  *       zeta = -ln e / sqrt(pi^2 + ln^2 e), m_eff = m/2 (pair) or m (wall);
  *       forces from the state at the start of the step, added in Eq. 16.
+ *   R26 Friction of soft spheres (the tangential contact force §2.2 credits
+ *       DEM with): at the contact point (half way between two centres, or on
+ *       the face) the tangential slip v_t meets -min(gamma_t |v_t|, mu F_n)
+ *       v_t / |v_t|; its torque turns the particles (I = 2/5 m r^2, one spin
+ *       component in 2D, three in 3D), with the spin updated from the
+ *       start-of-step torques.
  */
 #include <math.h>
 #include <stdint.h>
@@ -98,6 +104,8 @@ typedef struct {
     int recirculate;         /* 1: outlet -> inlet re-injection of particles (reading R21) */
     int collision_model;     /* 0: time-driven hard spheres (§2.2); 1: soft spheres (R25) */
     double dem_kn;           /* soft-sphere normal stiffness, N/m */
+    double dem_mu;           /* soft-sphere Coulomb friction coefficient (R26; 0 = none) */
+    double dem_gamma_t;      /* soft-sphere tangential damping, kg/s (R26) */
 } ob_setup;
 
 /* ---- lattice-unit constants derived from an ob_setup ---- */
@@ -112,6 +120,8 @@ typedef struct {
     double wall_u[6][3];
     double cs_smag;
     double kn, eta, eta_w;   /* soft spheres: stiffness, pair and wall damping */
+    double mu_f, gamma_t;    /* soft spheres: friction coefficient, tangential damping */
+    double inertia;          /* moment of inertia of a particle, 2/5 m r^2 */
 } ob_consts;
 
 typedef struct {
@@ -143,6 +153,8 @@ typedef struct {
     int64_t *cell_start;     /* ncell + 1 */
     double *fpre, *fd;       /* np * 3, sorted order, last step */
     double *fc;              /* np * 3, sorted order: soft-sphere contact forces */
+    double *spin;            /* np * 3, sorted order: angular velocity (R26; z only in 2D) */
+    double *tq;              /* np * 3, sorted order: contact torques of the step */
     int model;               /* collision model (0 hard, 1 soft spheres) */
     double *diag_fpre, *diag_fd;   /* np * 3, id order, last step */
     double *diag_fc;               /* np * 3, id order, last step */
@@ -315,6 +327,9 @@ void ob_units(const ob_setup *s, ob_consts *k)
      * restitution e to a linear spring-dashpot pair of reduced mass m/2 (and
      * to a particle against a wall, reduced mass m) */
     k->kn = s->dem_kn * s->dt * s->dt / (s->rho_g * s->h * s->h * s->h);
+    k->mu_f = s->dem_mu;
+    k->gamma_t = s->dem_gamma_t * s->dt / (s->rho_g * s->h * s->h * s->h);
+    k->inertia = 0.4 * k->mp * k->r * k->r;
     k->eta = k->eta_w = 0.0;
     if (s->e > 0.0 && s->e < 1.0 && k->kn > 0.0) {
         double le = log(s->e);
@@ -348,7 +363,7 @@ void ob_destroy(ob_bed *b)
                     b->eps_g, b->omega, b->rho, b->u, b->uact, b->beta, b->fpg,
                     b->tau_t, b->gradp, b->sum_pre, b->sum_abs_pre, b->P, b->v, b->id,
                     b->cell, b->cell_start, b->fpre, b->fd, b->best, b->wall_hit,
-                    b->pairs, b->diag_fpre, b->diag_fd};
+                    b->pairs, b->diag_fpre, b->diag_fd, b->fc, b->diag_fc, b->spin, b->tq};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(b);
 }
@@ -357,7 +372,7 @@ static int alloc_particles(ob_bed *b, int64_t np)
 {
     free(b->P); free(b->v); free(b->id); free(b->cell); free(b->fpre); free(b->fd);
     free(b->best); free(b->wall_hit); free(b->diag_fpre); free(b->diag_fd); free(b->fc);
-    free(b->diag_fc);
+    free(b->diag_fc); free(b->spin); free(b->tq);
     size_t m = (size_t)(np > 0 ? np : 1);
     b->np = np;
     b->P = calloc(m * 3, sizeof(double));
@@ -372,8 +387,10 @@ static int alloc_particles(ob_bed *b, int64_t np)
     b->diag_fd = calloc(m * 3, sizeof(double));
     b->fc = calloc(m * 3, sizeof(double));
     b->diag_fc = calloc(m * 3, sizeof(double));
+    b->spin = calloc(m * 3, sizeof(double));
+    b->tq = calloc(m * 3, sizeof(double));
     return (b->P && b->v && b->id && b->cell && b->fpre && b->fd && b->best && b->wall_hit &&
-            b->diag_fpre && b->diag_fd && b->fc && b->diag_fc);
+            b->diag_fpre && b->diag_fd && b->fc && b->diag_fc && b->spin && b->tq);
 }
 
 ob_bed *ob_create(const ob_setup *s)
@@ -389,6 +406,7 @@ ob_bed *ob_create(const ob_setup *s)
     /* soft spheres need a stiffness and 0 < e <= 1 (R25) */
     if (s->collision_model != 0 && s->collision_model != 1) return NULL;
     if (s->collision_model == 1 && !(s->dem_kn > 0.0 && s->e > 0.0 && s->e <= 1.0)) return NULL;
+    if (!(s->dem_mu >= 0.0) || !(s->dem_gamma_t >= 0.0)) return NULL;
     /* recirculation needs the inlet below and the outlet above (reading R21) */
     if (s->recirculate && !(s->bc[2 * (s->dim - 1)] == OB_INLET && s->bc[2 * s->dim - 1] == OB_OUTLET))
         return NULL;
@@ -486,6 +504,7 @@ static void sort_particles(ob_bed *b)
     sort_key *keys = malloc(sizeof(sort_key) * (size_t)(np > 0 ? np : 1));
     double *P2 = malloc(sizeof(double) * 3 * (size_t)(np > 0 ? np : 1));
     double *v2 = malloc(sizeof(double) * 3 * (size_t)(np > 0 ? np : 1));
+    double *w2 = malloc(sizeof(double) * 3 * (size_t)(np > 0 ? np : 1));
     for (int64_t p = 0; p < np; ++p) {
         keys[p].cell = cell_of(b, &b->P[p * 3]);
         keys[p].id = b->id[p];
@@ -497,10 +516,12 @@ static void sort_particles(ob_bed *b)
         for (int a = 0; a < 3; ++a) {
             P2[p * 3 + a] = b->P[s * 3 + a];
             v2[p * 3 + a] = b->v[s * 3 + a];
+            w2[p * 3 + a] = b->spin[s * 3 + a];
         }
     }
     memcpy(b->P, P2, sizeof(double) * 3 * (size_t)np);
     memcpy(b->v, v2, sizeof(double) * 3 * (size_t)np);
+    memcpy(b->spin, w2, sizeof(double) * 3 * (size_t)np);
     for (int64_t p = 0; p < np; ++p) {
         b->id[p] = keys[p].id;
         b->cell[p] = keys[p].cell;
@@ -511,6 +532,7 @@ static void sort_particles(ob_bed *b)
     free(keys);
     free(P2);
     free(v2);
+    free(w2);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1009,15 +1031,54 @@ static void detect_and_resolve(ob_bed *b)
 /* Soft-sphere contacts (reading R25, the paper's §2.2 outlook on DEM for     */
 /* dense beds): every overlapping pair and every wall overlap pushes with a  */
 /* linear spring-dashpot normal force F = k_n delta - eta (v_rel . n),       */
-/* never pulling.  Forces from the positions and velocities at the start of  */
-/* the step, sorted order.                                                    */
+/* never pulling.  With friction (R26) the contact point's tangential slip   */
+/* meets a viscous force -gamma_t v_t capped at mu F (Coulomb), which also   */
+/* turns the particles.  Forces and torques from the positions and           */
+/* velocities at the start of the step, sorted order.                        */
 /* ------------------------------------------------------------------------ */
+static void cross3(const double *a, const double *b, double *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* One contact seen from particle p: unit normal nrm pointing towards p, lever
+ * arm l from p's centre to the contact point (at -l nrm), normal force fn
+ * (already clipped at zero), relative velocity of the contact point vc
+ * (p's minus the other body's).  Adds the force on p to F and its torque to T. */
+static void contact_add(const ob_bed *b, const double *nrm, double l, double fn, const double *vc,
+                        double *F, double *T)
+{
+    for (int a = 0; a < 3; ++a) F[a] += fn * nrm[a];
+    if (!(b->k.mu_f > 0.0 && b->k.gamma_t > 0.0 && fn > 0.0)) return;
+    double vcn = vc[0] * nrm[0] + vc[1] * nrm[1] + vc[2] * nrm[2];
+    double vt[3], s2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        vt[a] = vc[a] - vcn * nrm[a];
+        s2 += vt[a] * vt[a];
+    }
+    double st = sqrt(s2);
+    if (!(st > 0.0)) return;
+    double mag = b->k.gamma_t * st, cap = b->k.mu_f * fn;
+    if (mag > cap) mag = cap;
+    double Ft[3], arm[3], t[3];
+    for (int a = 0; a < 3; ++a) {
+        Ft[a] = -mag * vt[a] / st;
+        F[a] += Ft[a];
+        arm[a] = -l * nrm[a];
+    }
+    cross3(arm, Ft, t);
+    for (int a = 0; a < 3; ++a) T[a] += t[a];
+}
+
 static void contact_forces(ob_bed *b)
 {
     const int dim = b->dim;
     const double d = b->k.d, r = b->k.r, kn = b->k.kn;
     for (int64_t p = 0; p < b->np; ++p) {
-        double F[3] = {0, 0, 0};
+        double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+        const double *vp = &b->v[p * 3], *wp = &b->spin[p * 3];
         int64_t x = b->cell[p];
         int64_t idx[3] = {x % b->n[0], (x / b->n[0]) % b->n[1], x / ((int64_t)b->n[0] * b->n[1])};
         int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -1042,31 +1103,50 @@ static void contact_forces(ob_bed *b)
                     d2 += dx[a] * dx[a];
                 }
                 if (!(d2 < d * d)) continue;
-                double dist = sqrt(d2), vn = 0.0;
-                for (int a = 0; a < dim; ++a) vn += (b->v[p * 3 + a] - b->v[j * 3 + a]) * (dx[a] / dist);
+                double dist = sqrt(d2), nrm[3], vn = 0.0;
+                for (int a = 0; a < 3; ++a) nrm[a] = dx[a] / dist;
+                for (int a = 0; a < dim; ++a) vn += (vp[a] - b->v[j * 3 + a]) * nrm[a];
                 double f = kn * (d - dist) - b->k.eta * vn;
                 if (f < 0.0) f = 0.0;
-                for (int a = 0; a < dim; ++a) F[a] += f * (dx[a] / dist);
+                /* contact point half way between the centres: relative
+                 * velocity (v_p - v_j) - l (w_p + w_j) x n with l = dist / 2 */
+                double l = 0.5 * dist, ws[3], wxn[3], vc[3];
+                for (int a = 0; a < 3; ++a) ws[a] = wp[a] + b->spin[j * 3 + a];
+                cross3(ws, nrm, wxn);
+                for (int a = 0; a < 3; ++a)
+                    vc[a] = (a < dim ? vp[a] - b->v[j * 3 + a] : 0.0) - l * wxn[a];
+                contact_add(b, nrm, l, f, vc, F, T);
             }
         }
-        /* walls (an open outlet of a circulating bed is not one, R21) */
+        /* walls (an open outlet of a circulating bed is not one, R21): the
+         * contact point lies on the face, at the centre's distance from it */
         for (int a = 0; a < dim; ++a) {
             if (b->bc[2 * a] == OB_PERIODIC) continue;
-            double pa = b->P[p * 3 + a], va = b->v[p * 3 + a];
-            if (pa < r) {
-                double f = kn * (r - pa) - b->k.eta_w * va;
-                if (f > 0.0) F[a] += f;
-            }
-            if (!(b->recirculate && a == dim - 1) && (double)b->n[a] - pa < r) {
-                double f = kn * (r - ((double)b->n[a] - pa)) + b->k.eta_w * va;
-                if (f > 0.0) F[a] -= f;
+            double pa = b->P[p * 3 + a], va = vp[a];
+            for (int side = 0; side < 2; ++side) {
+                if (side == 1 && b->recirculate && a == dim - 1) continue;
+                double l = side == 0 ? pa : (double)b->n[a] - pa;
+                if (!(l < r)) continue;
+                double nrm[3] = {0, 0, 0};
+                nrm[a] = side == 0 ? 1.0 : -1.0;
+                double f = kn * (r - l) - b->k.eta_w * (va * nrm[a]);
+                if (f < 0.0) f = 0.0;
+                double wxn[3], vc[3];
+                cross3(wp, nrm, wxn);
+                for (int c = 0; c < 3; ++c) vc[c] = (c < dim ? vp[c] : 0.0) - l * wxn[c];
+                contact_add(b, nrm, l, f, vc, F, T);
             }
         }
         for (int a = 0; a < 3; ++a) {
-            b->fc[p * 3 + a] = F[a];
-            b->diag_fc[b->id[p] * 3 + a] = F[a];
+            b->fc[p * 3 + a] = a < dim ? F[a] : 0.0;
+            b->tq[p * 3 + a] = T[a];
+            b->diag_fc[b->id[p] * 3 + a] = b->fc[p * 3 + a];
         }
     }
+    /* spin: I dw = T dt, after every torque has been taken from the
+     * start-of-step state (in 2D only the z component is non-zero) */
+    for (int64_t p = 0; p < b->np; ++p)
+        for (int a = 0; a < 3; ++a) b->spin[p * 3 + a] += b->tq[p * 3 + a] / b->k.inertia;
 }
 
 void ob_step(ob_bed *b)
@@ -1105,11 +1185,13 @@ int64_t ob_npairs(const ob_bed *b) { return b->npairs; }
 
 void ob_constants(const ob_bed *b, double *out)
 {
-    /* tau nu mu rho_s d r vp mp e g_eff[3] fb[3] u0[3] cs kn eta eta_w */
+    /* tau nu mu rho_s d r vp mp e g_eff[3] fb[3] u0[3] cs kn eta eta_w mu_f
+     * gamma_t inertia */
     const ob_consts *k = &b->k;
     double v[] = {k->tau, k->nu, k->mu, k->rho_s, k->d, k->r, k->vp, k->mp, k->e,
                   k->g_eff[0], k->g_eff[1], k->g_eff[2], k->fb[0], k->fb[1], k->fb[2],
-                  k->u0[0], k->u0[1], k->u0[2], k->cs_smag, k->kn, k->eta, k->eta_w};
+                  k->u0[0], k->u0[1], k->u0[2], k->cs_smag, k->kn, k->eta, k->eta_w, k->mu_f,
+                  k->gamma_t, k->inertia};
     memcpy(out, v, sizeof(v));
 }
 
@@ -1119,7 +1201,8 @@ void ob_units_flat(const ob_setup *s, double *out)
     ob_units(s, &k);
     double v[] = {k.tau, k.nu, k.mu, k.rho_s, k.d, k.r, k.vp, k.mp, k.e,
                   k.g_eff[0], k.g_eff[1], k.g_eff[2], k.fb[0], k.fb[1], k.fb[2],
-                  k.u0[0], k.u0[1], k.u0[2], k.cs_smag, k.kn, k.eta, k.eta_w};
+                  k.u0[0], k.u0[1], k.u0[2], k.cs_smag, k.kn, k.eta, k.eta_w, k.mu_f,
+                  k.gamma_t, k.inertia};
     memcpy(out, v, sizeof(v));
 }
 
@@ -1158,6 +1241,22 @@ int ob_set_particles(ob_bed *b, int64_t np, const double *P, const double *v)
     }
     sort_particles(b);
     return 0;
+}
+
+/* angular velocities (R26) in id order: the z component per particle in 2D,
+ * three components in 3D */
+void ob_get_spin(const ob_bed *b, double *out)
+{
+    const int nc = b->dim == 2 ? 1 : 3;
+    for (int64_t p = 0; p < b->np; ++p)
+        for (int c = 0; c < nc; ++c) out[b->id[p] * nc + c] = b->spin[p * 3 + (b->dim == 2 ? 2 : c)];
+}
+
+void ob_set_spin(ob_bed *b, const double *in)
+{
+    const int nc = b->dim == 2 ? 1 : 3;
+    for (int64_t p = 0; p < b->np; ++p)
+        for (int c = 0; c < nc; ++c) b->spin[p * 3 + (b->dim == 2 ? 2 : c)] = in[b->id[p] * nc + c];
 }
 
 /* sorted order: ids and cell_start */

@@ -24,7 +24,7 @@ VECTOR_FIELDS = {F_U, F_UACT, F_VS, F_FPG, F_GRADP, F_SUM_PRE, F_SUM_ABS_PRE}
 P_FPRE, P_FD, P_CELL, P_BEST, P_WALL, P_FC = range(6)
 CONST_NAMES = ["tau", "nu", "mu", "rho_s", "d", "r", "vp", "mp", "e", "g_eff_x", "g_eff_y",
                "g_eff_z", "fb_x", "fb_y", "fb_z", "u0_x", "u0_y", "u0_z", "cs_smag",
-               "kn", "eta", "eta_w"]
+               "kn", "eta", "eta_w", "mu_f", "gamma_t", "inertia"]
 
 
 class Setup(ctypes.Structure):
@@ -41,7 +41,8 @@ class Setup(ctypes.Structure):
         ("u0", ctypes.c_double * 3), ("cs_smag", ctypes.c_double),
         ("superficial_mode", ctypes.c_int), ("pressure_plus", ctypes.c_int),
         ("recirculate", ctypes.c_int), ("collision_model", ctypes.c_int),
-        ("dem_kn", ctypes.c_double),
+        ("dem_kn", ctypes.c_double), ("dem_mu", ctypes.c_double),
+        ("dem_gamma_t", ctypes.c_double),
     ]
 
 
@@ -76,6 +77,8 @@ def lib():
         L.ob_set_particles.argtypes = [vp, ctypes.c_int64, dp, dp]
         L.ob_set_particles.restype = ctypes.c_int
         L.ob_get_sorted.argtypes = [vp, i64p, i64p]
+        L.ob_get_spin.argtypes = [vp, dp]
+        L.ob_set_spin.argtypes = [vp, dp]
         L.ob_get_field.argtypes = [vp, ctypes.c_int, dp]
         L.ob_get_field.restype = ctypes.c_int
         L.ob_get_particle_diag.argtypes = [vp, ctypes.c_int, dp]
@@ -142,6 +145,8 @@ def make_setup(w):
     s.recirculate = int(getattr(w, "recirculate", False))
     s.collision_model = int(getattr(w, "collision_model", 0))
     s.dem_kn = float(getattr(w, "dem_kn", 0.0))
+    s.dem_mu = float(getattr(w, "dem_mu", 0.0))
+    s.dem_gamma_t = float(getattr(w, "dem_gamma_t", 0.0))
     return s, keep
 
 
@@ -230,6 +235,19 @@ class OracleBed:
         v = np.ascontiguousarray(v, dtype=np.float64)
         if lib().ob_set_particles(self._h, P.shape[0], _dp(P), _dp(v)) != 0:
             raise MemoryError("oracle particle allocation failed")
+
+    def spin(self) -> np.ndarray:
+        """Angular velocities in id order (lattice units): (N,) in 2D (the z
+        component), (N, 3) in 3D."""
+        nc = 1 if self.dim == 2 else 3
+        out = np.empty(max(self.np, 1) * nc)
+        lib().ob_get_spin(self._h, _dp(out))
+        out = out[: self.np * nc]
+        return out if nc == 1 else out.reshape(self.np, 3)
+
+    def set_spin(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+        lib().ob_set_spin(self._h, _dp(w))
 
     def sorted_ids(self):
         ids = np.empty(max(self.np, 1), dtype=np.int64)

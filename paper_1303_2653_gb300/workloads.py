@@ -112,6 +112,8 @@ class Workload:
     recirculate: bool = False     # outlet -> inlet re-injection of particles
     collision_model: int = 0      # 0: time-driven hard spheres, 1: soft spheres
     dem_kn: float = 0.0           # soft-sphere normal stiffness (N/m)
+    dem_mu: float = 0.0           # soft-sphere Coulomb friction coefficient (0 = none)
+    dem_gamma_t: float = 0.0      # soft-sphere tangential damping (kg/s)
     storage: int = STORE_F32
     steps: int = 1
     seed: int = 0

@@ -989,3 +989,177 @@ def test_soft_sphere_outlet_of_circulating_bed_is_open():
     assert fc[0, 1] == 0.0 and fc[0, 0] == 0.0
     assert fc[1, 1] > 0.0
     assert bed.stats()["solids_out"] == 1
+
+
+# ------------------------------------------------ soft-sphere friction (R26)
+
+def _cross(a, b):
+    return np.cross(np.asarray(a, dtype=float), np.asarray(b, dtype=float))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_friction_turns_sliding_into_rolling(dim):
+    # A sphere set sliding on a floor (no spin) is slowed and spun up by
+    # friction until its contact point stops slipping; the angular momentum
+    # about the contact point is conserved meanwhile, so it rolls on at
+    # v0 / (1 + I / (m l^2)) with l the lever arm (5/7 v0 for l = r), and its
+    # contact point is then at rest.
+    g, v0 = 1e-5, 1e-3
+    d, rho_s, steps = 0.5, 1e9, 40.0
+    mp = rho_s * math.pi * d ** 3 / 6.0
+    kn = 0.5 * mp * (math.pi / steps) ** 2
+    g_eff = (1.0 - 1.0 / rho_s) * g
+    l = 0.25 - mp * g_eff / kn           # resting on its spring
+    n = (16, 8) if dim == 2 else (16, 6, 8)
+    P = np.full((1, dim), 3.0)
+    P[0, -1] = l
+    V = np.zeros((1, dim))
+    V[0, 0] = v0
+    grav = (0.0, -g, 0.0) if dim == 2 else (0.0, 0.0, -g)
+    w, _, _ = _soft(dim=dim, n=n, e=0.3, contact_steps=steps, bc=(W.WALL,) * 6, g=grav, pos=P,
+                    vel=V, rho_s=rho_s, dem_mu=0.5, dem_gamma_t=0.08 * mp)
+    bed = O.OracleBed(w)
+    bed.step(1500)
+    Pn, Vn = bed.particles()
+    spin = bed.spin()
+    inertia = 0.4 * mp * 0.25 ** 2
+    assert bed.constants()["inertia"] == pytest.approx(inertia, rel=1e-14)
+    assert Pn[0, -1] == pytest.approx(l, rel=1e-9)
+    assert Vn[0, 0] == pytest.approx(v0 / (1.0 + inertia / (mp * l * l)), rel=1e-6)
+    # rolling: the contact point (at -l n below the centre) is at rest
+    om = np.array([0.0, 0.0, spin[0]]) if dim == 2 else spin[0]
+    nrm = np.zeros(3)
+    nrm[dim - 1] = 1.0
+    vel = np.zeros(3)
+    vel[:dim] = Vn[0]
+    vc = vel + _cross(om, -l * nrm)
+    assert np.abs(vc).max() <= 1e-6 * v0
+    # the slide lasted about (2/7) v0 / (mu g): far shorter than the run
+    assert Vn[0, 0] < 0.75 * v0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_friction_keeps_angular_momentum_of_a_pair(dim):
+    # An oblique collision of two spinning spheres with friction: the contact
+    # forces are equal and opposite and act at one point half way between the
+    # centres, so the total angular momentum sum m P x v + I w about any point
+    # is kept while the spins change.  The gas acts on the particles at a
+    # relative rate of about 18 nu / (rho_s d^2) = 7e-9 per step: 1e-6 over
+    # the run; a torque of the wrong sign or arm would change L by ~1e-1.
+    d, rho_s = 0.5, 1e9
+    n = (16, 12) if dim == 2 else (12, 12, 12)
+    if dim == 2:
+        P = np.array([[5.0, 6.0], [5.6, 6.2]])
+        V = np.array([[1e-3, 0.0], [-1e-3, 0.0]])
+    else:
+        P = np.array([[5.0, 6.0, 6.0], [5.6, 6.2, 5.9]])
+        V = np.array([[1e-3, 0.0, 2e-4], [-1e-3, 0.0, 0.0]])
+    w, mp, kn = _soft(dim=dim, n=n, d_p=d, rho_s=rho_s, e=0.8, contact_steps=30.0, pos=P, vel=V,
+                      dem_mu=0.4, dem_gamma_t=0.05 * rho_s * math.pi * d ** 3 / 6.0)
+    bed = O.OracleBed(w)
+    spin0 = np.array([2e-3, -1e-3]) if dim == 2 else np.array([[0.0, 1e-3, 2e-3], [-1e-3, 0.0, 0.0]])
+    bed.set_spin(spin0)
+    inertia = bed.constants()["inertia"]
+
+    def ang(Pp, Vp, sp):
+        P3 = np.zeros((2, 3)); V3 = np.zeros((2, 3))
+        P3[:, :dim] = Pp; V3[:, :dim] = Vp
+        om = np.column_stack([np.zeros(2), np.zeros(2), sp]) if dim == 2 else sp
+        return (mp * np.cross(P3, V3)).sum(axis=0) + inertia * om.sum(axis=0)
+
+    L0 = ang(*bed.particles(), bed.spin())
+    bed.step(150)
+    Pn, Vn = bed.particles()
+    L1 = ang(Pn, Vn, bed.spin())
+    assert np.abs(bed.spin() - spin0).max() > 1e-4          # friction acted
+    assert np.abs(L1 - L0).max() <= 1e-6 * np.abs(L0).max()
+
+
+def test_friction_off_reduces_to_the_normal_contact():
+    # mu = 0 (or gamma_t = 0): no tangential force and no spin, the same
+    # state as the frictionless model of R25
+    base = W.packed_bed(dim=2, n=(12, 24))
+    runs = []
+    for mu, gt in ((0.0, 0.0), (0.0, 1e-6), (0.5, 0.0)):
+        bed = O.OracleBed(base.with_(dem_mu=mu, dem_gamma_t=gt))
+        bed.step(3)
+        runs.append((*bed.particles(), bed.spin()))
+    for P, V, sp in runs[1:]:
+        np.testing.assert_array_equal(P, runs[0][0])
+        np.testing.assert_array_equal(V, runs[0][1])
+        assert not sp.any()
+
+
+def _friction_bruteforce(P, v, wz, n, per, d, k, top_open=False):
+    """All pairs and faces with friction (2D: spins about z)."""
+    N, dim = P.shape
+    r = 0.5 * d
+    F = np.zeros((N, 2))
+    T = np.zeros(N)
+
+    def add(i, nrm, l, fn, vc):
+        F[i] += fn * nrm
+        vt = vc - (vc @ nrm) * nrm
+        st = math.sqrt(vt @ vt)
+        if fn > 0 and st > 0:
+            ft = -min(k["gamma_t"] * st, k["mu_f"] * fn) * vt / st
+            F[i] += ft
+            arm = -l * nrm
+            T[i] += arm[0] * ft[1] - arm[1] * ft[0]
+
+    def wx(om, vec):                     # (0, 0, om) x vec in the plane
+        return np.array([-om * vec[1], om * vec[0]])
+
+    for i in range(N):
+        for j in range(N):
+            if i == j:
+                continue
+            dx = P[i] - P[j]
+            for a in range(dim):
+                if per[a]:
+                    dx[a] -= n[a] * round(dx[a] / n[a])
+            dist = math.sqrt(dx @ dx)
+            if dist >= d:
+                continue
+            nrm = dx / dist
+            fn = max(k["kn"] * (d - dist) - k["eta"] * ((v[i] - v[j]) @ nrm), 0.0)
+            l = 0.5 * dist
+            add(i, nrm, l, fn, (v[i] - v[j]) - l * wx(wz[i] + wz[j], nrm))
+        for a in range(dim):
+            if per[a]:
+                continue
+            for side in (0, 1):
+                l = P[i, a] if side == 0 else n[a] - P[i, a]
+                if l >= r:
+                    continue
+                nrm = np.zeros(2)
+                nrm[a] = 1.0 if side == 0 else -1.0
+                fn = max(k["kn"] * (r - l) - k["eta_w"] * (v[i] @ nrm), 0.0)
+                add(i, nrm, l, fn, v[i] - l * wx(wz[i], nrm))
+    return F, T
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_friction_forces_and_torques_match_all_pairs(walls):
+    n = (7, 6)
+    rng = np.random.default_rng(21)
+    d = 0.7
+    box = np.array(n, dtype=float)
+    pos = W.rsa(2, box, [0.36] * 2, box - 0.36, (0, 0, 0) if walls else (1, 1, 1), 0.8 * d, 60, 9)
+    vel = rng.normal(scale=2e-3, size=pos.shape)
+    bc = (W.WALL,) * 6 if walls else (W.PERIODIC,) * 6
+    w, mp, kn = _soft(dim=2, n=n, d_p=d, rho_s=50.0, e=0.6, contact_steps=12.0, bc=bc, pos=pos,
+                      vel=vel, dem_mu=0.3, dem_gamma_t=2.0)
+    bed = O.OracleBed(w)
+    spin0 = rng.normal(scale=5e-3, size=len(pos))
+    bed.set_spin(spin0)
+    P0, v0 = bed.particles()
+    k = bed.constants()
+    bed.step(1)
+    F, T = _friction_bruteforce(P0, v0, spin0, n, [not walls] * 2, d, k)
+    fc = bed.particle_diag(O.P_FC)
+    np.testing.assert_allclose(fc, F, rtol=0, atol=1e-12 * np.abs(F).max())
+    np.testing.assert_allclose(bed.spin() - spin0, T / k["inertia"], rtol=0,
+                               atol=1e-12 * np.abs(T / k["inertia"]).max())
+    # both regimes occur: capped (Coulomb) and viscous contacts
+    assert np.abs(T).max() > 0
