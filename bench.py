@@ -73,6 +73,9 @@ def parse():
                     help="dense soft-sphere bed (Table 1 particles, 256 x 1024 cells, lower half "
                          "packed): step time, kernel split and the contact kernel's roofline")
     ap.add_argument("--dem-steps", type=int, default=400)
+    ap.add_argument("--dem-mu", type=float, default=0.0,
+                    help="friction coefficient of the dense bed (0: normal contacts only; "
+                         "> 0 adds friction with gamma_t = 0.05 m_p / dt and particle spin)")
     return ap.parse_args()
 
 
@@ -697,7 +700,7 @@ def bubble_main(args):
 
 # ------------------------------------------------------------- soft spheres
 
-def contact_bytes(w, storage):
+def contact_bytes(w, storage, friction=False):
     """Algorithmic bytes of one soft-sphere contact launch, per particle: its
     cell index, in-cell offsets and velocity read once, the contact force
     written once, and the cell-list entries of its 3 (2D) or 9 (3D)
@@ -709,6 +712,8 @@ def contact_bytes(w, storage):
     d = w.dim
     rows = 3 if d == 2 else 9
     per_particle = 4 + d * r + d * r + d * r + rows * 2 * 4
+    if friction:   # spin read and the new spin written
+        per_particle += 2 * (1 if d == 2 else 3) * r
     return per_particle * len(w.pos)
 
 
@@ -729,6 +734,8 @@ def dem_main(args):
     st_code = {"f32": W.STORE_F32, "f16": W.STORE_F16, "bf16": W.STORE_BF16,
                "f64": W.STORE_F64}[storage]
     w = W.packed_bed(dim=2, n=(256, 1024), storage=st_code, cs_smag=0.1)
+    if args.dem_mu > 0:
+        w = W.with_friction(w, mu=args.dem_mu, gamma_frac=0.05)
     bed = L.Bed(w, check_every=0)
     st = bed.stream
     bed.step(max(args.warmup, 3))
@@ -746,7 +753,7 @@ def dem_main(args):
     ms = bed.step_profiled(prof_steps)
     peak, peak_kind = measured_peaks()
     t_contact = ms["collide_particles"] / 1e3 / prof_steps
-    nb = contact_bytes(w, storage)
+    nb = contact_bytes(w, storage, friction=args.dem_mu > 0)
     ach = nb / t_contact / 1e9
     s = bed.stats()
     line = {"metric": "dense soft-sphere bed: coupled step throughput", "unit": "MLUPS",
@@ -756,7 +763,8 @@ def dem_main(args):
             "warmup": max(args.warmup, 3), "dtype": {"f64": "f64"}.get(storage, "f32"),
             "storage": storage, "data": "synthetic",
             "config": {"workload": w.name, "cells": w.ncell, "particles": len(w.pos),
-                       "contact_steps": 20, "e": w.e, "cs_smag": w.cs_smag},
+                       "contact_steps": 20, "e": w.e, "cs_smag": w.cs_smag,
+                       "friction_mu": w.dem_mu, "gamma_t_kg_s": w.dem_gamma_t},
             "kernel_ms_per_step": {k: v / prof_steps for k, v in ms.items()},
             "roofline_contacts": {"bound": "hbm", "achieved": ach, "peak": peak,
                                   "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,

@@ -136,6 +136,14 @@ typedef struct {
     double dem_kn;        /* soft-sphere normal stiffness k_n, N/m (> 0 with
                              LBDPS_COLLIDE_SOFT; a pair contact must last at least
                              4 steps: pi sqrt(m_p / (2 k_n)) >= 4 dt) */
+    double dem_mu;        /* soft-sphere friction, the tangential contact force §2.2
+                             credits DEM with: Coulomb coefficient mu >= 0.  With mu > 0
+                             and dem_gamma_t > 0 the contact point's tangential slip v_t
+                             (spins included) meets -min(gamma_t |v_t|, mu F_n) v_t/|v_t|,
+                             whose torque turns the particles (I = 2/5 m_p r^2; one spin
+                             component in 2D, three in 3D).  0 = no friction */
+    double dem_gamma_t;   /* tangential damping gamma_t, kg/s (>= 0; at most 0.25 m_p / dt,
+                             above which the explicit update of a sliding pair is unstable) */
 } lbdps_particle_desc;
 
 #define LBDPS_COLLIDE_HARD 0
@@ -243,8 +251,19 @@ int lbdps_check_guards(lbdps_t *h, int *damaged);
 int lbdps_particles(lbdps_t *h, int units, double *pos, double *vel, int64_t cap);
 
 /* Replace the particle state: n particles in id order, lattice units,
- * n x dim each; sorts them into cells.  Same validation as create. */
+ * n x dim each; sorts them into cells; spins (friction) restart at zero.
+ * Checks that the positions lie inside the domain (no overlap check). */
 int lbdps_set_particles(lbdps_t *h, int64_t n, const double *pos, const double *vel);
+
+/* Particle spins of soft spheres with friction (dem_mu, dem_gamma_t > 0), in id
+ * order: one value per particle in 2D (about the axis normal to the plane,
+ * counter-clockwise positive), three in 3D; rad per step (LBDPS_UNITS_LATTICE)
+ * or rad/s (LBDPS_UNITS_SI).  cap counts doubles.  Zeros without friction. */
+int lbdps_particle_spin(lbdps_t *h, int units, double *out, int64_t cap);
+
+/* Replace the spins (lattice units, layout of lbdps_particle_spin, n particles);
+ * LBDPS_ERR_INVALID without friction. */
+int lbdps_set_particle_spin(lbdps_t *h, const double *in, int64_t n);
 
 /* Copy the pre-collision populations f_i (full values, Eq. 2) as double,
  * layout [q][cell]; cap in doubles (>= q * ncell). */
@@ -272,8 +291,9 @@ int lbdps_stats(lbdps_t *h, lbdps_stats_t *out);
 int lbdps_health(lbdps_t *h, int *health);
 
 /* Lattice-unit constants derived at create, in this order: tau, nu, mu,
- * rho_s/rho_g, d, r, V_p, m_p, e, g_eff[3], F_b[3], u0[3], C_s, and the
- * soft-sphere k_n, eta (pair) and eta (wall), 0 with hard spheres. */
+ * rho_s/rho_g, d, r, V_p, m_p, e, g_eff[3], F_b[3], u0[3], C_s, then (as far
+ * as cap allows) the soft-sphere k_n, eta (pair), eta (wall), mu, gamma_t
+ * (0 with hard spheres) and the moment of inertia 2/5 m_p r^2. */
 int lbdps_constants(lbdps_t *h, double *out, int cap);
 
 /* Shape queries. */

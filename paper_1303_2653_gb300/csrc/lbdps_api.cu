@@ -60,6 +60,8 @@ struct Derived {
     double geff[3], fb[3], u0[3], wall_u[6][3];
     double cs;
     double kn, eta, eta_w;     // soft spheres: stiffness, pair and wall damping
+    double mu_f, gamma_t;      // soft-sphere friction: Coulomb coefficient, tangential damping
+    double inertia;            // 2/5 m_p r^2
 };
 
 constexpr double kPi = 3.141592653589793238462643383;
@@ -98,7 +100,10 @@ Derived derive(const lbdps_lattice_desc &L, const lbdps_particle_desc &Pd, const
             k.eta = 2.0 * z * std::sqrt(0.5 * k.mp * k.kn);
             k.eta_w = 2.0 * z * std::sqrt(k.mp * k.kn);
         }
+        k.mu_f = Pd.dem_mu;
+        k.gamma_t = Pd.dem_gamma_t * L.dt / (P.rho_g * L.h * L.h * L.h);
     }
+    k.inertia = 0.4 * k.mp * k.r * k.r;
     return k;
 }
 
@@ -191,6 +196,8 @@ struct Engine {
     virtual int fields(int mask, int units, double *out, size_t cap) = 0;
     virtual int particles(int units, double *pos, double *vel, int64_t cap) = 0;
     virtual int set_particles(const double *pos, const double *vel) = 0;
+    virtual int spin(int units, double *out, int64_t cap) = 0;
+    virtual int set_spin(const double *in) = 0;
     virtual int populations(double *f, size_t cap) = 0;
     virtual int set_populations(const double *f, size_t count) = 0;
     virtual int particle_diag(int which, double *out, size_t cap) = 0;
@@ -226,6 +233,7 @@ struct lbdps {
     cudaGraphExec_t chunk[2] = {nullptr, nullptr};   // kChunkSteps steps, per starting parity
     int recirculate = 0;               // outlet -> inlet re-injection of particles
     bool soft = false;                 // soft-sphere contacts in place of hard spheres
+    bool friction = false;             // soft spheres with friction (spins kept)
     unsigned *health_host = nullptr;   // pinned: the health word, then 16 doubles of statistics
     double *stats_host = nullptr;      // inside the same pinned block
     std::vector<double> inlet_lat;     // face cells x dim
@@ -238,6 +246,7 @@ namespace {
 // ---------------------------------------------------------------------------
 template <class L, class Real, class S> struct EngineT : Engine {
     static constexpr int D = L::D, Q = L::Q;
+    static constexpr int NW = D == 2 ? 1 : 3;   // spin components
     lbdps *H;
     S *f[2] = {nullptr, nullptr};
     Fields<Real> fld{};
@@ -315,6 +324,14 @@ template <class L, class Real, class S> struct EngineT : Engine {
                 fc[a] = (Real *)get(sizeof(Real) * np);
                 if (!fc[a]) return fail(LBDPS_ERR_OOM, "device allocation failed");
             }
+            if (H->friction)
+                for (int c = 0; c < NW; ++c) {
+                    part[0].w[c] = (Real *)get(sizeof(Real) * np);
+                    part[1].w[c] = (Real *)get(sizeof(Real) * np);
+                    stage.w[c] = (Real *)get(sizeof(Real) * np);
+                    if (!part[0].w[c] || !part[1].w[c] || !stage.w[c])
+                        return fail(LBDPS_ERR_OOM, "device allocation failed");
+                }
             if (H->prm.diagnostics) {
                 diag_fc = (Real *)get(sizeof(Real) * D * np);
                 if (!diag_fc) return fail(LBDPS_ERR_OOM, "device allocation failed");
@@ -431,6 +448,10 @@ template <class L, class Real, class S> struct EngineT : Engine {
         p.kn = (Real)k.kn;
         p.eta = (Real)k.eta;
         p.eta_w = (Real)k.eta_w;
+        p.mu_f = (Real)k.mu_f;
+        p.gamma_t = (Real)k.gamma_t;
+        p.inv_inertia = (Real)(1.0 / k.inertia);
+        for (int c = 0; c < 3; ++c) p.spin_out[c] = H->friction && c < NW ? stage.w[c] : nullptr;
     }
 
     int upload_initial(const double *pos_lat, const double *vel_lat) override
@@ -486,6 +507,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
             CU(cudaStreamSynchronize(st));
         }
         CU(cudaMemcpyAsync(part[nxt].id, ids.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+        for (int c = 0; c < NW && H->friction; ++c)
+            CU(cudaMemsetAsync(part[nxt].w[c], 0, sizeof(Real) * np, st));   // particles start without spin
         CU(cudaStreamSynchronize(st));
         return sort_from(nxt, cur);
     }
@@ -617,6 +640,9 @@ template <class L, class Real, class S> struct EngineT : Engine {
                                cudaMemcpyDeviceToDevice, st));
         }
         CU(cudaMemcpyAsync(part[to].id, part[from].id, sizeof(int) * np, cudaMemcpyDeviceToDevice, st));
+        for (int c = 0; c < NW && H->friction; ++c)
+            CU(cudaMemcpyAsync(part[to].w[c], part[from].w[c], sizeof(Real) * np,
+                               cudaMemcpyDeviceToDevice, st));
         return LBDPS_OK;
     }
 
@@ -719,6 +745,46 @@ template <class L, class Real, class S> struct EngineT : Engine {
                 if (pos) pos[o] = Pd[k] * ps;
                 if (vel) vel[o] = (double)vd[k] * vs;
             }
+        }
+        return LBDPS_OK;
+    }
+
+    // spins in id order: NW values per particle, rad per step (lattice) or rad / s
+    int spin(int units, double *out, int64_t cap) override
+    {
+        const int np = H->np, cur = H->parity;
+        if (cap < (int64_t)np * NW) return fail(LBDPS_ERR_CAPACITY, "need %lld doubles", (long long)np * NW);
+        if (!H->friction) {
+            std::fill(out, out + (size_t)np * NW, 0.0);
+            return LBDPS_OK;
+        }
+        if (np == 0) return LBDPS_OK;
+        std::vector<int> ids;
+        std::vector<Real> wd;
+        int rc = d2h(ids, part[cur].id, np);
+        if (rc) return rc;
+        const double ws = units == LBDPS_UNITS_SI ? 1.0 / H->dt : 1.0;
+        for (int c = 0; c < NW; ++c) {
+            if ((rc = d2h(wd, part[cur].w[c], np))) return rc;
+            for (int k = 0; k < np; ++k) out[(size_t)ids[k] * NW + c] = (double)wd[k] * ws;
+        }
+        return LBDPS_OK;
+    }
+
+    int set_spin(const double *in) override
+    {
+        const int np = H->np, cur = H->parity;
+        if (!H->friction) return fail(LBDPS_ERR_INVALID, "spins need soft spheres with friction");
+        if (np == 0) return LBDPS_OK;
+        std::vector<int> ids;
+        int rc = d2h(ids, part[cur].id, np);
+        if (rc) return rc;
+        std::vector<Real> wd((size_t)np);
+        for (int c = 0; c < NW; ++c) {
+            for (int k = 0; k < np; ++k) wd[k] = (Real)in[(size_t)ids[k] * NW + c];
+            CU(cudaMemcpyAsync(part[cur].w[c], wd.data(), sizeof(Real) * np, cudaMemcpyHostToDevice,
+                               H->stream));
+            CU(cudaStreamSynchronize(H->stream));
         }
         return LBDPS_OK;
     }
@@ -886,7 +952,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
         const size_t nc = (size_t)H->ncell, np = (size_t)H->np;
         return sizeof(S) * pop_slots() + (sizeof(double) + 2 * sizeof(Real)) * D * np +
                2 * sizeof(int) * np + sizeof(int) * (nc + 1) +
-               sizeof(int) * (cell_tiles(H->ncell) + 1) + sizeof(unsigned long long);
+               sizeof(int) * (cell_tiles(H->ncell) + 1) + sizeof(unsigned long long) +
+               (H->friction ? sizeof(Real) * NW * np : 0);
     }
 
     int save(char *buf) override
@@ -915,6 +982,11 @@ template <class L, class Real, class S> struct EngineT : Engine {
                            cudaMemcpyDeviceToHost, st));
         o += sizeof(int) * (cell_tiles(H->ncell) + 1);
         CU(cudaMemcpyAsync(buf + o, solids_out, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        o += sizeof(unsigned long long);
+        for (int c = 0; c < NW && H->friction; ++c) {
+            CU(cudaMemcpyAsync(buf + o, part[cur].w[c], sizeof(Real) * np, cudaMemcpyDeviceToHost, st));
+            o += sizeof(Real) * np;
+        }
         CU(cudaStreamSynchronize(st));
         return LBDPS_OK;
     }
@@ -945,6 +1017,11 @@ template <class L, class Real, class S> struct EngineT : Engine {
                            cudaMemcpyHostToDevice, st));
         o += sizeof(int) * (cell_tiles(H->ncell) + 1);
         CU(cudaMemcpyAsync(solids_out, buf + o, sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+        o += sizeof(unsigned long long);
+        for (int c = 0; c < NW && H->friction; ++c) {
+            CU(cudaMemcpyAsync(part[cur].w[c], buf + o, sizeof(Real) * np, cudaMemcpyHostToDevice, st));
+            o += sizeof(Real) * np;
+        }
         CU(cudaMemsetAsync(counts, 0, sizeof(int) * (nc + 1), st));
         CU(cudaStreamSynchronize(st));
         return LBDPS_OK;
@@ -1187,6 +1264,11 @@ static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc 
     if (soft && !(par->dem_kn > 0 && std::isfinite(par->dem_kn)))
         return fail(LBDPS_ERR_INVALID, "soft spheres need dem_kn > 0");
     if (soft && !(par->e > 0)) return fail(LBDPS_ERR_INVALID, "soft spheres need e > 0");
+    if (!(par->dem_mu >= 0 && std::isfinite(par->dem_mu)) ||
+        !(par->dem_gamma_t >= 0 && std::isfinite(par->dem_gamma_t)))
+        return fail(LBDPS_ERR_INVALID, "dem_mu and dem_gamma_t must be finite and >= 0");
+    const bool friction = par->dem_mu > 0 && par->dem_gamma_t > 0;
+    if (friction && !soft) return fail(LBDPS_ERR_INVALID, "friction needs soft spheres");
     if (par->recirculate && !(bc[2 * (D - 1)] == BC_INLET && bc[2 * (D - 1) + 1] == BC_OUTLET))
         return fail(LBDPS_ERR_INVALID, "recirculate needs the inlet below and the outlet above");
     if (!(prm->rho_g > 0) || !(prm->mu_g > 0)) return fail(LBDPS_ERR_INVALID, "bad gas properties");
@@ -1207,6 +1289,7 @@ static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc 
     h->dt = lat->dt;
     h->recirculate = par->recirculate;
     h->soft = soft;
+    h->friction = friction;
     h->prm = *prm;
     h->k = derive(*lat, *par, *prm);
     const Derived &k = h->k;
@@ -1216,6 +1299,12 @@ static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc 
     if (soft && !(kPi * std::sqrt(0.5 * k.mp / k.kn) >= 4.0))
         return fail(LBDPS_ERR_INVALID, "dem_kn too stiff: a pair contact lasts %.3g steps (at least 4)",
                     kPi * std::sqrt(0.5 * k.mp / k.kn));
+    // the viscous friction of a sliding pair damps the slip by gamma_t
+    // (2 / m_p + 2 r^2 / I) = 7 gamma_t / m_p per step: explicit updates need
+    // it well below 2
+    if (friction && !(k.gamma_t <= 0.25 * k.mp))
+        return fail(LBDPS_ERR_INVALID, "dem_gamma_t too large: %.3g m_p per step (at most 0.25)",
+                    k.gamma_t / k.mp);
     double u0s = 0;
     for (int a = 0; a < D; ++a) u0s += k.u0[a] * k.u0[a];
     if (!(u0s < 0.09)) return fail(LBDPS_ERR_INVALID, "|u0| must be below 0.3 in lattice units");
@@ -1419,6 +1508,21 @@ int lbdps_set_particles(lbdps_t *h, int64_t n, const double *pos, const double *
     return LBDPS_OK;
 }
 
+int lbdps_particle_spin(lbdps_t *h, int units, double *out, int64_t cap)
+{
+    if (!h || !out) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    CU(cudaStreamSynchronize(h->stream));
+    return h->eng->spin(units, out, cap);
+}
+
+int lbdps_set_particle_spin(lbdps_t *h, const double *in, int64_t n)
+{
+    if (!h || (n > 0 && !in)) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    if (n != h->np) return fail(LBDPS_ERR_INVALID, "particle count must stay %d", h->np);
+    CU(cudaStreamSynchronize(h->stream));
+    return h->eng->set_spin(in);
+}
+
 int lbdps_populations(lbdps_t *h, double *f, size_t cap)
 {
     if (!h || !f) return fail(LBDPS_ERR_INVALID, "bad arguments");
@@ -1503,13 +1607,14 @@ int lbdps_constants(lbdps_t *h, double *out, int cap)
 {
     if (!h || !out) return fail(LBDPS_ERR_INVALID, "bad arguments");
     const Derived &k = h->k;
-    const double v[22] = {k.tau, k.nu, k.mu, k.rho_s, k.d, k.r, k.vp, k.mp, k.e,
+    const double v[25] = {k.tau, k.nu, k.mu, k.rho_s, k.d, k.r, k.vp, k.mp, k.e,
                           k.geff[0], k.geff[1], k.geff[2], k.fb[0], k.fb[1], k.fb[2],
-                          k.u0[0], k.u0[1], k.u0[2], k.cs, k.kn, k.eta, k.eta_w};
+                          k.u0[0], k.u0[1], k.u0[2], k.cs, k.kn, k.eta, k.eta_w, k.mu_f,
+                          k.gamma_t, k.inertia};
     // the first 19 are always there; the soft-sphere constants follow when
     // there is room
     if (cap < 19) return fail(LBDPS_ERR_CAPACITY, "need 19 doubles");
-    std::memcpy(out, v, sizeof(double) * (size_t)std::min(cap, 22));
+    std::memcpy(out, v, sizeof(double) * (size_t)std::min(cap, 25));
     return LBDPS_OK;
 }
 

@@ -147,6 +147,10 @@ template <class Real> struct StepParams {
     // with hard spheres), stiffness and pair / wall damping
     Real *fc[3];
     Real kn, eta, eta_w;
+    // soft-sphere friction: Coulomb coefficient, tangential damping and 1 / I
+    // (mu_f = 0: none); the new spins go to spin_out (sorted slot order)
+    Real mu_f, gamma_t, inv_inertia;
+    Real *spin_out[3];
 };
 
 // Layout of the population arrays: the lattice plus one ghost layer on every
@@ -240,6 +244,9 @@ template <class Real> struct Particles {
     int *id;
     int *cell;
     Real *off[3];
+    // angular velocity of soft spheres with friction (null otherwise): the
+    // component normal to the plane in 2D (w[0]), three components in 3D
+    Real *w[3];
 };
 
 // ---------------------------------------------------------------------------

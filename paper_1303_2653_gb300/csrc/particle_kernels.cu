@@ -537,13 +537,19 @@ k_gather(CellList cells, const int2 *__restrict__ slot, const int *__restrict__ 
     if (s >= np) return;
     const int2 kc = slot[s];
     const int my = idslot[s];
+    constexpr int NW = D == 2 ? 1 : 3;   // spin components
+    const bool spin = src.w[0] != nullptr;
     double P[D];
-    Real v[D], off[D];
+    Real v[D], off[D], w[NW];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         P[a] = __ldg(src.P[a] + kc.x);
         v[a] = __ldg(src.v[a] + kc.x);
         off[a] = __ldg(src.off[a] + kc.x);
+    }
+    if (spin) {
+#pragma unroll
+        for (int c = 0; c < NW; ++c) w[c] = __ldg(src.w[c] + kc.x);
     }
     const int lo = cells.begin(kc.y), hi = cells.begin(kc.y + 1);
     int rank = 0;
@@ -555,6 +561,10 @@ k_gather(CellList cells, const int2 *__restrict__ slot, const int *__restrict__ 
         dst.P[a][d] = P[a];
         dst.v[a][d] = v[a];
         dst.off[a][d] = off[a];
+    }
+    if (spin) {
+#pragma unroll
+        for (int c = 0; c < NW; ++c) dst.w[c][d] = w[c];
     }
     dst.id[d] = my;
     dst.cell[d] = kc.y;

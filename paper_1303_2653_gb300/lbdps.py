@@ -32,7 +32,7 @@ PDIAG_FPRE, PDIAG_FD, PDIAG_BEST, PDIAG_WALL, PDIAG_CELL, PDIAG_ORDER, PDIAG_FC 
 COLLIDE_HARD, COLLIDE_SOFT = 0, 1
 CONST_NAMES = ["tau", "nu", "mu", "rho_s", "d", "r", "vp", "mp", "e", "g_eff_x", "g_eff_y",
                "g_eff_z", "fb_x", "fb_y", "fb_z", "u0_x", "u0_y", "u0_z", "cs_smag",
-               "kn", "eta", "eta_w"]
+               "kn", "eta", "eta_w", "mu_f", "gamma_t", "inertia"]
 KERNEL_CLASSES = ["collide_stream", "drag", "sort", "collide_particles"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -51,7 +51,8 @@ class ParticleDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d_p", ctypes.c_double), ("rho_s", ctypes.c_double),
                 ("e", ctypes.c_double), ("pos", _dp), ("vel", _dp),
                 ("recirculate", ctypes.c_int), ("collision_model", ctypes.c_int),
-                ("dem_kn", ctypes.c_double)]
+                ("dem_kn", ctypes.c_double), ("dem_mu", ctypes.c_double),
+                ("dem_gamma_t", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):
@@ -106,6 +107,8 @@ def lib():
             "lbdps_fields": ([vp, i, i, _dp, sz], i),
             "lbdps_particles": ([vp, i, _dp, _dp, i64], i),
             "lbdps_set_particles": ([vp, i64, _dp, _dp], i),
+            "lbdps_particle_spin": ([vp, i, _dp, i64], i),
+            "lbdps_set_particle_spin": ([vp, _dp, i64], i),
             "lbdps_populations": ([vp, _dp, sz], i),
             "lbdps_set_populations": ([vp, _dp, sz], i),
             "lbdps_particle_diag": ([vp, i, _dp, sz], i),
@@ -193,7 +196,8 @@ def describe(w, storage: Optional[int] = None, diagnostics: bool = False,
     keep += [pos, vel]
     par = ParticleDesc(pos.shape[0], float(w.d_p), float(w.rho_s), float(w.e), _ptr(pos),
                        _ptr(vel), int(w.recirculate), int(getattr(w, "collision_model", 0)),
-                       float(getattr(w, "dem_kn", 0.0)))
+                       float(getattr(w, "dem_kn", 0.0)), float(getattr(w, "dem_mu", 0.0)),
+                       float(getattr(w, "dem_gamma_t", 0.0)))
     prm = Params()
     prm.rho_g, prm.mu_g = float(w.rho_g), float(w.mu_g)
     for a in range(3):
@@ -345,6 +349,19 @@ class Bed:
         vel = np.ascontiguousarray(vel, dtype=np.float64)
         _check(lib().lbdps_set_particles(self._h, pos.shape[0], _ptr(pos), _ptr(vel)),
                "lbdps_set_particles")
+
+    def spin(self, units: int = UNITS_LATTICE) -> np.ndarray:
+        """Particle spins in id order: (N,) in 2D, (N, 3) in 3D."""
+        nc = 1 if self.dim == 2 else 3
+        out = np.empty(max(self.np, 1) * nc)
+        _check(lib().lbdps_particle_spin(self._h, int(units), _ptr(out), self.np * nc),
+               "lbdps_particle_spin")
+        out = out[: self.np * nc]
+        return out if nc == 1 else out.reshape(self.np, 3)
+
+    def set_spin(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+        _check(lib().lbdps_set_particle_spin(self._h, _ptr(w), self.np), "lbdps_set_particle_spin")
 
     def populations(self) -> np.ndarray:
         out = np.empty((self.q, self.ncell))

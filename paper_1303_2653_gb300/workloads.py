@@ -215,6 +215,14 @@ def soft_spheres(w: Workload, contact_steps: float = 20.0, e: Optional[float] = 
     return w2.with_(dem_kn=dem_stiffness(w2, contact_steps))
 
 
+def with_friction(w: Workload, mu: float = 0.5, gamma_frac: float = 0.05) -> Workload:
+    """The soft-sphere bed with friction: Coulomb coefficient ``mu`` and the
+    tangential damping ``gamma_frac`` m_p / dt (a sliding pair's slip then
+    relaxes by 7 gamma_frac per step)."""
+    m_p = w.rho_s * math.pi * w.d_p ** 3 / 6.0
+    return w.with_(dem_mu=mu, dem_gamma_t=gamma_frac * m_p / w.dt, name=w.name + "-fric")
+
+
 def packed_bed(dim=2, n=(32, 64), fill_rows=None, gap=0.9, n_particles=None,
                seed=SEED_BASE + 7, storage=STORE_F64, contact_steps=20.0, e=0.7,
                sigma_v=0.05, cs_smag=0.0) -> Workload:

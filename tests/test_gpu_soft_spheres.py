@@ -296,3 +296,131 @@ def test_contacts_across_a_wide_periodic_face(storage):
     np.testing.assert_array_equal(pg, ob.pairs())
     assert len(pg) == m
     bed.close()
+
+
+# ------------------------------------------------------------------ friction
+
+def _fric_pair(w, storage, seed=4):
+    """GPU bed and oracle from the same state, with the same random spins."""
+    bed, ob = _pair(w, storage)
+    rng = np.random.default_rng(seed)
+    nc = 1 if w.dim == 2 else 3
+    spin = rng.normal(scale=2e-3, size=(len(w.pos), nc)).reshape(-1)
+    bed.set_spin(spin)
+    ob.set_spin(bed.spin())
+    return bed, ob
+
+
+def test_friction_constants_match_oracle():
+    w = W.with_friction(_packed("packed2d", W.STORE_F32))
+    bed, ob = _pair(w, W.STORE_F32)
+    g, o = bed.constants(), ob.constants()
+    for k in ("mu_f", "gamma_t", "inertia"):
+        assert g[k] == pytest.approx(o[k], rel=1e-15), k
+    assert g["gamma_t"] > 0
+    bed.close()
+
+
+@pytest.mark.parametrize("name", ["packed2d", "packed3d"])
+@pytest.mark.parametrize("storage", [W.STORE_F64, W.STORE_F32])
+def test_friction_one_step_parity(name, storage):
+    L = _lb()
+    w = W.with_friction(_packed(name, storage))
+    bed, ob = _fric_pair(w, storage)
+    s0 = bed.spin()
+    bed.step(1)
+    ob.step(1)
+    tol = 1e-11 if storage == W.STORE_F64 else 1e-5
+    fc_g, fc_o = bed.particle_diag(L.PDIAG_FC), ob.particle_diag(O.P_FC)
+    assert np.abs(fc_g - fc_o).max() <= tol * np.abs(fc_o).max()
+    ds_g, ds_o = bed.spin() - s0, ob.spin() - s0
+    assert np.abs(ds_o).max() > 0
+    assert np.abs(ds_g - ds_o).max() <= tol * np.abs(ds_o).max()
+    Pg, vg = bed.particles()
+    Po, vo = ob.particles()
+    assert np.abs(vg - vo).max() <= 20 * tol * np.abs(vo).max()
+    assert bed.check_guards() == 0
+    bed.close()
+
+
+def test_friction_ten_steps_fp64():
+    w = W.with_friction(_packed("packed2d", W.STORE_F64))
+    bed, ob = _fric_pair(w, W.STORE_F64)
+    bed.step(10)
+    ob.step(10)
+    Pg, vg = bed.particles()
+    Po, vo = ob.particles()
+    assert np.abs(vg - vo).max() <= 1e-9 * np.abs(vo).max()
+    assert np.abs(Pg - Po).max() <= 1e-10
+    assert np.abs(bed.spin() - ob.spin()).max() <= 1e-9 * np.abs(ob.spin()).max()
+    bed.close()
+
+
+@pytest.mark.parametrize("storage", [W.STORE_F64, W.STORE_F32])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_friction_rolling_on_gpu(storage, dim):
+    # sliding turns into rolling at v0 / (1 + I / (m l^2))
+    L = _lb()
+    g, v0, d, rho_s, steps = 1e-5, 1e-3, 0.5, 1e9, 40.0
+    mp = rho_s * math.pi * d ** 3 / 6.0
+    kn = 0.5 * mp * (math.pi / steps) ** 2
+    l = 0.25 - mp * (1.0 - 1.0 / rho_s) * g / kn
+    n = (16, 8) if dim == 2 else (16, 6, 8)
+    P = np.full((1, dim), 3.0)
+    P[0, -1] = l
+    V = np.zeros((1, dim))
+    V[0, 0] = v0
+    grav = (0.0, -g, 0.0) if dim == 2 else (0.0, 0.0, -g)
+    w = W.Workload(name="roll", dim=dim, n=n, bc=(W.WALL,) * 6, h=1.0, dt=1.0, d_p=d, rho_s=rho_s,
+                   e=0.3, pos=P, vel=V, rho_g=1.0, mu_g=0.1, g=grav, storage=storage,
+                   collision_model=1, dem_kn=kn, dem_mu=0.5, dem_gamma_t=0.08 * mp)
+    bed = L.Bed(w, storage=storage)
+    bed.step(1500)
+    Pn, Vn = bed.particles()
+    inertia = bed.constants()["inertia"]
+    tol = 1e-6 if storage == W.STORE_F64 else 1e-4
+    assert Vn[0, 0] == pytest.approx(v0 / (1.0 + inertia / (mp * l * l)), rel=tol)
+    spin = bed.spin()
+    om = spin[0] if dim == 2 else spin[0, 1]
+    # rolling along +x on a floor below: w_z = -v / l in 2D, w_y = v / l in 3D
+    assert om == pytest.approx((-1.0 if dim == 2 else 1.0) * Vn[0, 0] / l, rel=tol)
+    bed.close()
+
+
+def test_friction_spins_checkpoint_and_reset():
+    L = _lb()
+    w = W.with_friction(_packed("packed2d", W.STORE_F32))
+    a = L.Bed(w)
+    a.step(20)
+    blob = a.save()
+    a.step(15)
+    b = L.Bed(w)
+    b.load(blob)
+    b.step(15)
+    np.testing.assert_array_equal(a.spin(), b.spin())
+    np.testing.assert_array_equal(a.particles()[1], b.particles()[1])
+    assert np.abs(a.spin()).max() > 0
+    P, v = a.particles()
+    a.set_particles(P, v)
+    assert not a.spin().any()
+    a.close()
+    b.close()
+    # spins only exist with friction
+    c = L.Bed(_packed("packed2d", W.STORE_F32))
+    assert not c.spin().any()
+    with pytest.raises(L.LbdpsError):
+        c.set_spin(np.ones(c.np))
+    c.close()
+
+
+def test_friction_create_rules():
+    L = _lb()
+    w = W.with_friction(_packed("packed2d", W.STORE_F32))
+    m_p = w.rho_s * math.pi * w.d_p ** 3 / 6.0
+    for bad in (dict(dem_mu=-0.1), dict(dem_gamma_t=0.3 * m_p / w.dt),
+                dict(collision_model=0, pos=W.scaled_riser2d(nx=32, ny=64).pos,
+                     vel=np.zeros_like(W.scaled_riser2d(nx=32, ny=64).pos))):
+        with pytest.raises(L.LbdpsError) as ei:
+            L.Bed(w.with_(**bad))
+        assert ei.value.code == L.ERR_INVALID
+    L.Bed(w.with_(dem_gamma_t=0.25 * m_p / w.dt * (1 - 1e-9))).close()
