@@ -200,6 +200,14 @@ void lbdps_destroy(lbdps_t *h);
  * check_every steps and LBDPS_ERR_DIVERGED / _DOMAIN is returned. */
 int lbdps_step(lbdps_t *h, int64_t nsteps);
 
+/* Advance nsteps coupled steps and take the FP64 statistics of lbdps_stats
+ * after every one of them, without a host wait between steps: each step's
+ * reductions are copied to pinned host memory on the handle's stream and the
+ * host waits once per 1,024 steps.  out receives nsteps records (host array,
+ * caller-owned), record k describing the state after step k + 1 of the call.
+ * Errors as lbdps_step; LBDPS_ERR_OOM if the pinned buffer cannot be had. */
+int lbdps_step_monitored(lbdps_t *h, int64_t nsteps, lbdps_stats_t *out);
+
 /* Advance nsteps steps launching each kernel separately with CUDA events
  * around it; kernel_ms[k] receives the summed milliseconds of kernel class k
  * (order: collide_stream, drag, sort, collide_particles), cap entries at

@@ -203,6 +203,9 @@ struct Engine {
     virtual int particle_diag(int which, double *out, size_t cap) = 0;
     virtual int collide_particles(int64_t *pairs, int64_t cap, int64_t *npairs) = 0;
     virtual int stats(lbdps_stats_t *out) = 0;
+    // reductions of the current state, written by the kernel into mapped
+    // pinned host memory `dst` (kStatOut doubles) on the stream, no wait
+    virtual int enqueue_stats(double *dst) = 0;
     virtual int health(unsigned *out) = 0;
     virtual int bubbles(double threshold, int voidage, int64_t *out) = 0;
     virtual int set_inlet(const double *inlet_lat) = 0;
@@ -236,10 +239,13 @@ struct lbdps {
     bool friction = false;             // soft spheres with friction (spins kept)
     unsigned *health_host = nullptr;   // pinned: the health word, then 16 doubles of statistics
     double *stats_host = nullptr;      // inside the same pinned block
+    double *mon_host = nullptr;        // pinned: kMonSteps statistics records (lbdps_step_monitored)
     std::vector<double> inlet_lat;     // face cells x dim
 };
 
 namespace {
+
+void decode_stats(lbdps *h, const double *v, bool bed, int64_t steps, lbdps_stats_t *out);
 
 // ---------------------------------------------------------------------------
 // Engine for one instantiation.
@@ -266,7 +272,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
     typename Vec4<Real>::type *tab_pk[2] = {nullptr, nullptr};
     Real *inlet_dev = nullptr;
     unsigned *health_dev = nullptr;
-    double *red_partials = nullptr, *red_out = nullptr;
+    double *red_partials = nullptr;
     unsigned *red_ticket = nullptr;
     unsigned long long *solids_out = nullptr;   // particles through the outlet so far
     BubbleScratch bub{};                         // allocated on the first lbdps_bubbles
@@ -353,14 +359,13 @@ template <class L, class Real, class S> struct EngineT : Engine {
         inlet_dev = (Real *)get(sizeof(Real) * D * std::max(nface, 1));
         health_dev = (unsigned *)get(sizeof(unsigned));
         red_partials = (double *)get(sizeof(double) * kStatPartials);
-        red_out = (double *)get(sizeof(double) * kStatOut);
         red_ticket = (unsigned *)get(sizeof(unsigned));
         solids_out = (unsigned long long *)get(sizeof(unsigned long long));
         npairs_dev = (unsigned long long *)get(sizeof(unsigned long long));
         void *must[] = {f[0], f[1], cl_local[0], cl_local[1], cl_base[0], cl_base[1], fld.rho,
                         fld.node4, key, counts, slot, idslot, tile_total, ticket,
                         best, wall, tab_branch, inlet_dev, health_dev,
-                        red_partials, red_out, red_ticket, solids_out, npairs_dev, part[0].id, part[1].id,
+                        red_partials, red_ticket, solids_out, npairs_dev, part[0].id, part[1].id,
                         part[0].cell, part[1].cell};
         for (void *p : must)
             if (!p) return fail(LBDPS_ERR_OOM, "device allocation failed");
@@ -865,32 +870,29 @@ template <class L, class Real, class S> struct EngineT : Engine {
         return LBDPS_OK;
     }
 
-    // All reductions of the statistics in one pass over the stream: results
-    // at disjoint offsets of red_out, one copy to pinned memory, one wait.
-    int stats(lbdps_stats_t *out) override
+    // All reductions of the statistics in one launch whose last block stores
+    // the results in mapped pinned host memory; stats() then waits once.
+    int enqueue_stats(double *dst) override
     {
         const int cur = H->parity;
         const bool bed = H->prm.diagnostics && H->steps > 0;
+        // the last block of the reduction stores the results over the
+        // host link itself: no copy node follows the kernel on the stream
+        double *dev = nullptr;
+        CU(cudaHostGetDevicePointer((void **)&dev, dst, 0));
         launch_reduce_all<L, Real, S>(lay, H->ncell, f[cur], part[cur], H->k.mp, H->np, cells(cur),
                                       sp.tab.eps_g, H->ntab, bed ? &fld : nullptr, red_partials,
-                                      red_ticket, health_dev, solids_out, red_out, H->stream);
+                                      red_ticket, health_dev, solids_out, dev, H->stream);
         CHECK_LAUNCH();
-        double *v = H->stats_host;
-        CU(cudaMemcpyAsync(v, red_out, sizeof(double) * kStatOut, cudaMemcpyDeviceToHost, H->stream));
+        return LBDPS_OK;
+    }
+
+    int stats(lbdps_stats_t *out) override
+    {
+        int rc = enqueue_stats(H->stats_host);
+        if (rc) return rc;
         CU(cudaStreamSynchronize(H->stream));
-        unsigned long long raw[2] = {0, 0};
-        std::memcpy(raw, v + 11, sizeof(raw));
-        *H->health_host = (unsigned)raw[0];
-        out->solids_out = (int64_t)raw[1];
-        out->mass = v[0] + (double)H->ncell;
-        for (int a = 0; a < 3; ++a) {
-            out->gas_momentum[a] = a < D ? v[1 + a] : 0.0;
-            out->particle_momentum[a] = a < D ? v[4 + a] : 0.0;
-        }
-        out->mean_eps_g = v[7] / (double)H->ncell;
-        out->mean_slip = bed ? (v[10] > 0 ? v[9] / v[10] : 0.0) : NAN;
-        out->steps = H->steps;
-        out->health = (int)*H->health_host;
+        decode_stats(H, H->stats_host, H->prm.diagnostics && H->steps > 0, H->steps, out);
         return LBDPS_OK;
     }
 
@@ -1175,6 +1177,57 @@ int run_steps(lbdps *h, int64_t nsteps)
     return LBDPS_OK;
 }
 
+// One statistics record from the kStatOut doubles of the reduction: the
+// health word and the outlet count travel as raw 64-bit words at the end.
+void decode_stats(lbdps *h, const double *v, bool bed, int64_t steps, lbdps_stats_t *out)
+{
+    const int D = h->dim;
+    unsigned long long raw[2] = {0, 0};
+    std::memcpy(raw, v + kStatValues, sizeof(raw));
+    *h->health_host = (unsigned)raw[0];
+    out->solids_out = (int64_t)raw[1];
+    out->mass = v[0] + (double)h->ncell;
+    for (int a = 0; a < 3; ++a) {
+        out->gas_momentum[a] = a < D ? v[1 + a] : 0.0;
+        out->particle_momentum[a] = a < D ? v[4 + a] : 0.0;
+    }
+    out->mean_eps_g = v[7] / (double)h->ncell;
+    out->mean_slip = bed ? (v[10] > 0 ? v[9] / v[10] : 0.0) : NAN;
+    out->steps = steps;
+    out->health = (int)raw[0];
+}
+
+// Records of the pinned ring used by lbdps_step_monitored: the host waits
+// once per kMonSteps steps.
+constexpr int kMonSteps = 1024;
+
+int run_monitored(lbdps *h, int64_t nsteps, lbdps_stats_t *out)
+{
+    if (!h->mon_host) {
+        if (cudaHostAlloc(&h->mon_host, sizeof(double) * kStatOut * kMonSteps, cudaHostAllocMapped) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            h->mon_host = nullptr;
+            return fail(LBDPS_ERR_OOM, "pinned host allocation failed");
+        }
+    }
+    for (int64_t s = 0; s < nsteps;) {
+        const int k = (int)std::min<int64_t>(kMonSteps, nsteps - s);
+        for (int t = 0; t < k; ++t) {
+            int rc = run_steps(h, 1);
+            if (rc) return rc;
+            rc = h->eng->enqueue_stats(h->mon_host + (size_t)t * kStatOut);
+            if (rc) return rc;
+        }
+        CU(cudaStreamSynchronize(h->stream));
+        const bool bed = h->prm.diagnostics;
+        for (int t = 0; t < k; ++t)
+            decode_stats(h, h->mon_host + (size_t)t * kStatOut, bed, h->steps - k + 1 + t, out + s + t);
+        s += k;
+    }
+    return LBDPS_OK;
+}
+
 void free_graphs(lbdps *h)
 {
     for (int p = 0; p < 2; ++p) {
@@ -1402,7 +1455,8 @@ int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
             rc = fail(LBDPS_ERR_INVALID, "params.alloc returned a block that is not 256-byte aligned");
         return cleanup(rc);
     }
-    if (cudaMallocHost(&h->health_host, 256) != cudaSuccess) {
+    // mapped: the statistics reduction writes its results here directly
+    if (cudaHostAlloc(&h->health_host, 256, cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
         return cleanup(fail(LBDPS_ERR_OOM, "pinned allocation failed"));
     }
@@ -1428,6 +1482,7 @@ void lbdps_destroy(lbdps_t *h)
     h->eng.reset();
     h->mem.release_all();
     if (h->health_host) cudaFreeHost(h->health_host);
+    if (h->mon_host) cudaFreeHost(h->mon_host);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -1436,6 +1491,12 @@ int lbdps_step(lbdps_t *h, int64_t nsteps)
 {
     if (!h || nsteps < 0) return fail(LBDPS_ERR_INVALID, "bad arguments");
     return run_steps(h, nsteps);
+}
+
+int lbdps_step_monitored(lbdps_t *h, int64_t nsteps, lbdps_stats_t *out)
+{
+    if (!h || nsteps < 0 || (nsteps > 0 && !out)) return fail(LBDPS_ERR_INVALID, "bad arguments");
+    return run_monitored(h, nsteps, out);
 }
 
 int lbdps_step_profiled(lbdps_t *h, int64_t nsteps, double *kernel_ms, int cap, int *nclass)

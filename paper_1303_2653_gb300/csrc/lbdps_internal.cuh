@@ -351,7 +351,7 @@ void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int 
 // kStatMaxBlocks blocks, each writing kStatValues partials; out holds
 // kStatValues values plus the health word and the outlet count.
 constexpr int kStatValues = 11;
-constexpr int kStatMaxBlocks = 1024;
+constexpr int kStatMaxBlocks = 304;
 constexpr int kStatPartials = kStatValues * kStatMaxBlocks;
 constexpr int kStatOut = kStatValues + 2;
 

@@ -7,12 +7,14 @@
 // FP64 arithmetic is slow on this part), each warp sums its lanes in the
 // arithmetic type, each block adds its warp totals in FP64 in a fixed order,
 // and the block that finishes last (ticket counter, nothing waits) adds the
-// block partials in block order.  The result does not depend on scheduling.
+// block partials in a fixed order.  The result does not depend on scheduling.
+// `out` is mapped pinned host memory: the last block's stores are the only
+// traffic to the host, so no copy has to follow the launch on the stream.
 #include "lbdps_internal.cuh"
 
 namespace lbdpsk {
 
-constexpr int kRedThreads = 256;
+constexpr int kRedThreads = 512;
 constexpr int kRedMaxBlocks = kStatMaxBlocks;
 
 template <class Real> struct Acc;
@@ -57,49 +59,79 @@ k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> 
     constexpr int D = L::D, Q = L::Q;
     Acc<Real> acc[kStatValues];
     const int stride = gridDim.x * blockDim.x;
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < ncell; x += stride) {
-        int q[3];
-        q[0] = x % lay.n[0];
-        q[1] = (x / lay.n[0]) % lay.n[1];
-        q[2] = x / (lay.n[0] * lay.n[1]);
-        const int xe = lay.ext(q);
-        Real s = Real(0), m[3] = {Real(0), Real(0), Real(0)};
+    // cells in batches of kB per thread (x, x + stride, ...): the loads of
+    // a batch are all issued before any is used, so that each thread keeps
+    // kB cells' worth of memory requests in flight
+    constexpr int kB = Q <= 9 ? 2 : 1;
+    for (int x0 = blockIdx.x * blockDim.x + threadIdx.x; x0 < ncell; x0 += kB * stride) {
+        Real fv[kB][Q];
+        int nn[kB];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            // population i of cell x as the next collision pulls it
-            const Real fi = Store<S>::load(f[(long long)i * lay.nce + xe - lay.off<L>(i)]);
-            s += fi;
+        for (int b = 0; b < kB; ++b) {
+            const int x = x0 + b * stride < ncell ? x0 + b * stride : x0;
+            int q[3];
+            q[0] = x % lay.n[0];
+            q[1] = (x / lay.n[0]) % lay.n[1];
+            q[2] = x / (lay.n[0] * lay.n[1]);
+            const int xe = lay.ext(q);
 #pragma unroll
-            for (int a = 0; a < D; ++a) {
-                if (L::c(i, a) == 1) m[a] += fi;
-                else if (L::c(i, a) == -1) m[a] -= fi;
-            }
+            for (int i = 0; i < Q; ++i)   // population i as the next collision pulls it
+                fv[b][i] = Store<S>::load(f[(long long)i * lay.nce + xe - lay.off<L>(i)]);
+            nn[b] = cells.begin(x + 1) - cells.begin(x);
         }
-        acc[0].add(s);
+        Real ev[kB];
 #pragma unroll
-        for (int a = 0; a < D; ++a) acc[1 + a].add(m[a]);
-        const int n = cells.begin(x + 1) - cells.begin(x);
-        acc[7].add(eps_tab[n < ntab ? n : ntab - 1]);
-        if (BED) {
-            acc[8].add(fld.eps_g[x]);
-            const int nt = fld.ntot[x];
-            if (nt > 0) {
-                const auto r4 = fld.node4[x];
-                const Real ua[3] = {r4.x, r4.y, D == 3 ? r4.z : Real(0)};
-                Real s2 = Real(0);
+        for (int b = 0; b < kB; ++b) ev[b] = eps_tab[nn[b] < ntab ? nn[b] : ntab - 1];
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+            const int x = x0 + b * stride;
+            if (x >= ncell) break;
+            Real sm = Real(0), m[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                sm += fv[b][i];
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
-                    const Real d = ua[a] - fld.vs[a][x];
-                    s2 += d * d;
+                    if (L::c(i, a) == 1) m[a] += fv[b][i];
+                    else if (L::c(i, a) == -1) m[a] -= fv[b][i];
                 }
-                acc[9].add(Real(nt) * sqrt(s2));
-                acc[10].add(Real(nt));
+            }
+            acc[0].add(sm);
+#pragma unroll
+            for (int a = 0; a < D; ++a) acc[1 + a].add(m[a]);
+            acc[7].add(ev[b]);
+            if (BED) {
+                acc[8].add(fld.eps_g[x]);
+                const int nt = fld.ntot[x];
+                if (nt > 0) {
+                    const auto r4 = fld.node4[x];
+                    const Real ua[3] = {r4.x, r4.y, D == 3 ? r4.z : Real(0)};
+                    Real s2 = Real(0);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        const Real d = ua[a] - fld.vs[a][x];
+                        s2 += d * d;
+                    }
+                    acc[9].add(Real(nt) * sqrt(s2));
+                    acc[10].add(Real(nt));
+                }
             }
         }
     }
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride) {
+    // particles in batches of two
+    for (int k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < np; k0 += 2 * stride) {
+        const int k1 = k0 + stride;
+        Real v0[3], v1[3];
 #pragma unroll
-        for (int a = 0; a < D; ++a) acc[4 + a].add(parts.v[a][k]);
+        for (int a = 0; a < D; ++a) {
+            v0[a] = parts.v[a][k0];
+            v1[a] = k1 < np ? parts.v[a][k1] : Real(0);
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            acc[4 + a].add(v0[a]);
+            if (k1 < np) acc[4 + a].add(v1[a]);
+        }
     }
 
     // block partials: warp sums in the arithmetic type, then the eight warp
@@ -127,22 +159,15 @@ k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // the last block: each thread adds the partials of a fixed subset of
-    // blocks (b = thread, thread + 256, ...), then warps and the block add
-    // those in a fixed order, value by value
-    for (int k = 0; k < kStatValues; ++k) {
-        double t = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += kRedThreads)
-            t += __ldcg(partials + b * kStatValues + k);
-        t = warp_sum<double>(t);
-        __syncthreads();
-        if (lane == 0) sh[warp][0] = t;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double u = 0.0;
-            for (int w = 0; w < kWarps; ++w) u += sh[w][0];
-            out[k] = (k >= 4 && k < 7) ? mp * u : u;
-        }
+    // the last block: warp w adds values w, w + 8, ...; its lane l adds the
+    // partials of blocks l, l + 32, ... in that order (independent loads,
+    // issued eight at a time), then the warp adds its lanes in a fixed order
+    for (int k = warp; k < kStatValues; k += kWarps) {
+        double u = 0.0;
+#pragma unroll 8
+        for (int b = lane; b < (int)gridDim.x; b += 32) u += __ldcg(partials + b * kStatValues + k);
+        u = warp_sum<double>(u);
+        if (lane == 0) out[k] = (k >= 4 && k < 7) ? mp * u : u;
     }
     if (threadIdx.x == 0) {
         // the health word and the outlet count travel with the values, so

@@ -103,6 +103,7 @@ def lib():
             "lbdps_destroy": ([vp], None),
             "lbdps_step": ([vp, i64], i),
             "lbdps_step_profiled": ([vp, i64, _dp, i, ctypes.POINTER(i)], i),
+            "lbdps_step_monitored": ([vp, i64, ctypes.POINTER(Stats)], i),
             "lbdps_sync": ([vp], i),
             "lbdps_fields": ([vp, i, i, _dp, sz], i),
             "lbdps_particles": ([vp, i, _dp, _dp, i64], i),
@@ -392,13 +393,23 @@ class Bed:
                                              ctypes.byref(npairs)), "lbdps_collide_particles")
         return buf[: npairs.value].copy()
 
-    def stats(self) -> dict:
-        s = Stats()
-        _check(lib().lbdps_stats(self._h, ctypes.byref(s)), "lbdps_stats")
+    @staticmethod
+    def _stats_dict(s) -> dict:
         return {"mass": s.mass, "gas_momentum": np.array(s.gas_momentum[:]),
                 "particle_momentum": np.array(s.particle_momentum[:]),
                 "mean_eps_g": s.mean_eps_g, "mean_slip": s.mean_slip, "steps": s.steps,
                 "health": s.health, "solids_out": s.solids_out}
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().lbdps_stats(self._h, ctypes.byref(s)), "lbdps_stats")
+        return self._stats_dict(s)
+
+    def step_monitored(self, n: int) -> list:
+        """n steps with the statistics after each one (one dict per step)."""
+        recs = (Stats * max(int(n), 1))()
+        _check(lib().lbdps_step_monitored(self._h, int(n), recs), "lbdps_step_monitored")
+        return [self._stats_dict(recs[k]) for k in range(int(n))]
 
     def bubbles(self, threshold: float = 0.85, voidage: int = 0) -> dict:
         """voidage: VOIDAGE_2D (Eq. 10) or VOIDAGE_G (Eq. 11)."""

@@ -373,11 +373,33 @@ def test_chunked_steps_equal_single_steps(check_every):
     b.close()
 
 
+def test_monitored_steps_equal_step_and_stats():
+    # lbdps_step_monitored queues the statistics of every step without
+    # waiting; each record equals lbdps_stats taken after that step
+    L = _lb()
+    w = W.scaled_riser2d(nx=32, ny=64, seed=43)
+    a = L.Bed(w, diagnostics=True)
+    b = L.Bed(w, diagnostics=True)
+    recs = a.step_monitored(40)
+    assert [r["steps"] for r in recs] == list(range(1, 41))
+    for k in range(40):
+        b.step(1)
+        s = b.stats()
+        for key in ("mass", "mean_eps_g", "mean_slip", "steps", "health", "solids_out"):
+            assert recs[k][key] == s[key], (k, key)
+        np.testing.assert_array_equal(recs[k]["gas_momentum"], s["gas_momentum"])
+        np.testing.assert_array_equal(recs[k]["particle_momentum"], s["particle_momentum"])
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    assert a.step_monitored(0) == []
+    a.close()
+    b.close()
+
+
 def test_no_kernel_writes_past_its_buffers():
     # every device block carries a guard zone; run each entry point that
     # launches kernels on beds large enough for the multi-block paths (the
-    # statistics reduction runs its maximum of 1,024 blocks above 262,144
-    # cells) and check that no guard was touched
+    # statistics reduction runs its maximum of 304 blocks of 512 threads
+    # above 155,648 cells or particles) and check that no guard was touched
     L = _lb()
     for w, st in [(W.riser2d(nx=256, ny=1536, n_particles=100000), W.STORE_F32),
                   (W.scaled_riser3d(nx=48, ny=48, nz=128), W.STORE_F16),
