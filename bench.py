@@ -49,7 +49,7 @@ def parse():
                     help="only build the bed and run this many steps (for ncu captures); "
                          "no timing, no JSON line")
     ap.add_argument("--workload", default="riser2d",
-                    choices=["riser2d", "riser3d", "riser3d-128x128x512"])
+                    choices=["riser2d", "riser3d", "riser3d-128x128x512", "bubbling2d"])
     ap.add_argument("--serving", action="store_true",
                     help="serving benchmark: Poisson stream of independent beds")
     ap.add_argument("--requests", type=int, default=96)
@@ -84,6 +84,10 @@ def workload(storage, name="riser2d"):
     st = {"f32": W.STORE_F32, "f16": W.STORE_F16, "bf16": W.STORE_BF16, "f64": W.STORE_F64}[storage]
     if name == "riser3d":
         return W.riser3d(storage=st)
+    if name == "bubbling2d":
+        # the small single-jet bed (64 x 128, 2,000 particles), FP64 as in
+        # its table row unless another storage is asked for
+        return W.bubbling2d(storage=st)
     if name == "riser3d-128x128x512":
         # the 3D riser at the same solid fraction on an eighth of the lattice
         # (1.6 GB of populations): the case ncu captures of the 3D kernels use
