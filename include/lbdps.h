@@ -187,8 +187,9 @@ typedef struct {
 /* Create a bed (the paper's step 1, Fig. 4).  Validates the description:
  * tau > 1/2, |u| < 0.3 in lattice units, d_p <= h, periodic axes of at least
  * 3 cells, inlet/outlet only on the vertical axis, particles inside the
- * domain and pairwise at least d_p apart.  Returns LBDPS_ERR_INVALID, _OOM
- * or _CUDA on failure and leaves *out NULL. */
+ * domain and (hard spheres) pairwise at least d_p apart, the last checked on
+ * the device after the initial sort.  Returns LBDPS_ERR_INVALID, _OOM or
+ * _CUDA on failure and leaves *out NULL. */
 int lbdps_create(const lbdps_lattice_desc *lattice, const lbdps_particle_desc *particles,
                  const lbdps_params *params, lbdps_t **out);
 

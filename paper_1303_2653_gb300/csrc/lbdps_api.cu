@@ -202,6 +202,9 @@ struct Engine {
     virtual int set_populations(const double *f, size_t count) = 0;
     virtual int particle_diag(int which, double *out, size_t cap) = 0;
     virtual int collide_particles(int64_t *pairs, int64_t cap, int64_t *npairs) = 0;
+    // pairs of the current (sorted) particles closer than d: count and the
+    // pair of smallest ids
+    virtual int overlaps(unsigned long long *count, int *id_i, int *id_j) = 0;
     virtual int stats(lbdps_stats_t *out) = 0;
     // reductions of the current state, written by the kernel into mapped
     // pinned host memory `dst` (kStatOut doubles) on the stream, no wait
@@ -277,6 +280,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
     unsigned long long *solids_out = nullptr;   // particles through the outlet so far
     BubbleScratch bub{};                         // allocated on the first lbdps_bubbles
     unsigned long long *npairs_dev = nullptr;
+    unsigned long long *ovl_dev = nullptr;      // overlap check: count, smallest pair
     StepParams<Real> sp{};
     PopLayout lay{};          // extended lattice of the population arrays
 
@@ -362,10 +366,11 @@ template <class L, class Real, class S> struct EngineT : Engine {
         red_ticket = (unsigned *)get(sizeof(unsigned));
         solids_out = (unsigned long long *)get(sizeof(unsigned long long));
         npairs_dev = (unsigned long long *)get(sizeof(unsigned long long));
+        ovl_dev = (unsigned long long *)get(2 * sizeof(unsigned long long));
         void *must[] = {f[0], f[1], cl_local[0], cl_local[1], cl_base[0], cl_base[1], fld.rho,
                         fld.node4, key, counts, slot, idslot, tile_total, ticket,
                         best, wall, tab_branch, inlet_dev, health_dev,
-                        red_partials, red_ticket, solids_out, npairs_dev, part[0].id, part[1].id,
+                        red_partials, red_ticket, solids_out, npairs_dev, ovl_dev, part[0].id, part[1].id,
                         part[0].cell, part[1].cell};
         for (void *p : must)
             if (!p) return fail(LBDPS_ERR_OOM, "device allocation failed");
@@ -632,6 +637,23 @@ template <class L, class Real, class S> struct EngineT : Engine {
         }
         if (npairs) *npairs = (int64_t)total;
         return result;
+    }
+
+    int overlaps(unsigned long long *count, int *id_i, int *id_j) override
+    {
+        cudaStream_t st = H->stream;
+        const int cur = H->parity;
+        const unsigned long long init[2] = {0ull, ~0ull};
+        CU(cudaMemcpyAsync(ovl_dev, init, sizeof(init), cudaMemcpyHostToDevice, st));
+        launch_overlaps<D, Real>(sp, part[cur], cells(cur), ovl_dev, ovl_dev + 1, H->np, st);
+        CHECK_LAUNCH();
+        unsigned long long res[2] = {0ull, 0ull};
+        CU(cudaMemcpyAsync(res, ovl_dev, sizeof(res), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        *count = res[0];
+        *id_i = (int)(res[1] >> 32);
+        *id_j = (int)(res[1] & 0xffffffffull);
+        return LBDPS_OK;
     }
 
     int copy_particles(int from, int to)
@@ -1045,7 +1067,7 @@ Engine *make_engine_l(lbdps *h)
 // ---------------------------------------------------------------------------
 // Validation helpers.
 // ---------------------------------------------------------------------------
-int validate_positions(const lbdps *h, const double *pos, bool check_overlap)
+int validate_positions(const lbdps *h, const double *pos)
 {
     const int D = h->dim, np = h->np;
     for (int i = 0; i < np; ++i)
@@ -1054,53 +1076,6 @@ int validate_positions(const lbdps *h, const double *pos, bool check_overlap)
             if (!(p >= 0.0 && p < (double)h->n[a]))
                 return fail(LBDPS_ERR_INVALID, "particle %d lies outside the domain on axis %d", i, a);
         }
-    if (!check_overlap || np < 2) return LBDPS_OK;
-    // cell list on the lattice itself (cells are at least one diameter wide)
-    std::vector<int> head((size_t)h->ncell, -1), next((size_t)np, -1);
-    auto cell_of = [&](const double *p) {
-        int q[3] = {0, 0, 0};
-        for (int a = 0; a < D; ++a) q[a] = std::min((int)std::floor(p[a]), h->n[a] - 1);
-        return q[0] + h->n[0] * (q[1] + h->n[1] * q[2]);
-    };
-    for (int i = 0; i < np; ++i) {
-        const int c = cell_of(pos + (size_t)i * D);
-        next[i] = head[c];
-        head[c] = i;
-    }
-    const double d2 = h->k.d * h->k.d;
-    for (int i = 0; i < np; ++i) {
-        const double *pi = pos + (size_t)i * D;
-        int idx[3] = {0, 0, 0};
-        for (int a = 0; a < D; ++a) idx[a] = std::min((int)std::floor(pi[a]), h->n[a] - 1);
-        for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
-        for (int oy = -1; oy <= 1; ++oy)
-        for (int ox = -1; ox <= 1; ++ox) {
-            int q[3] = {idx[0] + ox, idx[1] + oy, idx[2] + oz};
-            bool skip = false;
-            for (int a = 0; a < D; ++a) {
-                if (q[a] < 0 || q[a] >= h->n[a]) {
-                    if (h->bc[2 * a] == BC_PERIODIC) q[a] = (q[a] + h->n[a]) % h->n[a];
-                    else skip = true;
-                }
-            }
-            if (skip) continue;
-            const int c = q[0] + h->n[0] * (q[1] + h->n[1] * q[2]);
-            for (int j = head[c]; j >= 0; j = next[j]) {
-                if (j <= i) continue;
-                double s = 0.0;
-                for (int a = 0; a < D; ++a) {
-                    double dd = pi[a] - pos[(size_t)j * D + a];
-                    if (h->bc[2 * a] == BC_PERIODIC) {
-                        const double L = (double)h->n[a];
-                        if (dd > 0.5 * L) dd -= L;
-                        else if (dd < -0.5 * L) dd += L;
-                    }
-                    s += dd * dd;
-                }
-                if (s < d2) return fail(LBDPS_ERR_INVALID, "particles %d and %d overlap", i, j);
-            }
-        }
-    }
     return LBDPS_OK;
 }
 
@@ -1271,7 +1246,7 @@ extern "C" {
 // Validation, derived constants and lattice-unit particles of a description
 // (no device work).  Shared by lbdps_create and lbdps_memory_estimate.
 static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
-                       const lbdps_params *prm, bool check_overlap, std::unique_ptr<lbdps> &hout,
+                       const lbdps_params *prm, std::unique_ptr<lbdps> &hout,
                        std::vector<double> &pos, std::vector<double> &vel)
 {
     if (!lat || !par || !prm) return fail(LBDPS_ERR_INVALID, "NULL description");
@@ -1395,8 +1370,7 @@ static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc 
         pos[i] = par->pos[i] / lat->h;
         vel[i] = par->vel[i] * vscale;
     }
-    // soft spheres may start in contact
-    int rc = validate_positions(h.get(), pos.data(), check_overlap && !soft);
+    int rc = validate_positions(h.get(), pos.data());
     if (rc) return rc;
     hout = std::move(h);
     return LBDPS_OK;
@@ -1410,7 +1384,7 @@ int lbdps_memory_estimate(const lbdps_lattice_desc *lat, const lbdps_particle_de
     if (!bytes) return fail(LBDPS_ERR_INVALID, "bytes is NULL");
     std::unique_ptr<lbdps> h;
     std::vector<double> pos, vel;
-    int rc = prepare_bed(lat, par, prm, false, h, pos, vel);
+    int rc = prepare_bed(lat, par, prm, h, pos, vel);
     if (rc) return rc;
     h->mem.count_only = true;
     h->eng.reset(h->dim == 2 ? make_engine_l<D2Q9>(h.get()) : make_engine_l<D3Q19>(h.get()));
@@ -1428,7 +1402,9 @@ int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
     *out = nullptr;
     std::unique_ptr<lbdps> h;
     std::vector<double> pos, vel;
-    int rc = prepare_bed(lat, par, prm, true, h, pos, vel);
+    // the pairwise overlap test of hard spheres runs on the device once the
+    // particles are sorted (below); the host checks the domain only
+    int rc = prepare_bed(lat, par, prm, h, pos, vel);
     if (rc) return rc;
     const int D = h->dim;
 
@@ -1469,6 +1445,19 @@ int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
         cudaFreeHost(h->health_host);
         return cleanup(fail(LBDPS_ERR_CUDA, "create: %s", cudaGetErrorString(cudaGetLastError())));
+    }
+    if (!h->soft && h->np > 1) {
+        unsigned long long novl = 0;
+        int oi = 0, oj = 0;
+        if ((rc = h->eng->overlaps(&novl, &oi, &oj))) {
+            cudaFreeHost(h->health_host);
+            return cleanup(rc);
+        }
+        if (novl > 0) {
+            cudaFreeHost(h->health_host);
+            return cleanup(fail(LBDPS_ERR_INVALID, "particles %d and %d overlap (%llu overlapping pairs)",
+                                oi, oj, novl));
+        }
     }
     *out = h.release();
     return LBDPS_OK;
@@ -1560,7 +1549,7 @@ int lbdps_set_particles(lbdps_t *h, int64_t n, const double *pos, const double *
 {
     if (!h || (n > 0 && (!pos || !vel))) return fail(LBDPS_ERR_INVALID, "bad arguments");
     if (n != h->np) return fail(LBDPS_ERR_INVALID, "particle count must stay %d", h->np);
-    int rc = validate_positions(h, pos, false);
+    int rc = validate_positions(h, pos);
     if (rc) return rc;
     CU(cudaStreamSynchronize(h->stream));
     rc = h->eng->set_particles(pos, vel);

@@ -338,6 +338,12 @@ void launch_detect(const StepParams<Real> &p, Particles<Real> parts, CellList ce
 void launch_scan(const int *counts, int *cell_start, int *block_sums, int ncell, cudaStream_t st);
 int scan_block_count(int ncell);
 
+// pairs of particles closer than d (creation check of hard spheres): count
+// and the smallest (id_i << 32 | id_j), i < j
+template <int D, class Real>
+void launch_overlaps(const StepParams<Real> &p, Particles<Real> parts, CellList cells,
+                     unsigned long long *count, unsigned long long *first, int np, cudaStream_t st);
+
 // soft-sphere contact forces of the step into p.fc (sorted slot order)
 template <int D, class Real>
 void launch_contacts(const StepParams<Real> &p, Particles<Real> parts, CellList cells,

@@ -740,6 +740,55 @@ void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int 
 }
 
 // ---------------------------------------------------------------------------
+// Creation check for hard spheres: pairs closer than d (the FP64 test of the
+// detection, without the approach condition).  Counts them and keeps the
+// smallest (id_i, id_j), i < j, as ((u64)id_i << 32) | id_j.
+// ---------------------------------------------------------------------------
+template <int D, class Real>
+__global__ void __launch_bounds__(256)
+k_overlaps(StepParams<Real> p, Particles<Real> parts, CellList cells,
+           unsigned long long *count, unsigned long long *first, int np)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    int idx[3];
+    cell_coords(D, p.n, parts.cell[i], idx);
+    float oi[3] = {0.f, 0.f, 0.f};
+    bool per[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        per[a] = (a < D) && (p.bc[2 * a] == BC_PERIODIC);
+        if (a < D) oi[a] = (float)parts.off[a][i];
+    }
+    const float cut = (float)p.d + 1e-4f;
+    const float cut2 = cut * cut;
+    const int idi = parts.id[i];
+    auto test = [&](int j, int rowbase, float sy, float sz) {
+        const int idj = parts.id[j];
+        if (!(idi < idj)) return;
+        if (coarse_d2<D, Real>(p, parts, idx, oi, per, j, rowbase, sy, sz) > cut2) return;
+        double d2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const double dx = sep_axis(parts.P[a][i], parts.P[a][j], per[a], p.len[a]);
+            d2 = __dadd_rn(d2, __dmul_rn(dx, dx));
+        }
+        if (!(d2 < p.d2)) return;
+        atomicAdd(count, 1ull);
+        atomicMin(first, ((unsigned long long)idi << 32) | (unsigned long long)idj);
+    };
+    visit_neighbours<D, Real>(p, cells, idx, per, oi, cut, test);
+}
+
+template <int D, class Real>
+void launch_overlaps(const StepParams<Real> &p, Particles<Real> parts, CellList cells,
+                     unsigned long long *count, unsigned long long *first, int np, cudaStream_t st)
+{
+    if (np == 0) return;
+    k_overlaps<D, Real><<<(np + 255) / 256, 256, 0, st>>>(p, parts, cells, count, first, np);
+}
+
+// ---------------------------------------------------------------------------
 #define LBDPS_INST_P(D, R)                                                                          \
     template void launch_drag_step<D, R>(const StepParams<R> &, Particles<R>, Particles<R>,        \
                                          CellList, Fields<R>, int *, int *, R *, R *, int,          \
@@ -750,7 +799,10 @@ void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int 
     template void launch_resolve<D, R>(const StepParams<R> &, Particles<R>, const int *,           \
                                        const int *, int, cudaStream_t);                            \
     template void launch_cell_keys<D, R>(const int *, Particles<R>, int *, int *, int,              \
-                                         cudaStream_t);
+                                         cudaStream_t);                                             \
+    template void launch_overlaps<D, R>(const StepParams<R> &, Particles<R>, CellList,              \
+                                        unsigned long long *, unsigned long long *, int,            \
+                                        cudaStream_t);
 
 LBDPS_INST_P(2, double)
 LBDPS_INST_P(2, float)

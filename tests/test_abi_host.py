@@ -68,11 +68,12 @@ def _desc(lib, **over):
     {"bc": (2, 3, 1, 1, 1, 1)},            # inlet on a horizontal axis
     {"n": (2, 8, 1), "bc": (1, 1, 1, 1, 1, 1)},   # periodic axis of 2 cells
     {"d_p": 2e-3},                          # particles wider than a cell
-    {"pos": [[2.5e-3, 2.5e-3], [2.55e-3, 2.5e-3]]},  # overlap
     {"pos": [[9.5e-3, 2.5e-3]]},            # outside the domain
     {"storage": 7},
 ])
 def test_create_rejects_invalid_descriptions_on_host(lib, bad):
+    # (overlapping hard spheres are found on the device after the initial
+    # sort: covered by the GPU tests)
     lat, par, prm, keep = _desc(lib, **bad)
     h = ctypes.c_void_p()
     rc = lib.lib().lbdps_create(ctypes.byref(lat), ctypes.byref(par), ctypes.byref(prm),

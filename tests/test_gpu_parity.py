@@ -426,6 +426,28 @@ def test_create_rejects_invalid():
     with pytest.raises(L.LbdpsError) as ei:
         L.Bed(w.with_(pos=bad))
     assert ei.value.code == L.ERR_INVALID
+    assert "particles 0 and 1 overlap (1 overlapping pairs)" in str(ei.value)
+    # the device check finds pairs across a periodic face and reports the
+    # pair of smallest ids among several
+    P = w.pos.copy()
+    n0h = w.n[0] * w.h
+    ny = w.n[1] * w.h
+    P[7] = [0.5 * n0h, 0.3 * w.d_p]
+    P[3] = [0.5 * n0h, ny - 0.3 * w.d_p]     # across the periodic y face from 7
+    side = -1.0 if P[8, 0] > 0.5 * n0h else 1.0
+    P[9] = P[8] + np.array([side * 0.5 * w.d_p, 0.0])
+    keep = np.ones(len(P), bool)
+    for k in (3, 7, 8, 9):   # clear the neighbourhoods of the planted pairs
+        near = np.abs(P - P[k]).max(axis=1) < 2 * w.d_p
+        near[[3, 7, 8, 9]] = False
+        keep &= ~near
+    new_id = np.cumsum(keep) - 1
+    P, V = P[keep], w.vel[keep]
+    with pytest.raises(L.LbdpsError) as ei:
+        L.Bed(w.with_(pos=P, vel=V))
+    assert "overlap (2 overlapping pairs)" in str(ei.value)
+    ids = [int(t) for t in str(ei.value).split("particles ")[1].split(" overlap")[0].split(" and ")]
+    assert ids == [new_id[3], new_id[7]]
     with pytest.raises(L.LbdpsError):
         L.Bed(w.with_(d_p=2 * w.h))
     with pytest.raises(L.LbdpsError):
