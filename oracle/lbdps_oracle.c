@@ -74,6 +74,9 @@
  *       v_t / |v_t|; its torque turns the particles (I = 2/5 m r^2, one spin
  *       component in 2D, three in 3D), with the spin updated from the
  *       start-of-step torques.
+ *   R27 Optional sequential hard-sphere rule (test only): every pair in
+ *       contact in (id_i, id_j) order, resolved from the velocities the
+ *       earlier ones left if it approaches then; then the walls.
  */
 #include <math.h>
 #include <stdint.h>
@@ -106,6 +109,7 @@ typedef struct {
     double dem_kn;           /* soft-sphere normal stiffness, N/m */
     double dem_mu;           /* soft-sphere Coulomb friction coefficient (R26; 0 = none) */
     double dem_gamma_t;      /* soft-sphere tangential damping, kg/s (R26) */
+    int collision_rule;      /* hard spheres: 0 mutual nearest (R14), 1 sequential (R27) */
 } ob_setup;
 
 /* ---- lattice-unit constants derived from an ob_setup ---- */
@@ -156,6 +160,7 @@ typedef struct {
     double *spin;            /* np * 3, sorted order: angular velocity (R26; z only in 2D) */
     double *tq;              /* np * 3, sorted order: contact torques of the step */
     int model;               /* collision model (0 hard, 1 soft spheres) */
+    int rule;                /* hard-sphere rule: 0 mutual nearest, 1 sequential */
     double *diag_fpre, *diag_fd;   /* np * 3, id order, last step */
     double *diag_fc;               /* np * 3, id order, last step */
     int64_t *best;           /* chosen partner (id) or -1 */
@@ -407,6 +412,7 @@ ob_bed *ob_create(const ob_setup *s)
     if (s->collision_model != 0 && s->collision_model != 1) return NULL;
     if (s->collision_model == 1 && !(s->dem_kn > 0.0 && s->e > 0.0 && s->e <= 1.0)) return NULL;
     if (!(s->dem_mu >= 0.0) || !(s->dem_gamma_t >= 0.0)) return NULL;
+    if (s->collision_rule != 0 && s->collision_rule != 1) return NULL;
     /* recirculation needs the inlet below and the outlet above (reading R21) */
     if (s->recirculate && !(s->bc[2 * (s->dim - 1)] == OB_INLET && s->bc[2 * s->dim - 1] == OB_OUTLET))
         return NULL;
@@ -424,6 +430,7 @@ ob_bed *ob_create(const ob_setup *s)
     b->pressure_plus = s->pressure_plus;
     b->recirculate = s->recirculate;
     b->model = s->collision_model;
+    b->rule = s->collision_rule;
     b->solids_out = 0;
     b->uscale = s->dt / s->h;
     set_lattice(b);
@@ -934,6 +941,8 @@ static void detect_and_resolve(ob_bed *b)
         pos_of[b->id[p]] = p;
     }
     b->npairs = 0;
+    /* every pair in contact, for the sequential rule (R27) */
+    int64_t ncont = 0, capc = 0, *cont = NULL;
 
     for (int64_t p = 0; p < np; ++p) {
         int64_t x = b->cell[p];
@@ -962,6 +971,15 @@ static void detect_and_resolve(ob_bed *b)
                     d2 = d2 + dx[a] * dx[a];
                 }
                 if (!(d2 < dd)) continue;
+                if (b->rule == 1 && b->id[p] < b->id[j]) {
+                    if (ncont == capc) {
+                        capc = capc ? 2 * capc : 64;
+                        cont = realloc(cont, sizeof(int64_t) * 2 * (size_t)capc);
+                    }
+                    cont[2 * ncont] = b->id[p];
+                    cont[2 * ncont + 1] = b->id[j];
+                    ++ncont;
+                }
                 /* approach: (P_i - P_j) . (v_i - v_j) < 0 */
                 double dot = 0.0;
                 for (int a = 0; a < dim; ++a)
@@ -988,6 +1006,42 @@ static void detect_and_resolve(ob_bed *b)
     qsort(b->pairs, (size_t)b->npairs, 2 * sizeof(int64_t), cmp_pair);
 
     for (int64_t p = 0; p < np; ++p) b->best[p] = (bestp[p] >= 0) ? b->id[bestp[p]] : -1;
+
+    if (b->rule == 1) {
+        /* R27: every pair in contact in canonical order (id_i, id_j),
+         * resolved by Eq. 17-18 from the velocities left by the earlier ones
+         * if it approaches then; then every wall contact whose particle
+         * moves toward the face */
+        if (ncont > 0) qsort(cont, (size_t)ncont, 2 * sizeof(int64_t), cmp_pair);
+        for (int64_t k = 0; k < ncont; ++k) {
+            int64_t p = pos_of[cont[2 * k]], j = pos_of[cont[2 * k + 1]];
+            double pi[3] = {0, 0, 0}, pj[3] = {0, 0, 0}, vi[3] = {0, 0, 0}, vj[3] = {0, 0, 0};
+            double dot = 0.0;
+            for (int a = 0; a < dim; ++a) {
+                pi[a] = sep_axis(b, a, b->P[p * 3 + a], b->P[j * 3 + a]);
+                vi[a] = b->v[p * 3 + a];
+                vj[a] = b->v[j * 3 + a];
+                dot = dot + pi[a] * (vi[a] - vj[a]);
+            }
+            if (!(dot < 0.0)) continue;
+            ob_binary_collision(dim, b->k.mp, b->k.mp, b->k.e, pi, pj, vi, vj);
+            for (int a = 0; a < dim; ++a) {
+                b->v[p * 3 + a] = vi[a];
+                b->v[j * 3 + a] = vj[a];
+            }
+        }
+        for (int64_t p = 0; p < np; ++p)
+            for (int a = 0; a < dim; ++a) {
+                double *va = &b->v[p * 3 + a];
+                if (((b->wall_hit[p] >> (2 * a)) & 1) && *va < 0.0) *va = -b->k.e * *va;
+                if (((b->wall_hit[p] >> (2 * a + 1)) & 1) && *va > 0.0) *va = -b->k.e * *va;
+            }
+        free(cont);
+        free(bestd2);
+        free(bestp);
+        free(pos_of);
+        return;
+    }
 
     /* Eq. 17-18 on mutual choices, from the pre-collision velocities */
     double *vnew = malloc(sizeof(double) * 3 * (size_t)(np > 0 ? np : 1));
@@ -1019,6 +1073,7 @@ static void detect_and_resolve(ob_bed *b)
     memcpy(b->v, vnew, sizeof(double) * 3 * (size_t)np);
     free(vnew);
     free(paired);
+    free(cont);
     free(bestd2);
     free(bestp);
     free(pos_of);

@@ -42,7 +42,7 @@ class Setup(ctypes.Structure):
         ("superficial_mode", ctypes.c_int), ("pressure_plus", ctypes.c_int),
         ("recirculate", ctypes.c_int), ("collision_model", ctypes.c_int),
         ("dem_kn", ctypes.c_double), ("dem_mu", ctypes.c_double),
-        ("dem_gamma_t", ctypes.c_double),
+        ("dem_gamma_t", ctypes.c_double), ("collision_rule", ctypes.c_int),
     ]
 
 
@@ -147,6 +147,7 @@ def make_setup(w):
     s.dem_kn = float(getattr(w, "dem_kn", 0.0))
     s.dem_mu = float(getattr(w, "dem_mu", 0.0))
     s.dem_gamma_t = float(getattr(w, "dem_gamma_t", 0.0))
+    s.collision_rule = int(getattr(w, "collision_rule", 0))
     return s, keep
 
 

@@ -1163,3 +1163,71 @@ def test_friction_forces_and_torques_match_all_pairs(walls):
                                atol=1e-12 * np.abs(T / k["inertia"]).max())
     # both regimes occur: capped (Coulomb) and viscous contacts
     assert np.abs(T).max() > 0
+
+
+# ------------------------------------------- sequential hard-sphere rule (R27)
+
+def test_sequential_rule_newtons_cradle():
+    # Three equal spheres in a row, all touching, the first moving into the
+    # others (e = 1).  Resolving the contacts in order and re-checking the
+    # approach passes the velocity down the row at once (0, 0, v); the
+    # mutual-nearest rule (R14) resolves one binary collision per call, as
+    # §2.2 describes binary collisions, and gets there in two.
+    v = 0.01
+    P = np.array([[2.0, 3.5], [2.0 + 0.99 * 0.5, 3.5], [2.0 + 2 * 0.99 * 0.5, 3.5]])
+    V = np.array([[v, 0.0], [0.0, 0.0], [0.0, 0.0]])
+    base = _bed(n=(8, 8), d_p=0.5, e=1.0, pos=np.zeros((0, 2)), vel=np.zeros((0, 2)))
+    seq = O.OracleBed(types.SimpleNamespace(**{**vars(base), "collision_rule": 1}))
+    seq.set_particles(P, V)
+    seq.collide_particles()
+    np.testing.assert_allclose(seq.particles()[1], [[0, 0], [0, 0], [v, 0]], atol=1e-17)
+    match = O.OracleBed(base)
+    match.set_particles(P, V)
+    match.collide_particles()
+    np.testing.assert_allclose(match.particles()[1], [[0, 0], [v, 0], [0, 0]], atol=1e-17)
+    match.set_particles(P, match.particles()[1])
+    match.collide_particles()
+    np.testing.assert_allclose(match.particles()[1], [[0, 0], [0, 0], [v, 0]], atol=1e-17)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_rules_agree_on_isolated_contacts(dim):
+    # When no particle has more than one approaching contact the two rules
+    # resolve the same pairs from the same velocities: identical results.
+    rng = np.random.default_rng(4 + dim)
+    n = (12, 12) if dim == 2 else (8, 8, 8)
+    d = 0.4
+    P, V = [], []
+    for c in range(12):
+        centre = (np.array([2 * (c % 4) + 1.5, 2 * (c // 4) + 1.5, 3.5]))[:dim]
+        u = rng.normal(size=dim)
+        u /= np.linalg.norm(u)
+        P += [centre - 0.45 * d * u, centre + 0.45 * d * u]
+        V += [0.01 * u + rng.normal(scale=1e-3, size=dim), -0.01 * u]
+    P, V = np.array(P), np.array(V)
+    base = _bed(dim=dim, n=n, d_p=d, e=0.7, pos=np.zeros((0, dim)), vel=np.zeros((0, dim)),
+                bc=(W.WALL,) * 6)
+    out = []
+    for rule in (0, 1):
+        bed = O.OracleBed(types.SimpleNamespace(**{**vars(base), "collision_rule": rule}))
+        bed.set_particles(P, V)
+        bed.collide_particles()
+        out.append(bed.particles()[1])
+        assert len(bed.pairs()) == 12
+    np.testing.assert_array_equal(out[0], out[1])
+    assert np.abs(out[0] - V).max() > 1e-3
+
+
+@pytest.mark.parametrize("dim,n,N", [(2, (6, 7), 200), (3, (4, 5, 6), 200)])
+def test_sequential_rule_keeps_momentum(dim, n, N):
+    # a dense, overlapping state in a periodic box: each sequential binary
+    # collision keeps momentum, so the total does
+    P, v = _packed_state(dim, n, N, 0.9, 3)
+    base = _bed(dim=dim, n=n, d_p=0.9, bc=(W.PERIODIC,) * 6, pos=np.zeros((0, dim)),
+                vel=np.zeros((0, dim)))
+    bed = O.OracleBed(types.SimpleNamespace(**{**vars(base), "collision_rule": 1}))
+    bed.set_particles(P, v)
+    bed.collide_particles()
+    v1 = bed.particles()[1]
+    assert np.abs(v1 - v).max() > 1e-3
+    np.testing.assert_allclose(v1.sum(axis=0), v.sum(axis=0), rtol=0, atol=1e-12)
