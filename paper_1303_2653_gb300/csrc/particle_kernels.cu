@@ -133,9 +133,9 @@ __device__ __forceinline__ void drag_pre_one(const StepParams<Real> &p, const Pa
 // Drag and integration (Fig. 4 steps 4-5), one thread per particle.
 //   F_pre of the thread's particle (Eq. 26);
 //   S^a(c) = sum of F_pre^a over the particles of its cell in sorted order
-//           (Eq. 27): members in the same warp come by shuffle, members in a
-//           neighbouring warp are recomputed (bit-identical), so every member
-//           of a cell adds the same values in the same order;
+//           (Eq. 27): members in the same block come from shared memory,
+//           members in a neighbouring block are recomputed (bit-identical),
+//           so every member of a cell adds the same values in the same order;
 //   F_d^a  = |F_p->g^a(c)| / |S^a| F_pre^a (Eq. 28; scale 1 when
 //           |S| <= 1e-12 sum |F_pre|);
 //   v += (1 - rho_g/rho_s) g + (F_d -+ V_p grad p) / m_p, P += v in FP64
@@ -169,12 +169,13 @@ k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, Cell
             Fields<Real> fld, int *__restrict__ key, int *__restrict__ counts, Real *diag_fpre,
             Real *diag_fd, int np)
 {
-    // the integrated state goes to `out` (same slots): other warps may still
+    // the integrated state goes to `out` (same slots): other blocks may still
     // read this particle's pre-step state to complete their cell sums
+    __shared__ Real sfp[D][256];   // pre-drag of the block's particles (blockDim <= 256)
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
     const bool active = k < np;
-    const int warp_first = k - lane;
+    const int block_first = k - (int)threadIdx.x;
+    const int block_end = block_first + (int)blockDim.x;
     int c = -1, s0 = 0, s1 = 0;
     int idx[3] = {0, 0, 0};
     Real fp[3] = {Real(0), Real(0), Real(0)}, gp[3] = {Real(0), Real(0), Real(0)};
@@ -196,32 +197,32 @@ k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, Cell
         for (int a = 0; a < D; ++a) fpg[a] = __ldg(fld.fpg[a] + c);
         cell_coords(D, p.n, c, idx);
         drag_pre_one<D, Real>(p, parts, fld, idx, o0, v0, fp, gp);
+#pragma unroll
+        for (int a = 0; a < D; ++a) sfp[a][threadIdx.x] = fp[a];
     }
-    // Eq. 27 in sorted order
-    const int len = s1 - s0;
-    const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    __syncthreads();
+    if (!active) return;
+    // Eq. 27 in sorted order: members held by this block come from shared
+    // memory, the others are recomputed (bit-identical)
     Real S[3] = {Real(0), Real(0), Real(0)}, A[3] = {Real(0), Real(0), Real(0)};
-    for (int t = 0; t < maxlen; ++t) {
-        const int j = s0 + t;
-        const bool in_warp = (j >= warp_first) && (j < warp_first + 32);
+    for (int j = s0; j < s1; ++j) {
         Real val[3];
+        if (j >= block_first && j < block_end) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) val[a] = __shfl_sync(0xffffffffu, fp[a], (j - warp_first) & 31);
-        if (t < len) {
-            if (!in_warp) {
-                Real g2[3], vj[3], oj[3];
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    vj[a] = __ldg(parts.v[a] + j);
-                    oj[a] = __ldg(parts.off[a] + j);
-                }
-                drag_pre_one<D, Real>(p, parts, fld, idx, oj, vj, val, g2);
-            }
+            for (int a = 0; a < D; ++a) val[a] = sfp[a][j - block_first];
+        } else {
+            Real g2[3], vj[3], oj[3];
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                S[a] += val[a];
-                A[a] += fabs(val[a]);
+                vj[a] = __ldg(parts.v[a] + j);
+                oj[a] = __ldg(parts.off[a] + j);
             }
+            drag_pre_one<D, Real>(p, parts, fld, idx, oj, vj, val, g2);
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            S[a] += val[a];
+            A[a] += fabs(val[a]);
         }
     }
     if (!active) return;
