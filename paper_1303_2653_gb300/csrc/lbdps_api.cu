@@ -209,6 +209,11 @@ struct Engine {
     // reductions of the current state, written by the kernel into mapped
     // pinned host memory `dst` (kStatOut doubles) on the stream, no wait
     virtual int enqueue_stats(double *dst) = 0;
+    // the same on stream st, with the health word and outlet count taken from
+    // snapshot slot `slot` (written by enqueue_snapshot at the end of a step)
+    // instead of the live words
+    virtual int enqueue_stats_snap(double *dst, cudaStream_t st, int slot) = 0;
+    virtual int enqueue_snapshot(int slot) = 0;
     virtual int health(unsigned *out) = 0;
     virtual int bubbles(double threshold, int voidage, int64_t *out) = 0;
     virtual int set_inlet(const double *inlet_lat) = 0;
@@ -243,6 +248,12 @@ struct lbdps {
     unsigned *health_host = nullptr;   // pinned: the health word, then 16 doubles of statistics
     double *stats_host = nullptr;      // inside the same pinned block
     double *mon_host = nullptr;        // pinned: kMonSteps statistics records (lbdps_step_monitored)
+    // monitored steps with the reductions beside the next step: graphs of one
+    // step plus the snapshot of its health word and outlet count (per
+    // starting parity), the reductions' stream and the events that order them
+    cudaGraphExec_t mon_graph[2] = {nullptr, nullptr};
+    cudaStream_t stats_stream = nullptr;
+    cudaEvent_t ev_step[2] = {nullptr, nullptr}, ev_red[2] = {nullptr, nullptr};
     std::vector<double> inlet_lat;     // face cells x dim
 };
 
@@ -281,6 +292,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
     BubbleScratch bub{};                         // allocated on the first lbdps_bubbles
     unsigned long long *npairs_dev = nullptr;
     unsigned long long *ovl_dev = nullptr;      // overlap check: count, smallest pair
+    unsigned long long *snap_dev = nullptr;     // 2 slots x (health word, outlet count)
     StepParams<Real> sp{};
     PopLayout lay{};          // extended lattice of the population arrays
 
@@ -367,10 +379,11 @@ template <class L, class Real, class S> struct EngineT : Engine {
         solids_out = (unsigned long long *)get(sizeof(unsigned long long));
         npairs_dev = (unsigned long long *)get(sizeof(unsigned long long));
         ovl_dev = (unsigned long long *)get(2 * sizeof(unsigned long long));
+        snap_dev = (unsigned long long *)get(4 * sizeof(unsigned long long));
         void *must[] = {f[0], f[1], cl_local[0], cl_local[1], cl_base[0], cl_base[1], fld.rho,
                         fld.node4, key, counts, slot, idslot, tile_total, ticket,
                         best, wall, tab_branch, inlet_dev, health_dev,
-                        red_partials, red_ticket, solids_out, npairs_dev, ovl_dev, part[0].id, part[1].id,
+                        red_partials, red_ticket, solids_out, npairs_dev, ovl_dev, snap_dev, part[0].id, part[1].id,
                         part[0].cell, part[1].cell};
         for (void *p : must)
             if (!p) return fail(LBDPS_ERR_OOM, "device allocation failed");
@@ -909,6 +922,28 @@ template <class L, class Real, class S> struct EngineT : Engine {
         return LBDPS_OK;
     }
 
+    int enqueue_stats_snap(double *dst, cudaStream_t st, int slot) override
+    {
+        const int cur = H->parity;
+        double *dev = nullptr;
+        CU(cudaHostGetDevicePointer((void **)&dev, dst, 0));
+        const unsigned long long *sn = snap_dev + 2 * slot;
+        // no node diagnostics: those arrays are rewritten by the step that
+        // runs beside this reduction
+        launch_reduce_all<L, Real, S>(lay, H->ncell, f[cur], part[cur], H->k.mp, H->np, cells(cur),
+                                      sp.tab.eps_g, H->ntab, nullptr, red_partials, red_ticket,
+                                      reinterpret_cast<const unsigned *>(sn), sn + 1, dev, st);
+        CHECK_LAUNCH();
+        return LBDPS_OK;
+    }
+
+    int enqueue_snapshot(int slot) override
+    {
+        launch_snapshot(health_dev, solids_out, snap_dev + 2 * slot, H->stream);
+        CHECK_LAUNCH();
+        return LBDPS_OK;
+    }
+
     int stats(lbdps_stats_t *out) override
     {
         int rc = enqueue_stats(H->stats_host);
@@ -1101,6 +1136,25 @@ int capture_steps(lbdps *h, int nsteps, cudaGraphExec_t *out)
     return LBDPS_OK;
 }
 
+// one step from parity h->parity followed by the snapshot into slot parity
+int capture_monitored_step(lbdps *h, cudaGraphExec_t *out)
+{
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = h->eng->enqueue_step(h->parity, nullptr);
+    if (rc == LBDPS_OK) rc = h->eng->enqueue_snapshot(h->parity);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(LBDPS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(LBDPS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return LBDPS_OK;
+}
+
 int check_health(lbdps *h)
 {
     int hw = 0;
@@ -1176,6 +1230,58 @@ void decode_stats(lbdps *h, const double *v, bool bed, int64_t steps, lbdps_stat
 // once per kMonSteps steps.
 constexpr int kMonSteps = 1024;
 
+// The reduction of the state after step s reads f, the particles and the
+// cell list of that state, which step s + 1 only reads (it writes the other
+// buffers); step s + 2 overwrites them.  So the reduction runs on its own
+// stream beside step s + 1, and step s + 2 waits for it.  The health word and
+// the outlet count, which step s + 1 updates, come from a snapshot taken at
+// the end of step s.
+int run_monitored_overlapped(lbdps *h, int64_t nsteps, lbdps_stats_t *out)
+{
+    if (!h->stats_stream) {
+        CU(cudaStreamCreateWithFlags(&h->stats_stream, cudaStreamNonBlocking));
+        for (int p = 0; p < 2; ++p) {
+            CU(cudaEventCreateWithFlags(&h->ev_step[p], cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&h->ev_red[p], cudaEventDisableTiming));
+        }
+    }
+    for (int64_t s = 0; s < nsteps;) {
+        const int k = (int)std::min<int64_t>(kMonSteps, nsteps - s);
+        bool pending[2] = {false, false};
+        for (int t = 0; t < k; ++t) {
+            const int p = h->parity;
+            if (!h->mon_graph[p]) {
+                int rc = capture_monitored_step(h, &h->mon_graph[p]);
+                if (rc) return rc;
+            }
+            if (pending[p]) CU(cudaStreamWaitEvent(h->stream, h->ev_red[p], 0));
+            CU(cudaGraphLaunch(h->mon_graph[p], h->stream));
+            h->parity ^= 1;
+            h->steps++;
+            CU(cudaEventRecord(h->ev_step[p], h->stream));
+            CU(cudaStreamWaitEvent(h->stats_stream, h->ev_step[p], 0));
+            int rc = h->eng->enqueue_stats_snap(h->mon_host + (size_t)t * kStatOut, h->stats_stream, p);
+            if (rc) return rc;
+            CU(cudaEventRecord(h->ev_red[p], h->stats_stream));
+            pending[p] = true;
+        }
+        CU(cudaStreamSynchronize(h->stats_stream));
+        CU(cudaStreamSynchronize(h->stream));
+        for (int t = 0; t < k; ++t)
+            decode_stats(h, h->mon_host + (size_t)t * kStatOut, false, h->steps - k + 1 + t, out + s + t);
+        s += k;
+        // the health word of the last record, as lbdps_step checks it
+        if (h->prm.check_every > 0) {
+            const int hw = out[s - 1].health;
+            if (hw & HEALTH_DIVERGED)
+                return fail(LBDPS_ERR_DIVERGED, "gas state diverged by step %lld", (long long)h->steps);
+            if (hw & HEALTH_DOMAIN)
+                return fail(LBDPS_ERR_DOMAIN, "a particle left the domain by step %lld", (long long)h->steps);
+        }
+    }
+    return LBDPS_OK;
+}
+
 int run_monitored(lbdps *h, int64_t nsteps, lbdps_stats_t *out)
 {
     if (!h->mon_host) {
@@ -1186,6 +1292,9 @@ int run_monitored(lbdps *h, int64_t nsteps, lbdps_stats_t *out)
             return fail(LBDPS_ERR_OOM, "pinned host allocation failed");
         }
     }
+    // node diagnostics are rewritten by every step: with them, each
+    // reduction runs before the next step on the handle's stream
+    if (h->prm.use_graph && !h->prm.diagnostics) return run_monitored_overlapped(h, nsteps, out);
     for (int64_t s = 0; s < nsteps;) {
         const int k = (int)std::min<int64_t>(kMonSteps, nsteps - s);
         for (int t = 0; t < k; ++t) {
@@ -1206,6 +1315,10 @@ int run_monitored(lbdps *h, int64_t nsteps, lbdps_stats_t *out)
 void free_graphs(lbdps *h)
 {
     for (int p = 0; p < 2; ++p) {
+        if (h->mon_graph[p]) {
+            cudaGraphExecDestroy(h->mon_graph[p]);
+            h->mon_graph[p] = nullptr;
+        }
         if (h->graph[p]) {
             cudaGraphExecDestroy(h->graph[p]);
             h->graph[p] = nullptr;
@@ -1467,7 +1580,13 @@ void lbdps_destroy(lbdps_t *h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->stats_stream) cudaStreamSynchronize(h->stats_stream);
     free_graphs(h);
+    if (h->stats_stream) cudaStreamDestroy(h->stats_stream);
+    for (int p = 0; p < 2; ++p) {
+        if (h->ev_step[p]) cudaEventDestroy(h->ev_step[p]);
+        if (h->ev_red[p]) cudaEventDestroy(h->ev_red[p]);
+    }
     h->eng.reset();
     h->mem.release_all();
     if (h->health_host) cudaFreeHost(h->health_host);

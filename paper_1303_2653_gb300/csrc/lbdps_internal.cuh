@@ -357,13 +357,17 @@ void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int 
 // kStatMaxBlocks blocks, each writing kStatValues partials; out holds
 // kStatValues values plus the health word and the outlet count.
 constexpr int kStatValues = 11;
-constexpr int kStatMaxBlocks = 304;
+constexpr int kStatMaxBlocks = 152;
 constexpr int kStatPartials = kStatValues * kStatMaxBlocks;
 constexpr int kStatOut = kStatValues + 2;
 
 // All bed statistics in one launch (values listed in stats_kernels.cu); bed
 // = the diagnostic fields or null; ticket must be zero on entry and is zero
 // again on exit.
+// copies the health word and the outlet count to out[0], out[1]
+void launch_snapshot(const unsigned *health, const unsigned long long *solids_out,
+                     unsigned long long *out, cudaStream_t st);
+
 template <class L, class Real, class S>
 void launch_reduce_all(const PopLayout &lay, int ncell, const S *f, Particles<Real> parts, double mp,
                        int np, CellList cells, const Real *eps_tab, int ntab,

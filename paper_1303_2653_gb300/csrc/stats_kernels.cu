@@ -199,6 +199,23 @@ void launch_reduce_all(const PopLayout &lay, int ncell, const S *f, Particles<Re
             health, solids_out, out);
 }
 
+// The health word and the outlet count at the end of a step, for a
+// reduction that runs beside the next step on another stream.
+__global__ void k_snapshot(const unsigned *health, const unsigned long long *solids_out,
+                           unsigned long long *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        out[0] = *health;
+        out[1] = *solids_out;
+    }
+}
+
+void launch_snapshot(const unsigned *health, const unsigned long long *solids_out,
+                     unsigned long long *out, cudaStream_t st)
+{
+    k_snapshot<<<1, 32, 0, st>>>(health, solids_out, out);
+}
+
 #define LBDPS_INST_RED(L, R, S)                                                                    \
     template void launch_reduce_all<L, R, S>(const PopLayout &, int, const S *, Particles<R>,       \
                                              double, int, CellList, const R *, int,                \

@@ -395,11 +395,41 @@ def test_monitored_steps_equal_step_and_stats():
     b.close()
 
 
+@pytest.mark.parametrize("name", ["riser2d", "cfb"])
+def test_overlapped_monitored_steps_equal_step_and_stats(name):
+    # without node diagnostics each step's reduction runs beside the next
+    # step on a second stream, with the health word and outlet count taken
+    # from a snapshot at the end of its step: the records equal lbdps_stats
+    # taken after each step of a bed stepped one at a time
+    L = _lb()
+    if name == "riser2d":
+        w = W.scaled_riser2d(nx=32, ny=64, seed=44)
+    else:   # particles leave through the outlet every few steps
+        w = _cfb_column(W.STORE_F32, n=200)
+    a = L.Bed(w)
+    b = L.Bed(w)
+    recs = a.step_monitored(60)
+    assert [r["steps"] for r in recs] == list(range(1, 61))
+    for k in range(60):
+        b.step(1)
+        s = b.stats()
+        for key in ("mass", "mean_eps_g", "steps", "health", "solids_out"):
+            assert recs[k][key] == s[key], (k, key)
+        np.testing.assert_array_equal(recs[k]["gas_momentum"], s["gas_momentum"])
+        np.testing.assert_array_equal(recs[k]["particle_momentum"], s["particle_momentum"])
+    if name == "cfb":
+        assert recs[-1]["solids_out"] > recs[0]["solids_out"]
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    assert a.check_guards() == 0
+    a.close()
+    b.close()
+
+
 def test_no_kernel_writes_past_its_buffers():
     # every device block carries a guard zone; run each entry point that
     # launches kernels on beds large enough for the multi-block paths (the
-    # statistics reduction runs its maximum of 304 blocks of 512 threads
-    # above 155,648 cells or particles) and check that no guard was touched
+    # statistics reduction runs its maximum of 152 blocks of 512 threads
+    # above 77,824 cells or particles) and check that no guard was touched
     L = _lb()
     for w, st in [(W.riser2d(nx=256, ny=1536, n_particles=100000), W.STORE_F32),
                   (W.scaled_riser3d(nx=48, ny=48, nz=128), W.STORE_F16),
