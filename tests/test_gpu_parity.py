@@ -520,3 +520,23 @@ def test_recirculation_rejected_without_inlet_below_outlet_above():
     with pytest.raises(L.LbdpsError) as ei:
         L.Bed(w.with_(bc=(W.WALL, W.WALL, W.OUTLET, W.INLET, W.PERIODIC, W.PERIODIC)))
     assert ei.value.code == L.ERR_INVALID
+
+
+@pytest.mark.parametrize("monitored", [False, True])
+def test_divergence_is_reported(monitored):
+    # a gas body force that drives |u| past the lattice limit within a few
+    # hundred steps: the health word flags it and a step call with
+    # check_every returns LBDPS_ERR_DIVERGED (no GPU fault, the state is
+    # only numerically unusable)
+    L = _lb()
+    w = W.channel2d(nx=16, ny=8, body_accel=0.0).with_(bc=(W.PERIODIC,) * 6)
+    w = w.with_(body_accel=(0.0, 2e-3 * w.h / w.dt ** 2, 0.0))
+    bed = L.Bed(w, check_every=32)
+    with pytest.raises(L.LbdpsError) as ei:
+        if monitored:
+            bed.step_monitored(2000)
+        else:
+            bed.step(2000)
+    assert ei.value.code == L.ERR_DIVERGED
+    assert bed.stats()["health"] & 1
+    bed.close()
