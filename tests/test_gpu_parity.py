@@ -540,3 +540,38 @@ def test_divergence_is_reported(monitored):
     assert ei.value.code == L.ERR_DIVERGED
     assert bed.stats()["health"] & 1
     bed.close()
+
+
+@pytest.mark.parametrize("storage", [W.STORE_F64, W.STORE_F32])
+def test_one_step_parity_crowded_cells_and_particles_on_faces(storage):
+    # cells holding up to 16 particles (the count tables near their top end)
+    # beside empty ones, and particles exactly on cell faces (zero in-cell
+    # offsets, nodes clamped at the walls): one step against the oracle
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from test_oracle_pins import _counted_bed
+    rng = np.random.default_rng(12)
+    counts = rng.integers(0, 17, size=(20, 12))
+    counts[rng.random(counts.shape) < 0.3] = 0
+    counts[5, :] = 0
+    w = _counted_bed(counts, storage=storage)
+    P = w.pos / w.h
+    extra = np.array([[3.0, 5.0], [0.5, 5.5], [6.0, 5.0], [11.9, 5.5], [9.0, 5.0]])
+    P = np.concatenate([P, extra])
+    rng2 = np.random.default_rng(3)
+    V = rng2.normal(scale=2e-3, size=P.shape)
+    w = w.with_(pos=P * w.h, vel=V * w.h / w.dt)
+    bed, ob = _pair(w, storage)
+    _compare_step(bed, ob, storage)
+    Pg, vg, Po, vo, fd_g, fd_o, kappa_cell = _particle_compare(bed, ob, storage)
+    tol_d = TOL_DERIVED[storage]
+    vmax = np.abs(vo).max()
+    c0 = np.floor(P).astype(np.int64)
+    kappa = kappa_cell[c0[:, 0] + w.n[0] * c0[:, 1]]
+    amp = np.maximum(1.0, kappa / 100.0)[:, None]
+    good = kappa < 1e3
+    assert good.mean() > 0.9
+    assert np.all(np.abs(vg[good] - vo[good]) <= tol_d * vmax * amp[good])
+    assert bed.check_guards() == 0
+    bed.close()
