@@ -160,7 +160,7 @@ template <> struct DragOccupancy<2, float> { static constexpr int value = LBDPS_
 template <> struct DragOccupancy<3, float> { static constexpr int value = LBDPS_DRAG_BLOCKS_3D_F32; };
 template <int D, class Real> struct DetectOccupancy { static constexpr int value = 2; };
 template <> struct DetectOccupancy<2, float> { static constexpr int value = 6; };
-template <> struct DetectOccupancy<3, float> { static constexpr int value = 3; };
+template <> struct DetectOccupancy<3, float> { static constexpr int value = 5; };
 
 // SOFT: add the soft-sphere contact force of the step (p.fc) in Eq. 16
 template <int D, class Real, bool SOFT>
@@ -381,8 +381,9 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot, int *t
 // for the next launch.
 // ---------------------------------------------------------------------------
 constexpr int kCellScanThreads = 1024;
-constexpr int kCellScanItems = kCellTile / kCellScanThreads;   // 4
-static_assert(kCellScanItems == 4, "one int4 per thread");
+constexpr int kCellScanItems = kCellTile / kCellScanThreads;
+constexpr int kCellScanVec = kCellScanItems / 4;   // int4 loads per thread
+static_assert(kCellScanItems % 4 == 0, "whole int4 per thread");
 
 __global__ void __launch_bounds__(kCellScanThreads)
 k_cell_scan(const int *__restrict__ counts, CellListOut out, int n)
@@ -391,22 +392,37 @@ k_cell_scan(const int *__restrict__ counts, CellListOut out, int n)
     __shared__ int total;
     __shared__ bool last;
     const int base = blockIdx.x * kCellTile + threadIdx.x * kCellScanItems;
-    int4 c4 = make_int4(0, 0, 0, 0);
-    if (base + kCellScanItems <= n) {
-        c4 = __ldg(reinterpret_cast<const int4 *>(counts + base));
-    } else {
-        if (base + 0 < n) c4.x = counts[base + 0];
-        if (base + 1 < n) c4.y = counts[base + 1];
-        if (base + 2 < n) c4.z = counts[base + 2];
+    // all of the thread's loads are issued before any is used
+    int4 c4[kCellScanVec];
+    const bool whole = base + kCellScanItems <= n;
+#pragma unroll
+    for (int v = 0; v < kCellScanVec; ++v) {
+        if (whole) {
+            c4[v] = __ldg(reinterpret_cast<const int4 *>(counts + base) + v);
+        } else {
+            const int e = base + 4 * v;
+            c4[v] = make_int4(e + 0 < n ? counts[e + 0] : 0, e + 1 < n ? counts[e + 1] : 0,
+                              e + 2 < n ? counts[e + 2] : 0, e + 3 < n ? counts[e + 3] : 0);
+        }
     }
-    const int run = block_exclusive_scan(c4.x + c4.y + c4.z + c4.w, warp_tot, &total);
-    const int4 e4 = make_int4(run, run + c4.x, run + c4.x + c4.y, run + c4.x + c4.y + c4.z);
-    if (base + kCellScanItems <= n) {
-        *reinterpret_cast<int4 *>(out.local + base) = e4;
-    } else {
-        if (base + 0 < n) out.local[base + 0] = e4.x;
-        if (base + 1 < n) out.local[base + 1] = e4.y;
-        if (base + 2 < n) out.local[base + 2] = e4.z;
+    int sum = 0;
+#pragma unroll
+    for (int v = 0; v < kCellScanVec; ++v) sum += c4[v].x + c4[v].y + c4[v].z + c4[v].w;
+    int run = block_exclusive_scan(sum, warp_tot, &total);
+#pragma unroll
+    for (int v = 0; v < kCellScanVec; ++v) {
+        const int4 e4 = make_int4(run, run + c4[v].x, run + c4[v].x + c4[v].y,
+                                  run + c4[v].x + c4[v].y + c4[v].z);
+        run += c4[v].x + c4[v].y + c4[v].z + c4[v].w;
+        if (whole) {
+            reinterpret_cast<int4 *>(out.local + base)[v] = e4;
+        } else {
+            const int e = base + 4 * v;
+            if (e + 0 < n) out.local[e + 0] = e4.x;
+            if (e + 1 < n) out.local[e + 1] = e4.y;
+            if (e + 2 < n) out.local[e + 2] = e4.z;
+            if (e + 3 < n) out.local[e + 3] = e4.w;
+        }
     }
     if (threadIdx.x == 0) {
         out.tile_total[blockIdx.x] = total;
