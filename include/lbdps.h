@@ -178,7 +178,12 @@ typedef struct {
     double mean_slip;            /* particle-weighted mean |u_act - v_s| of the last
                                     step (needs diagnostics, else NaN)                */
     int64_t steps;               /* steps taken so far                              */
-    int health;                  /* bitmask: 1 diverged, 2 domain, 4 capacity       */
+    int health;                  /* bitmask: 1 diverged, 2 domain, 4 capacity, 8 packed
+                                    (a statistics reduction saw a cell holding more
+                                    particle centres than can be there without overlaps,
+                                    the close-packing count of the cell grown by d_p:
+                                    hard spheres piled up, §2.2 limits them to low solid
+                                    fractions; reported only, never an error)          */
     int64_t solids_out;          /* particles that left through the outlet since creation
                                     (recirculate = 1; the solids flux of §3.2 is
                                     solids_out m_p / (outlet area x time))            */
@@ -296,7 +301,7 @@ int lbdps_collide_particles(lbdps_t *h, int64_t *pairs, int64_t cap, int64_t *np
 /* Deterministic FP64 reductions of the current state. */
 int lbdps_stats(lbdps_t *h, lbdps_stats_t *out);
 
-/* Health bitmask (1 diverged, 2 domain, 4 capacity) accumulated so far. */
+/* Health bitmask (1 diverged, 2 domain, 4 capacity, 8 packed) accumulated so far. */
 int lbdps_health(lbdps_t *h, int *health);
 
 /* Lattice-unit constants derived at create, in this order: tau, nu, mu,

@@ -295,6 +295,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
     unsigned long long *snap_dev = nullptr;     // 2 slots x (health word, outlet count)
     StepParams<Real> sp{};
     PopLayout lay{};          // extended lattice of the population arrays
+    int packed_limit = 0;     // more particle centres per cell cannot all be apart
 
     explicit EngineT(lbdps *h) : H(h) {}
     size_t pop_slots() const { return (size_t)Q * (size_t)lay.nce; }
@@ -474,6 +475,13 @@ template <class L, class Real, class S> struct EngineT : Engine {
         p.mu_f = (Real)k.mu_f;
         p.gamma_t = (Real)k.gamma_t;
         p.inv_inertia = (Real)(1.0 / k.inertia);
+        {
+            // spheres centred in a cell lie in the cell grown by d: at close
+            // packing that box holds at most this many (lattice units)
+            const double unit = D == 2 ? kPi * k.r * k.r : k.vp;
+            const double cap = D == 2 ? kPi / (2.0 * std::sqrt(3.0)) : kPi / (3.0 * std::sqrt(2.0));
+            packed_limit = (int)std::ceil(cap * std::pow(1.0 + k.d, D) / unit);
+        }
         for (int c = 0; c < 3; ++c) p.spin_out[c] = H->friction && c < NW ? stage.w[c] : nullptr;
     }
 
@@ -917,7 +925,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
         CU(cudaHostGetDevicePointer((void **)&dev, dst, 0));
         launch_reduce_all<L, Real, S>(lay, H->ncell, f[cur], part[cur], H->k.mp, H->np, cells(cur),
                                       sp.tab.eps_g, H->ntab, bed ? &fld : nullptr, red_partials,
-                                      red_ticket, health_dev, solids_out, dev, H->stream);
+                                      red_ticket, health_dev, solids_out, dev, health_dev,
+                                      packed_limit, H->stream);
         CHECK_LAUNCH();
         return LBDPS_OK;
     }
@@ -932,7 +941,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
         // runs beside this reduction
         launch_reduce_all<L, Real, S>(lay, H->ncell, f[cur], part[cur], H->k.mp, H->np, cells(cur),
                                       sp.tab.eps_g, H->ntab, nullptr, red_partials, red_ticket,
-                                      reinterpret_cast<const unsigned *>(sn), sn + 1, dev, st);
+                                      reinterpret_cast<const unsigned *>(sn), sn + 1, dev, health_dev,
+                                      packed_limit, st);
         CHECK_LAUNCH();
         return LBDPS_OK;
     }

@@ -11,7 +11,10 @@ namespace lbdpsk {
 
 enum { BC_WALL = 0, BC_PERIODIC = 1, BC_INLET = 2, BC_OUTLET = 3 };
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
-enum : unsigned { HEALTH_DIVERGED = 1u, HEALTH_DOMAIN = 2u, HEALTH_CAPACITY = 4u };
+// HEALTH_PACKED: a cell held more particle centres than could be there
+// without overlaps (time-driven hard spheres cannot hold a dense bed apart,
+// §2.2); found by the statistics reduction, reported, not an error
+enum : unsigned { HEALTH_DIVERGED = 1u, HEALTH_DOMAIN = 2u, HEALTH_CAPACITY = 4u, HEALTH_PACKED = 8u };
 
 // ---------------------------------------------------------------------------
 // Velocity sets.  D2Q9 in the paper's order (Eq. 4): rest, the four axis
@@ -373,7 +376,7 @@ void launch_reduce_all(const PopLayout &lay, int ncell, const S *f, Particles<Re
                        int np, CellList cells, const Real *eps_tab, int ntab,
                        const Fields<Real> *bed, double *partials, unsigned *ticket,
                        const unsigned *health, const unsigned long long *solids_out, double *out,
-                       cudaStream_t st);
+                       unsigned *health_live, int packed_limit, cudaStream_t st);
 
 int reduce_block_count(int n);
 

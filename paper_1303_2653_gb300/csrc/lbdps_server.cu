@@ -232,7 +232,8 @@ int lbdps_server_poll(lbdps_server_t *s, double wait_s, lbdps_done_t *out, int c
             d.t_admit = a.t_admit - s->t0;
             d.t_done = now_s() - s->t0;
             d.status = lbdps_stats(a.h, &d.stats);
-            if (d.status == LBDPS_OK && d.stats.health) d.status = LBDPS_ERR_DIVERGED;
+            // a packed cell (health bit 8) is reported in the record, not a failure
+            if (d.status == LBDPS_OK && (d.stats.health & 3)) d.status = LBDPS_ERR_DIVERGED;
             s->done.push_back(d);
             cudaEventDestroy(a.last);
             cudaEventDestroy(a.tick);

@@ -54,10 +54,12 @@ __global__ void __launch_bounds__(kRedThreads)
 k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> parts, double mp,
              int np, CellList cells, const Real *__restrict__ eps_tab, int ntab, Fields<Real> fld,
              double *partials, unsigned *ticket, const unsigned *health,
-             const unsigned long long *solids_out, double *out)
+             const unsigned long long *solids_out, double *out, unsigned *health_live,
+             int packed_limit)
 {
     constexpr int D = L::D, Q = L::Q;
     Acc<Real> acc[kStatValues];
+    int packed = 0;   // a cell held more centres than can be there without overlaps
     const int stride = gridDim.x * blockDim.x;
     // cells in batches of kB per thread (x, x + stride, ...): the loads of
     // a batch are all issued before any is used, so that each thread keeps
@@ -81,7 +83,10 @@ k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> 
         }
         Real ev[kB];
 #pragma unroll
-        for (int b = 0; b < kB; ++b) ev[b] = eps_tab[nn[b] < ntab ? nn[b] : ntab - 1];
+        for (int b = 0; b < kB; ++b) {
+            ev[b] = eps_tab[nn[b] < ntab ? nn[b] : ntab - 1];
+            if (x0 + b * stride < ncell && nn[b] > packed_limit) packed = 1;
+        }
 #pragma unroll
         for (int b = 0; b < kB; ++b) {
             const int x = x0 + b * stride;
@@ -145,7 +150,7 @@ k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> 
         const Real t = warp_sum<Real>(acc[k].value());
         if (lane == 0) sh[warp][k] = (double)t;
     }
-    __syncthreads();
+    if (__syncthreads_or(packed) && threadIdx.x == 0) atomicOr(health_live, HEALTH_PACKED);
     if (threadIdx.x < kStatValues) {
         double t = 0.0;
         for (int w = 0; w < kWarps; ++w) t += sh[w][threadIdx.x];
@@ -173,7 +178,7 @@ k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> 
         // the health word and the outlet count travel with the values, so
         // that the host reads everything with one copy
         unsigned long long *raw = reinterpret_cast<unsigned long long *>(out);
-        raw[kStatValues] = *health;
+        raw[kStatValues] = *health | (__ldcg(health_live) & HEALTH_PACKED);
         raw[kStatValues + 1] = *solids_out;
         *ticket = 0u;
     }
@@ -184,7 +189,7 @@ void launch_reduce_all(const PopLayout &lay, int ncell, const S *f, Particles<Re
                        int np, CellList cells, const Real *eps_tab, int ntab,
                        const Fields<Real> *bed, double *partials, unsigned *ticket,
                        const unsigned *health, const unsigned long long *solids_out, double *out,
-                       cudaStream_t st)
+                       unsigned *health_live, int packed_limit, cudaStream_t st)
 {
     const int n = ncell > np ? ncell : np;
     int nb = (n + kRedThreads - 1) / kRedThreads;
@@ -192,11 +197,11 @@ void launch_reduce_all(const PopLayout &lay, int ncell, const S *f, Particles<Re
     if (bed)
         k_reduce_all<L, Real, S, true><<<nb, kRedThreads, 0, st>>>(
             lay, ncell, f, parts, mp, np, cells, eps_tab, ntab, *bed, partials, ticket, health,
-            solids_out, out);
+            solids_out, out, health_live, packed_limit);
     else
         k_reduce_all<L, Real, S, false><<<nb, kRedThreads, 0, st>>>(
             lay, ncell, f, parts, mp, np, cells, eps_tab, ntab, Fields<Real>{}, partials, ticket,
-            health, solids_out, out);
+            health, solids_out, out, health_live, packed_limit);
 }
 
 // The health word and the outlet count at the end of a step, for a
@@ -221,7 +226,7 @@ void launch_snapshot(const unsigned *health, const unsigned long long *solids_ou
                                              double, int, CellList, const R *, int,                \
                                              const Fields<R> *, double *, unsigned *,               \
                                              const unsigned *, const unsigned long long *,          \
-                                             double *, cudaStream_t);
+                                             double *, unsigned *, int, cudaStream_t);
 LBDPS_INST_RED(D2Q9, double, double)
 LBDPS_INST_RED(D2Q9, float, float)
 LBDPS_INST_RED(D2Q9, float, __half)

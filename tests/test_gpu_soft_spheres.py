@@ -447,3 +447,30 @@ def test_soft_long_run_statistics(mu):
     assert abs(Pg[:, 1].mean() - Po[:, 1].mean()) < 0.05
     assert sg["mass"] == pytest.approx(so["mass"], rel=1e-6)
     bed.close()
+
+
+def test_packed_cell_is_reported_not_failed():
+    # more particle centres in a cell than can be there without overlaps
+    # (the close-packing count of the cell grown by one diameter; possible
+    # with overlapping soft spheres, and what piled-up hard spheres reach in
+    # a settled dense bed) sets health bit 8; stepping with check_every
+    # carries on, since the state is valid
+    L = _lb()
+    w = W.packed_bed(dim=2, n=(12, 12), n_particles=60, storage=W.STORE_F32)
+    rng = np.random.default_rng(8)
+    P = w.pos.copy()
+    P[:50] = (np.array([5.0, 5.0]) + rng.uniform(0.05, 0.95, size=(50, 2))) * w.h
+    w = w.with_(pos=P)
+    dl = w.d_p / w.h
+    cap = math.pi / (2 * math.sqrt(3)) * (1 + dl) ** 2 / (math.pi * (0.5 * dl) ** 2)
+    assert 50 > math.ceil(cap)
+    bed = L.Bed(w, check_every=4)
+    bed.step(8)
+    assert bed.stats()["health"] & 8
+    assert not bed.stats()["health"] & 3
+    bed.close()
+    # a bed within close packing does not set it
+    ok = L.Bed(W.packed_bed(dim=2, n=(24, 48), storage=W.STORE_F32), check_every=4)
+    ok.step(8)
+    assert ok.stats()["health"] == 0
+    ok.close()
