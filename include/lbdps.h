@@ -208,10 +208,14 @@ int lbdps_step(lbdps_t *h, int64_t nsteps);
 
 /* Advance nsteps coupled steps and take the FP64 statistics of lbdps_stats
  * after every one of them, without a host wait between steps: each step's
- * reductions are copied to pinned host memory on the handle's stream and the
- * host waits once per 1,024 steps.  out receives nsteps records (host array,
- * caller-owned), record k describing the state after step k + 1 of the call.
- * Errors as lbdps_step; LBDPS_ERR_OOM if the pinned buffer cannot be had. */
+ * reduction writes its results straight into mapped pinned host memory and
+ * the host waits once per 1,024 steps.  Without node diagnostics (and with
+ * graphs) the reduction of step s runs on a second stream beside step s + 1,
+ * reading the health word and outlet count from a snapshot taken at the end
+ * of step s; mean_slip is then NaN.  out receives nsteps records (host
+ * array, caller-owned), record k describing the state after step k + 1 of the
+ * call.  With check_every > 0, LBDPS_ERR_DIVERGED / _DOMAIN as lbdps_step;
+ * LBDPS_ERR_OOM if the pinned buffer cannot be had. */
 int lbdps_step_monitored(lbdps_t *h, int64_t nsteps, lbdps_stats_t *out);
 
 /* Advance nsteps steps launching each kernel separately with CUDA events

@@ -1231,3 +1231,23 @@ def test_sequential_rule_keeps_momentum(dim, n, N):
     v1 = bed.particles()[1]
     assert np.abs(v1 - v).max() > 1e-3
     np.testing.assert_allclose(v1.sum(axis=0), v.sum(axis=0), rtol=0, atol=1e-12)
+
+
+def test_sequential_rule_leaves_separating_contacts_alone():
+    # R27 resolves a contact only if it approaches when its turn comes: a
+    # touching pair moving apart keeps its velocities, and so does a pair
+    # that an earlier collision in the order has turned around
+    base = _bed(n=(8, 8), d_p=0.5, e=1.0, pos=np.zeros((0, 2)), vel=np.zeros((0, 2)))
+    seq = O.OracleBed(types.SimpleNamespace(**{**vars(base), "collision_rule": 1}))
+    P = np.array([[2.0, 3.5], [2.45, 3.5]])
+    V = np.array([[-0.01, 0.0], [0.01, 0.0]])
+    seq.set_particles(P, V)
+    seq.collide_particles()
+    np.testing.assert_array_equal(seq.particles()[1], V)
+    # 0 and 1 approach, 1 and 2 touch while 2 runs ahead of 1 after the
+    # first collision: (1, 2) is skipped
+    P = np.array([[2.0, 3.5], [2.45, 3.5], [2.9, 3.5]])
+    V = np.array([[0.01, 0.0], [0.0, 0.0], [0.02, 0.0]])
+    seq.set_particles(P, V)
+    seq.collide_particles()
+    np.testing.assert_allclose(seq.particles()[1], [[0, 0], [0.01, 0], [0.02, 0]], atol=1e-17)
