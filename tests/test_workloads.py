@@ -1,5 +1,6 @@
 """Seeded input generator: splitmix64 stream, RSA placement, Maxwellian."""
 import numpy as np
+import pytest
 
 from paper_1303_2653_gb300 import workloads as W
 
@@ -37,3 +38,24 @@ def test_riser_workload_shape():
     assert w.n == (32, 64) and w.pos.shape == (w.n_particles, 2)
     area = w.n_particles * np.pi * (0.5 * w.d_p) ** 2 / (32 * 64 * w.h * w.h)
     assert abs(area - 0.05) < 1e-12
+
+
+def test_soft_sphere_workload_helpers():
+    import math
+    from scipy.spatial.distance import pdist
+    w = W.packed_bed(dim=2, n=(16, 24), gap=0.9, contact_steps=20.0)
+    # centres at least gap d_p apart, inside the lower half, closed box
+    assert pdist(w.pos).min() >= 0.9 * w.d_p * (1 - 1e-12)
+    assert w.pos[:, 1].max() <= 12 * w.h and w.pos.min() >= 0.5 * w.d_p
+    assert w.bc[:4] == (W.WALL,) * 4 and w.collision_model == 1
+    # k_n makes an undamped pair contact (half a period, reduced mass m/2)
+    # last the asked number of steps
+    m_p = w.rho_s * math.pi * w.d_p ** 3 / 6.0
+    t_c = math.pi * math.sqrt(0.5 * m_p / w.dem_kn)
+    assert t_c / w.dt == pytest.approx(20.0, rel=1e-12)
+    s = W.soft_spheres(W.riser2d(nx=32, ny=64, n_particles=500), contact_steps=8.0, e=0.5)
+    assert s.collision_model == 1 and s.e == 0.5 and s.dem_kn == W.dem_stiffness(s, 8.0)
+    f = W.with_friction(w, mu=0.3, gamma_frac=0.1)
+    assert f.dem_mu == 0.3 and f.dem_gamma_t == pytest.approx(0.1 * m_p / w.dt, rel=1e-14)
+    w3 = W.packed_bed(dim=3, n=(6, 6, 8), n_particles=2000)
+    assert w3.pos.shape == (2000, 3) and pdist(w3.pos).min() >= 0.9 * w3.d_p * (1 - 1e-12)
