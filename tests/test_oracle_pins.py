@@ -1251,3 +1251,72 @@ def test_sequential_rule_leaves_separating_contacts_alone():
     seq.set_particles(P, V)
     seq.collide_particles()
     np.testing.assert_allclose(seq.particles()[1], [[0, 0], [0.01, 0], [0.02, 0]], atol=1e-17)
+
+
+def _friction_bruteforce_3d(P, v, w, n, per, d, k):
+    """All pairs and faces with friction in 3D (spins with three components)."""
+    N = P.shape[0]
+    r = 0.5 * d
+    F = np.zeros((N, 3))
+    T = np.zeros((N, 3))
+
+    def add(i, nrm, l, fn, vc):
+        F[i] += fn * nrm
+        vt = vc - (vc @ nrm) * nrm
+        st = math.sqrt(vt @ vt)
+        if fn > 0 and st > 0:
+            ft = -min(k["gamma_t"] * st, k["mu_f"] * fn) * vt / st
+            F[i] += ft
+            T[i] += np.cross(-l * nrm, ft)
+
+    for i in range(N):
+        for j in range(N):
+            if i == j:
+                continue
+            dx = P[i] - P[j]
+            for a in range(3):
+                if per[a]:
+                    dx[a] -= n[a] * round(dx[a] / n[a])
+            dist = math.sqrt(dx @ dx)
+            if dist >= d:
+                continue
+            nrm = dx / dist
+            fn = max(k["kn"] * (d - dist) - k["eta"] * ((v[i] - v[j]) @ nrm), 0.0)
+            l = 0.5 * dist
+            add(i, nrm, l, fn, (v[i] - v[j]) - l * np.cross(w[i] + w[j], nrm))
+        for a in range(3):
+            if per[a]:
+                continue
+            for side in (0, 1):
+                l = P[i, a] if side == 0 else n[a] - P[i, a]
+                if l >= r:
+                    continue
+                nrm = np.zeros(3)
+                nrm[a] = 1.0 if side == 0 else -1.0
+                fn = max(k["kn"] * (r - l) - k["eta_w"] * (v[i] @ nrm), 0.0)
+                add(i, nrm, l, fn, v[i] - l * np.cross(w[i], nrm))
+    return F, T
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_friction_forces_and_torques_match_all_pairs_3d(walls):
+    n = (4, 5, 4)
+    rng = np.random.default_rng(31)
+    d = 0.7
+    box = np.array(n, dtype=float)
+    pos = W.rsa(3, box, [0.36] * 3, box - 0.36, (0, 0, 0) if walls else (1, 1, 1), 0.8 * d, 90, 12)
+    vel = rng.normal(scale=2e-3, size=pos.shape)
+    bc = (W.WALL,) * 6 if walls else (W.PERIODIC,) * 6
+    w, mp, kn = _soft(dim=3, n=n, d_p=d, rho_s=50.0, e=0.6, contact_steps=12.0, bc=bc, pos=pos,
+                      vel=vel, dem_mu=0.3, dem_gamma_t=2.0)
+    bed = O.OracleBed(w)
+    spin0 = rng.normal(scale=5e-3, size=(len(pos), 3))
+    bed.set_spin(spin0)
+    P0, v0 = bed.particles()
+    k = bed.constants()
+    bed.step(1)
+    F, T = _friction_bruteforce_3d(P0, v0, spin0, n, [not walls] * 3, d, k)
+    np.testing.assert_allclose(bed.particle_diag(O.P_FC), F, rtol=0, atol=1e-12 * np.abs(F).max())
+    np.testing.assert_allclose(bed.spin() - spin0, T / k["inertia"], rtol=0,
+                               atol=1e-12 * np.abs(T / k["inertia"]).max())
+    assert (np.abs(T).sum(axis=1) > 0).mean() > 0.3
