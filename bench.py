@@ -13,6 +13,15 @@ second / 1e6), whole job over all ranks.  Multi-GPU runs are independent
 replicas of the bed (weak scaling, no data-path collective).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Other modes, one JSON line each: --workload riser3d | bubbling2d (the D3Q19
+riser, the small FP64 bubbling bed), --storage f16 | bf16 | f64, --serving
+(continuous batching of a Poisson stream of beds against one-by-one FP32),
+--precision (per-field error of each storage format against the FP64
+oracle), --cfb (solids flux of the circulating-bed riser), --bubble (bubble
+diameters of the Table 1 bed with a jet pulse), --dem [--dem-mu M] (the dense
+soft-sphere bed, with friction for M > 0), --profile-steps N (build a bed and
+run N steps, for ncu).
 """
 import argparse
 import hashlib
