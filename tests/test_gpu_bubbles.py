@@ -19,7 +19,7 @@ sys.path.insert(0, HERE)
 
 from oracle import oracle as O                      # noqa: E402
 from paper_1303_2653_gb300 import workloads as W    # noqa: E402
-from test_oracle_pins import _counted_bed           # noqa: E402
+from test_oracle_pins import _counted_bed, _counted_bed3d  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -51,6 +51,22 @@ def test_bubbles_match_oracle(seed):
     ob = O.OracleBed(w)
     for thr, v in [(0.85, L.VOIDAGE_2D), (0.6, L.VOIDAGE_2D), (0.97, L.VOIDAGE_G)]:
         assert bed.bubbles(thr, v) == ob.bubbles(thr, v)
+    bed.close()
+
+
+@pytest.mark.parametrize("seed,periodic_x", [(4, False), (6, True), (7, True)])
+def test_bubbles_3d_match_oracle(seed, periodic_x):
+    # 3D: face neighbours along x, y and z, z vertical, the x face wrapping
+    L = _lb()
+    rng = np.random.default_rng(seed)
+    counts = rng.integers(0, 28, size=(12, 10, 11))
+    counts[rng.random(counts.shape) < 0.1] = 0
+    w = _counted_bed3d(counts, periodic_x, storage=W.STORE_F32)
+    bed = L.Bed(w)
+    ob = O.OracleBed(w)
+    for thr in (0.99, 0.985, 0.975, 0.9):
+        got = bed.bubbles(thr, L.VOIDAGE_G)
+        assert got == ob.bubbles(thr, L.VOIDAGE_G)
     bed.close()
 
 

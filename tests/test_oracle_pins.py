@@ -828,12 +828,12 @@ def test_bubbles_match_scipy_labelling(seed):
     assert bed.bubbles(0.97, 1) == _scipy_bubbles(epsg > 0.97)
 
 
-def _counted_bed3d(counts, periodic_x=False):
+def _counted_bed3d(counts, periodic_x=False, storage=W.STORE_F64):
     """A closed 3D box of Table 1 particles whose cell (x, y, z) holds
     counts[z, y, x] centres on a 3 x 3 x 3 sub-grid of the cell (spacing h/3
     > d_p, so no two overlap); x optionally periodic."""
     nz, ny, nx = counts.shape
-    w = W.packed_bed(dim=3, n=(nx, ny, nz), n_particles=1)
+    w = W.packed_bed(dim=3, n=(nx, ny, nz), n_particles=1, storage=storage)
     pts = []
     for z in range(nz):
         for y in range(ny):
