@@ -43,8 +43,9 @@
  *   R8  Eq. 23 literally: gamma(eps_s, tau_t) in the relaxation term and
  *       gamma(eps_s, tau) in the solid term.  Body force by Guo's source term.
  *   R9  Walls: half-way bounce-back (moving-wall variant for closed-form
- *       tests).  Inlet: incoming populations at feq(1, u_in).  Outlet:
- *       incoming populations at feq(1, u of the receiving cell).
+ *       tests).  Inlet: incoming populations at feq(1, u_in), u_in that of
+ *       the receiving cell's own column of the inlet face.  Outlet: incoming
+ *       populations at feq(1, u of the receiving cell).
  *   R10 Node fields (rho, u, beta) are the collision-time values of the same
  *       step; superficial -> actual velocity divides by eps_2d (flag).
  *   R11 Bilinear (trilinear) interpolation from cell-centre nodes, clamped at

@@ -264,6 +264,39 @@ def test_uniform_inflow_outflow_fixed_point(dim):
     np.testing.assert_allclose(bed.field(O.F_RHO), 1.0, atol=1e-10)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_inlet_populations_follow_the_profile(dim):
+    # A velocity inlet fills each population that enters a bottom cell from
+    # below with the equilibrium at density 1 and that cell's inlet velocity
+    # (reading R9); directions whose source crosses a side wall bounce back.
+    if dim == 2:
+        n, bc = (7, 6), (W.WALL, W.WALL, W.INLET, W.OUTLET, W.PERIODIC, W.PERIODIC)
+        c, w = _c2()
+    else:
+        n, bc = (5, 4, 6), (W.WALL, W.WALL, W.WALL, W.WALL, W.INLET, W.OUTLET)
+        c, w = _c3()
+    nface = int(np.prod(n[:-1]))
+    rng = np.random.default_rng(11)
+    inlet = rng.uniform(-2e-3, 2e-3, (nface, dim))
+    inlet[:, -1] = rng.uniform(1e-3, 4e-3, nface)
+    pos = np.zeros((0, dim))
+    bed = O.OracleBed(_bed(dim=dim, n=n, bc=bc, mu_g=0.2, inlet_u=inlet, pos=pos, vel=pos))
+    bed.step(1)
+    f = bed.populations()
+    checked = 0
+    for j in range(nface):
+        q = np.array([j % n[0], j // n[0]])[: dim - 1]
+        for i in range(len(w)):
+            src = q - c[i][: dim - 1]
+            if c[i][-1] != 1 or np.any(src < 0) or np.any(src >= np.array(n[: dim - 1])):
+                continue
+            cu = c[i] @ inlet[j]
+            want = w[i] * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * inlet[j] @ inlet[j])
+            assert f[i, j] == pytest.approx(want, rel=1e-14), (j, i)
+            checked += 1
+    assert checked > 2 * nface
+
+
 # -------------------------------------------------------- coupled-step invariants
 
 def _small_riser(dim=2, cs=0.0, **kw):
@@ -552,9 +585,32 @@ def test_mean_voidage_of_current_positions():
     assert np.any(bed.field(O.F_NTOT) != n)
 
 
-def test_les_reduces_to_bgk_and_solves_quadratic():
-    w0 = _small_riser(2, 0.0)
-    w1 = _small_riser(2, 0.2)
+def _c2():
+    c = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]])
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    return c, w
+
+
+def _c3():
+    """D3Q19 in storage order: rest, the six axis directions (+x, -x, +y, -y,
+    +z, -z), then the twelve edge diagonals in opposite pairs (xy, xz, yz)."""
+    c = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+                  [1, 1, 0], [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1], [-1, 0, -1],
+                  [1, 0, -1], [-1, 0, 1], [0, 1, 1], [0, -1, -1], [0, 1, -1], [0, -1, 1]])
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    return c, w
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_les_reduces_to_bgk_and_solves_quadratic(dim):
+    if dim == 2:
+        w0, w1 = _small_riser(2, 0.0), _small_riser(2, 0.2)
+        c, wts = _c2()
+    else:
+        # three different sides, and Q_ab summed over all three axes
+        mk = lambda cs: W.scaled_riser3d(nx=8, ny=6, nz=12, storage=W.STORE_F64, cs_smag=cs)
+        w0, w1 = mk(0.0), mk(0.2)
+        c, wts = _c3()
     b0, b1 = O.OracleBed(w0), O.OracleBed(w1)
     b0.step(1)
     np.testing.assert_array_equal(b0.field(O.F_TAU_T), b0.constants()["tau"])
@@ -565,9 +621,7 @@ def test_les_reduces_to_bgk_and_solves_quadratic():
     tau = b1.constants()["tau"]
     tt = b1.field(O.F_TAU_T)
     rho = b1.field(O.F_RHO)
-    u = b1.field(O.F_U)
-    c = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]])
-    wts = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    u = b1.field(O.F_U)[:, :dim]
     cu = u @ c.T
     uu = (u * u).sum(axis=1, keepdims=True)
     fe = wts * rho[:, None] * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * uu)
@@ -580,12 +634,6 @@ def test_les_reduces_to_bgk_and_solves_quadratic():
 
 
 # ------------------------------------------------ interpolation and integration
-
-def _c2():
-    c = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]])
-    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
-    return c, w
-
 
 def test_pressure_force_interpolates_quadratic_density():
     # Gas at rest with rho = 1 + a (x-x0)^2 + b (y-y0)^2 and resting particles:
@@ -619,6 +667,51 @@ def test_pressure_force_interpolates_quadratic_density():
     bed2.set_populations(w[:, None] * rho[None, :])
     bed2.step(1)
     np.testing.assert_allclose(bed2.particles()[1], -want, rtol=1e-9, atol=1e-20)
+
+
+def test_pressure_force_interpolates_quadratic_density_3d():
+    # The same on D3Q19 with trilinear weights, in a box whose three sides
+    # differ (a z stride or node index built from the wrong side reads other
+    # nodes): grad p = 2 (a_x (x-x0), a_y (y-y0), a_z (z-z0)) / 3.
+    n, a, x0 = (10, 7, 12), np.array([2e-4, -3e-4, 1.5e-4]), np.array([4.3, 3.1, 6.7])
+    rng = np.random.default_rng(4)
+    P = np.column_stack([rng.uniform(1.5, n[k] - 1.5, 60) for k in range(3)])
+    keep = [0]
+    for i in range(1, len(P)):
+        if np.min(np.linalg.norm(P[keep] - P[i], axis=1)) > 0.25:
+            keep.append(i)
+    P = P[keep]
+    bed = O.OracleBed(_bed(dim=3, n=n, bc=(W.WALL,) * 6, d_p=0.2, rho_s=500.0, pos=P,
+                           vel=np.zeros_like(P)))
+    idx = np.arange(n[0] * n[1] * n[2])
+    X = np.column_stack([idx % n[0], (idx // n[0]) % n[1], idx // (n[0] * n[1])]) + 0.5
+    rho = 1 + ((X - x0) ** 2 * a).sum(axis=1)
+    _, w = _c3()
+    bed.set_populations(w[:, None] * rho[None, :])
+    bed.step(1)
+    P1, v1 = bed.particles()
+    want = -2 * a * (P - x0) / 3.0 / 500.0
+    np.testing.assert_allclose(v1, want, rtol=1e-9, atol=1e-20)
+    np.testing.assert_allclose(P1, P + v1, rtol=0, atol=1e-15)
+
+
+def test_close_packing_cap_3d():
+    # Eq. 10 in 3D: eps_s = n V_p / h^3 up to the close packing of spheres,
+    # pi / (3 sqrt 2); two spheres of d = 0.9 h in one cell would fill 0.76 of
+    # it.  In 3D the gas voidage is 1 - eps_s (no Eq. 11).
+    n = (7, 5, 5)
+    P = np.array([[2.05, 2.05, 2.05], [2.95, 2.95, 2.95], [4.5, 2.5, 2.5]])
+    bed = O.OracleBed(_bed(dim=3, n=n, bc=(W.WALL,) * 6, d_p=0.9, rho_s=500.0, pos=P,
+                           vel=np.zeros_like(P)))
+    bed.step(1)
+    es, eg = bed.field(O.F_EPS_S), bed.field(O.F_EPS_G)
+    two, one = 2 + n[0] * (2 + n[1] * 2), 4 + n[0] * (2 + n[1] * 2)
+    vp = math.pi * 0.9 ** 3 / 6
+    assert 2 * vp > math.pi / (3 * math.sqrt(2))
+    assert es[two] == pytest.approx(math.pi / (3 * math.sqrt(2)), rel=1e-15)
+    assert es[one] == pytest.approx(vp, rel=1e-15)
+    np.testing.assert_allclose(eg, 1.0 - es, rtol=0, atol=1e-15)
+    assert np.count_nonzero(es) == 2
 
 
 def test_pre_drag_at_node_and_face_midpoint():
