@@ -892,6 +892,34 @@ def test_global_momentum_balance_periodic_box(dim):
     assert np.abs((-(1 - gt) / tt)[:, None] * (m - rho[:, None] * u)).sum() > 1e-3 * np.abs(dm).sum()
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_statistics_are_the_sums_of_the_state(dim):
+    # The FP64 statistics of a step (spec reductions): gas mass and
+    # momentum are sum_i f_i and sum_i c_i f_i over all cells, the particle
+    # momentum is m_p sum_k v_k, and the mean slip is the particle-weighted
+    # mean over occupied cells of |u_act - v_s| from the step's deposition.
+    # Recomputed here with exactly rounded sums.
+    w = _dense_bed(dim)
+    bed = O.OracleBed(w)
+    bed.step(3)
+    st = bed.stats()
+    f = bed.populations()
+    c, _ = _c2() if dim == 2 else _c3()
+    assert st["mass"] == pytest.approx(math.fsum(f.ravel()), rel=1e-15)
+    for a in range(dim):
+        ga = math.fsum((c[:, a][:, None] * f).ravel())
+        assert st["gas_momentum"][a] == pytest.approx(ga, rel=1e-12, abs=1e-15)
+    _, v = bed.particles()
+    mp = bed.constants()["mp"]
+    np.testing.assert_allclose(st["particle_momentum"][:dim],
+                               [mp * math.fsum(v[:, a]) for a in range(dim)], rtol=1e-12)
+    n = bed.field(O.F_NTOT).astype(float)
+    slip = np.linalg.norm(bed.field(O.F_UACT)[:, :dim] - bed.field(O.F_VS)[:, :dim], axis=1)
+    assert (n > 1).any() and (n == 0).any()
+    assert st["mean_slip"] == pytest.approx(math.fsum(n * slip) / math.fsum(n), rel=1e-13)
+    assert st["mean_slip"] > 0
+
+
 def test_touching_spheres_without_approach_do_not_collide():
     # §2.2: a contact collides only when (P1-P2).(v1-v2) is negative; equal
     # velocities (zero product) or separating spheres do not collide.
