@@ -114,6 +114,12 @@ def test_gamma_limits():
         assert O.gamma(1.0, tau) == pytest.approx(1.0, abs=1e-15)
         g = [O.gamma(e, tau) for e in np.linspace(0, 1, 101)]
         assert np.all(np.diff(g) > 0)
+    # Eq. 9 in tau: a partially filled cell loses its solid weighting as tau
+    # falls to 1/2 and approaches the solid fraction itself as tau grows
+    for es in (0.1, 0.45, 0.9):
+        assert O.gamma(es, 0.5) == 0.0
+        assert O.gamma(es, 0.5 + 1e-12) == pytest.approx(0.0, abs=1e-10)
+        assert O.gamma(es, 1e9) == pytest.approx(es, rel=1e-8)
 
 
 def test_eps3d_packings():
@@ -140,6 +146,20 @@ def test_beta_isolated_sphere(slip):
     assert f == pytest.approx(_schiller_naumann_force(re, rho, slip, d), rel=1e-6)
     if re < 1e-3:   # Stokes' law
         assert f == pytest.approx(3 * math.pi * mu * d * slip, rel=1e-3)
+
+
+@pytest.mark.parametrize("eps", [0.7401, 0.76, 0.81, 0.9, 0.96])
+@pytest.mark.parametrize("slip", [1e-3, 0.3, 30.0])
+def test_beta_dilute_branch_carries_omega(eps, slip):
+    # Eq. 19 above eps_g = 0.74: 3/4 (1-eps) eps rho C_d0 |u-v| / d times the
+    # EMMS correction omega(eps) of Eq. 20, with C_d0 the Schiller-Naumann
+    # coefficient at Re_p = eps rho |u-v| d / mu (Eq. 21-22)
+    rho, mu, d = 1.2, 1.8e-5, 1e-4
+    re = eps * rho * slip * d / mu
+    cd = 24.0 / re * (1 + 0.15 * re ** 0.687) if re < 1000 else 0.44
+    want = 0.75 * (1 - eps) * eps * rho * cd * slip / d * O.omega(eps)
+    assert O.beta(eps, slip, rho, mu, d) == pytest.approx(want, rel=1e-12)
+    assert O.omega(eps) != 1.0
 
 
 @pytest.mark.parametrize("eps", [0.4, 0.55, 0.74])
