@@ -49,7 +49,9 @@ class Setup(ctypes.Structure):
 def lib():
     global _LIB
     if _LIB is None:
-        path = _build.build()
+        # LBDPS_ORACLE_LIB names another build of the oracle source: the
+        # mutation check of the pins loads its planted-mistake libraries so
+        path = os.environ.get("LBDPS_ORACLE_LIB") or _build.build()
         L = ctypes.CDLL(path)
         d = ctypes.c_double
         dp = ctypes.POINTER(ctypes.c_double)
