@@ -225,6 +225,31 @@ MUTANTS = [
     ('beta switch',
      'if (eps_g > 0.74) {\n        double omega',
      'if (eps_g > 0.8) {\n        double omega'),
+    # deposition, partner choice and wall rules of the hard spheres, soft walls
+    ('vs mean',
+     'sum[a] / (double)n : 0.0',
+     'sum[a] / (double)(n + 1) : 0.0'),
+    ('tie to later candidate',
+     'if (d2 < bestd2[p] || (d2 == bestd2[p]',
+     'if (d2 <= bestd2[p] || (d2 == bestd2[p]'),
+    ('partner tie to larger id',
+     '(d2 == bestd2[p] && b->id[j] < b->id[bestp[p]])',
+     '(d2 == bestd2[p] && b->id[j] > b->id[bestp[p]])'),
+    ('walls for paired too',
+     'if (paired[p] || !b->wall_hit[p]) continue;',
+     'if (!b->wall_hit[p]) continue;'),
+    ('lower wall without approach',
+     'if (pa < r && va < 0.0) b->wall_hit[p] |= 1 << (2 * a);',
+     'if (pa < r) b->wall_hit[p] |= 1 << (2 * a);'),
+    ('upper wall approach sign',
+     '(double)b->n[a] - pa < r && va > 0.0)',
+     '(double)b->n[a] - pa < r && va < 0.0)'),
+    ('soft wall lever is r',
+     'for (int c = 0; c < 3; ++c) vc[c] = (c < dim ? vp[c] : 0.0) - l * wxn[c];\n                contact_add(b, nrm, l, f, vc, F, T);',
+     'for (int c = 0; c < 3; ++c) vc[c] = (c < dim ? vp[c] : 0.0) - r * wxn[c];\n                contact_add(b, nrm, r, f, vc, F, T);'),
+    ('pair order descending',
+     'if (a[0] != b[0]) return a[0] < b[0] ? -1 : 1;',
+     'if (a[0] != b[0]) return a[0] < b[0] ? 1 : -1;'),
 ]
 
 

@@ -527,6 +527,34 @@ def test_detection_matches_bruteforce(dim, n, N):
         assert best[i] == min(cand, key=lambda j: (d2(j), j))
 
 
+def test_partner_ties_go_to_the_smaller_id():
+    # Reading R14: among approaching contacts at exactly the same distance the
+    # one with the smaller id is chosen.  Coordinates and speeds are exact in
+    # binary, so both squared distances are 1/64.  Group 1: particle 0 between
+    # 2 (cell to its left, visited first) and 1 (its own cell); group 2:
+    # particle 3 with 4 and 5, all three in one cell.
+    u = 0.015625
+    P = np.array([[4.0, 4.5], [4.125, 4.5], [3.875, 4.5],
+                  [2.0, 2.0], [2.0, 2.125], [2.125, 2.0]])
+    v = np.array([[0.0, 0.0], [-u, 0.0], [u, 0.0],
+                  [0.0, 0.0], [0.0, -u], [-u, 0.0]])
+    w = _bed(n=(8, 8), d_p=0.15, pos=np.zeros((0, 2)), vel=np.zeros((0, 2)))
+    bed = O.OracleBed(w)
+    bed.set_particles(P, v)
+    bed.collide_particles()
+    best = bed.particle_diag(O.P_BEST).astype(np.int64)
+    np.testing.assert_array_equal(best, [1, 0, 0, 4, 3, 3])
+    # the chosen pairs collide head on (Eq. 17-18, equal masses); the third
+    # particle of each group chose a partner that chose another: untouched
+    _, v1 = bed.particles()
+    e = w.e
+    np.testing.assert_array_equal(v1[[2, 5]], v[[2, 5]])
+    np.testing.assert_allclose(v1[0], [-(1 + e) / 2 * u, 0.0], rtol=1e-14)
+    np.testing.assert_allclose(v1[1], [-(1 - e) / 2 * u, 0.0], rtol=1e-14)
+    np.testing.assert_allclose(v1[3], [0.0, -(1 + e) / 2 * u], rtol=1e-14)
+    np.testing.assert_allclose(v1[4], [0.0, -(1 - e) / 2 * u], rtol=1e-14)
+
+
 def test_resolution_momentum_and_walls():
     # mutual nearest pairs collide by Eq. 17-18, the rest bounce off walls:
     # total particle momentum changes only through wall contacts
