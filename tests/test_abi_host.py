@@ -135,3 +135,95 @@ def test_noalloc_sort_rejects_oversize_on_host(lib):
                                           None)
     assert rc == lib.ERR_CAPACITY
     assert b"exceed" in lib.lib().lbdps_last_error()
+
+
+def test_handle_calls_reject_null_arguments_on_host(lib):
+    # every call on a bed or a server answers LBDPS_ERR_INVALID for a NULL
+    # handle (or a NULL output) without touching the device
+    L = lib.lib()
+    calls = {
+        "lbdps_step": (None, 1),
+        "lbdps_step_monitored": (None, 1, None),
+        "lbdps_step_profiled": (None, 1, None, 0, None),
+        "lbdps_sync": (None,),
+        "lbdps_fields": (None, 1, 0, None, 0),
+        "lbdps_particles": (None, 0, None, None, 0),
+        "lbdps_set_particles": (None, 0, None, None),
+        "lbdps_particle_spin": (None, 0, None, 0),
+        "lbdps_set_particle_spin": (None, None, 0),
+        "lbdps_populations": (None, None, 0),
+        "lbdps_set_populations": (None, None, 0),
+        "lbdps_particle_diag": (None, 0, None, 0),
+        "lbdps_collide_particles": (None, None, 0, None),
+        "lbdps_stats": (None, None),
+        "lbdps_health": (None, None),
+        "lbdps_constants": (None, None, 0),
+        "lbdps_shape": (None, None, None, None, None),
+        "lbdps_save": (None, None, 0, None),
+        "lbdps_load": (None, None, 0),
+        "lbdps_record_event": (None, None),
+        "lbdps_bubbles": (None, 0.85, 0, None),
+        "lbdps_set_inlet": (None, None),
+        "lbdps_check_guards": (None, None),
+        "lbdps_server_submit": (None, None, None, None, 1, 0, None),
+        "lbdps_server_poll": (None, 0.0, None, 0, None),
+        "lbdps_server_load": (None, None, None, None),
+        "lbdps_server_take": (None, 1, None),
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == lib.ERR_INVALID, name
+        assert L.lbdps_last_error(), name
+    L.lbdps_destroy(None)
+    L.lbdps_server_destroy(None)
+
+
+def test_empty_server_on_host(lib):
+    # creating a server reserves nothing on the device: bad limits are
+    # rejected, an empty server reports no load, and taking an unknown
+    # request fails cleanly
+    L = lib.lib()
+    s = ctypes.c_void_p()
+    for budget, active, tick in ((0, 4, 8), (1 << 30, 0, 8), (1 << 30, 4, 0)):
+        assert L.lbdps_server_create(budget, active, tick, ctypes.byref(s)) == lib.ERR_INVALID
+    assert L.lbdps_server_create(1 << 30, 4, 8, ctypes.byref(s)) == lib.OK and s.value
+    q, a, used = ctypes.c_int(-1), ctypes.c_int(-1), ctypes.c_size_t(7)
+    assert L.lbdps_server_load(s, ctypes.byref(q), ctypes.byref(a), ctypes.byref(used)) == lib.OK
+    assert (q.value, a.value, used.value) == (0, 0, 0)
+    h = ctypes.c_void_p(1)
+    assert L.lbdps_server_take(s, 12345, ctypes.byref(h)) == lib.ERR_INVALID
+    assert not h.value
+    assert b"no kept result" in L.lbdps_last_error()
+    L.lbdps_server_destroy(s)
+
+
+def test_memory_estimate_on_host(lib):
+    # lbdps_memory_estimate does no device work: it validates like
+    # lbdps_create and counts the bytes of every buffer of the bed
+    L = lib.lib()
+
+    def est(**over):
+        lat, par, prm, keep = _desc(lib, **over)
+        out = ctypes.c_size_t(0)
+        rc = L.lbdps_memory_estimate(ctypes.byref(lat), ctypes.byref(par), ctypes.byref(prm),
+                                     ctypes.byref(out))
+        return rc, out.value
+
+    ncell, q = 64 * 64, 9
+    big = {"n": (64, 64, 1), "h": 1e-3}
+    rc64, b64 = est(**big, storage=0)
+    rc32, b32 = est(**big, storage=1)
+    rc16, b16 = est(**big, storage=2)
+    rcbf, bbf = est(**big, storage=3)
+    assert (rc64, rc32, rc16, rcbf) == (lib.OK,) * 4
+    # two population buffers of q values per cell, and more (ghost layer)
+    assert b64 - b32 >= 2 * q * ncell * 4
+    assert b32 - b16 >= 2 * q * ncell * 2
+    assert b16 == bbf
+    # the particle arrays grow with the particle count
+    # (each buffer rounded up to 256 B: 2 and 200 particles differ)
+    grid = [[(i + 0.5) * 1e-3, (j + 0.5) * 1e-3] for i in range(20) for j in range(10)]
+    rc, b32_200 = est(**big, storage=1, pos=grid)
+    assert rc == lib.OK and b32_200 > b32
+    # the same validation as create
+    rc, _ = est(storage=7)
+    assert rc == lib.ERR_INVALID and b"bad storage" in L.lbdps_last_error()
