@@ -227,3 +227,39 @@ def test_memory_estimate_on_host(lib):
     # the same validation as create
     rc, _ = est(storage=7)
     assert rc == lib.ERR_INVALID and b"bad storage" in L.lbdps_last_error()
+
+
+def test_missing_library_fails_loudly(lib, monkeypatch, tmp_path):
+    # no fallback: without liblbdps.so every entry point raises
+    from paper_1303_2653_gb300 import workloads as W
+    monkeypatch.setattr(lib, "LIB_PATH", str(tmp_path / "liblbdps.so"))
+    monkeypatch.setattr(lib, "_LIB", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        lib.lib()
+    with pytest.raises(RuntimeError, match="missing"):
+        lib.memory_estimate(W.bubbling2d(nx=16, ny=32, n_particles=10))
+
+
+def test_product_never_reaches_the_oracle():
+    # the package (Python, CUDA, C) neither imports, includes, links nor
+    # loads anything of the oracle
+    import ast
+    pkg = os.path.join(ROOT, "paper_1303_2653_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            path = os.path.join(dirpath, f)
+            if f.endswith(".py"):
+                tree = ast.parse(open(path).read())
+                for node in ast.walk(tree):
+                    if isinstance(node, ast.Import):
+                        mods = [a.name for a in node.names]
+                    elif isinstance(node, ast.ImportFrom):
+                        mods = [node.module or ""]
+                    else:
+                        continue
+                    assert not any(m.split(".")[0] == "oracle" for m in mods), (path, mods)
+                assert "liboracle" not in open(path).read(), path
+            elif f.endswith((".cu", ".cuh", ".c", ".h")):
+                text = open(path).read()
+                assert "lbdps_oracle" not in text and "liboracle" not in text, path
+                assert not re.search(r"\bob_[a-z]+\(", text), path
