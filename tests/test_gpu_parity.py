@@ -66,6 +66,8 @@ TOL_DERIVED = {W.STORE_F64: 1e-11, W.STORE_F32: 1e-5}
 def _workloads():
     return {
         "riser2d": W.scaled_riser2d(nx=48, ny=96),
+        # 13,000 cells: three full 4,096-cell scan tiles and a ragged fourth
+        "riser2d_tiles": W.scaled_riser2d(nx=100, ny=130),
         "riser2d_les": W.scaled_riser2d(nx=40, ny=64, cs_smag=0.15, seed=77),
         "bubbling2d": W.bubbling2d(nx=32, ny=64, n_particles=600, steps=5),
         "dense2d": W.riser2d(nx=24, ny=48, n_particles=1200, solid_fraction=0.25, sigma_v=0.6,
@@ -90,7 +92,7 @@ def test_constants_match_oracle():
 
 # ------------------------------------------------------------ sort / binning
 
-@pytest.mark.parametrize("name", ["riser2d", "dense2d", "riser3d"])
+@pytest.mark.parametrize("name", ["riser2d", "riser2d_tiles", "dense2d", "riser3d"])
 def test_initial_sort_bit_exact(name):
     w = _workloads()[name]
     L = _lb()
