@@ -57,3 +57,19 @@ def test_two_ranks_take_the_max_time_and_count_all_cells():
         assert t == 20.0
         assert value == pytest.approx(2 * 1000 * 50 / 0.020 / 1e6)
         assert printed == ""
+
+
+def test_oracle_sample_is_a_slab_of_large_beds():
+    # the CPU baseline times the oracle on the full bed when it is small and
+    # on a slab with the full cross section and the same solid fraction
+    import bench
+    from paper_1303_2653_gb300 import workloads as W
+    small = W.scaled_riser2d(nx=32, ny=64)
+    s, what = bench.oracle_sample(small)
+    assert what == "the full bed" and s.n == small.n and s.storage == W.STORE_F64
+    big = W.scaled_riser3d(nx=32, ny=32, nz=256)
+    s, what = bench.oracle_sample(big, max_cells=50_000)
+    assert s.n == (32, 32, 48) and "slab" in what
+    assert s.bc == big.bc and s.storage == W.STORE_F64
+    assert abs(s.n_particles / s.ncell - big.n_particles / big.ncell) <= 1.0 / s.ncell
+    assert s.h == pytest.approx(big.h, rel=0.02) and s.d_p == big.d_p
