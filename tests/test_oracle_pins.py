@@ -1637,3 +1637,16 @@ def test_friction_forces_and_torques_match_all_pairs_3d(walls):
     np.testing.assert_allclose(bed.spin() - spin0, T / k["inertia"], rtol=0,
                                atol=1e-12 * np.abs(T / k["inertia"]).max())
     assert (np.abs(T).sum(axis=1) > 0).mean() > 0.3
+
+
+def test_mutation_check_sample():
+    # three planted mistakes from different parts of the oracle (the full
+    # list, run by hand: python tests/mutation_check.py) are each caught
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    r = subprocess.run([sys.executable, os.path.join(here, "mutation_check.py"), "-j", "3",
+                        "-k", "omega_s sign", "-k", "cross3 sign", "-k", "tie to later"],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "3 of 3 caught" in r.stdout
