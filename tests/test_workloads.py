@@ -59,3 +59,47 @@ def test_soft_sphere_workload_helpers():
     assert f.dem_mu == 0.3 and f.dem_gamma_t == pytest.approx(0.1 * m_p / w.dt, rel=1e-14)
     w3 = W.packed_bed(dim=3, n=(6, 6, 8), n_particles=2000)
     assert w3.pos.shape == (2000, 3) and pdist(w3.pos).min() >= 0.9 * w3.d_p * (1 - 1e-12)
+
+
+def test_documented_workload_recipes():
+    # the synthetic stand-ins for the paper's two simulations and the bench
+    # beds carry the sizes and derived lattice quantities stated for them:
+    # Table 1 (bubbling bed), Table 2 (riser), and the riser, bubbling and 3D
+    # benches built on them
+    import math
+    from oracle import oracle as O
+    area = lambda w, rows: w.n_particles * math.pi * (0.5 * w.d_p) ** 2 / (w.n[0] * rows * w.h ** 2)
+
+    b = W.bubbling2d()
+    k = O.units(b)
+    assert (b.n, b.n_particles, b.h, b.dt, b.d_p, b.rho_s) == ((64, 128), 2000, 2e-3, 1e-4, 5e-4, 2500.0)
+    assert k["tau"] == pytest.approx(0.50113, abs=1e-5)
+    assert k["u0_y"] == pytest.approx(0.1885 * 1e-4 / 2e-3, rel=1e-3)
+    jet = np.flatnonzero(b.inlet_u[:, 1] > 1.5 * b.inlet_u[:, 1].min())
+    assert jet.tolist() == [30, 31, 32, 33]
+    assert b.inlet_u[30, 1] == pytest.approx(5 * b.inlet_u[0, 1], rel=1e-12)
+
+    r = W.riser2d()
+    k = O.units(r)
+    assert (r.n, r.n_particles, r.d_p, r.rho_s) == ((256, 2048), 200000, 54e-6, 930.0)
+    assert area(r, 2048) == pytest.approx(0.05, rel=1e-12)
+    assert r.h == pytest.approx(1.322e-4, rel=1e-3) and r.dt == pytest.approx(2.98e-6, rel=1e-3)
+    assert k["tau"] == pytest.approx(0.50818, abs=1e-5) and k["u0_y"] == pytest.approx(0.0338)
+
+    t1 = W.bubbling_table1()
+    k = O.units(t1)
+    assert (t1.n, t1.n_particles, t1.h, t1.dt) == ((25, 100), 15000, 2.7e-4, 1.35e-6)
+    assert area(t1, 45) == pytest.approx(0.42, abs=2e-3)
+    assert k["tau"] == pytest.approx(0.50089, abs=1e-5)
+
+    t2 = W.cfb_riser2d()
+    assert (t2.n, t2.n_particles) == ((60, 720), 123921)
+    assert t2.dt == pytest.approx(6.0e-6, rel=1e-3)
+
+    r3 = W.riser3d()
+    k = O.units(r3)
+    assert (r3.n, r3.n_particles) == ((256, 256, 1024), 4000000)
+    vp = math.pi * r3.d_p ** 3 / 6
+    assert r3.n_particles * vp / (math.prod(r3.n) * r3.h ** 3) == pytest.approx(0.03, rel=1e-12)
+    assert r3.h == pytest.approx(5.47e-5, rel=1e-3) and r3.dt == pytest.approx(1.23e-6, abs=5e-9)
+    assert k["tau"] == pytest.approx(0.5198, abs=1e-4)
