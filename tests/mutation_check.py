@@ -250,6 +250,16 @@ MUTANTS = [
     ('pair order descending',
      'if (a[0] != b[0]) return a[0] < b[0] ? -1 : 1;',
      'if (a[0] != b[0]) return a[0] < b[0] ? 1 : -1;'),
+    # soft-sphere walls, the open outlet, bubble regions
+    ('wall damping with m/2',
+     'k->eta_w = 2.0 * z * sqrt(k->mp * k->kn);',
+     'k->eta_w = 2.0 * z * sqrt(0.5 * k->mp * k->kn);'),
+    ('soft outlet closed',
+     'if (side == 1 && b->recirculate && a == dim - 1) continue;',
+     'if (side == 1 && b->recirculate && a == dim - 1 && 0) continue;'),
+    ('freeboard counted',
+     'if (top) continue;',
+     'if (top && 0) continue;'),
 ]
 
 
