@@ -57,6 +57,14 @@
  *       smallest distance (ties to the smaller id); mutual picks collide by
  *       Eq. 17-18 on pre-collision velocities; wall contacts (the wall is an
  *       infinitely heavy particle at rest) apply to the rest.
+ *   R15 A 2D cell is h x h x h: Eq. 25 carries h^2/dt = 1 in lattice units
+ *       and a particle is a sphere, m_p = rho_s pi d^3 / 6.
+ *   R16 The gas density in Eq. 19, 21 and 22 is the reference density (1 in
+ *       lattice units), not the local rho.
+ *   R17 Every lattice quantity is derived from the SI columns of Tables 1-2
+ *       (two printed dimensionless entries are garbled).
+ *   R18 Particles in a cell are ordered by id, which fixes every summation
+ *       order (Eq. 8, 27).
  *   R19 The bed-mean voidage is that of the current positions (Eq. 10-11
  *       from a fresh count), not of the last deposition.
  *   R21 Solids loop of the circulating bed (§3.2): a particle that crosses
