@@ -114,6 +114,7 @@ int admit(lbdps_server *s)
         if (cudaEventCreateWithFlags(&a->last, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&a->tick, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
+            if (a->last) cudaEventDestroy(a->last);
             lbdps_destroy(h);
             return sfail(LBDPS_ERR_CUDA, "server: event creation failed");
         }

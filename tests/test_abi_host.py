@@ -263,3 +263,34 @@ def test_product_never_reaches_the_oracle():
                 text = open(path).read()
                 assert "lbdps_oracle" not in text and "liboracle" not in text, path
                 assert not re.search(r"\bob_[a-z]+\(", text), path
+
+
+def test_server_reports_a_request_it_cannot_create(lib):
+    # without a device, creating the bed of an admitted request fails with
+    # LBDPS_ERR_CUDA; the server reports that request as done with the
+    # status instead of losing it.  A request larger than the whole budget is
+    # refused at submission.
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("needs a machine without a GPU")
+    L = lib.lib()
+    lat, par, prm, keep = _desc(lib)
+    s = ctypes.c_void_p()
+    assert L.lbdps_server_create(1 << 30, 4, 8, ctypes.byref(s)) == lib.OK
+    rid = ctypes.c_uint64(0)
+    assert L.lbdps_server_submit(s, ctypes.byref(lat), ctypes.byref(par), ctypes.byref(prm),
+                                 10, 0, ctypes.byref(rid)) == lib.OK
+    recs, nd = (lib.DoneRec * 4)(), ctypes.c_int(0)
+    assert L.lbdps_server_poll(s, 0.0, recs, 4, ctypes.byref(nd)) == lib.OK
+    assert nd.value == 1 and recs[0].id == rid.value and recs[0].status == lib.ERR_CUDA
+    q, a = ctypes.c_int(-1), ctypes.c_int(-1)
+    used = ctypes.c_size_t(1)
+    L.lbdps_server_load(s, ctypes.byref(q), ctypes.byref(a), ctypes.byref(used))
+    assert (q.value, a.value, used.value) == (0, 0, 0)
+    L.lbdps_server_destroy(s)
+    small = ctypes.c_void_p()
+    assert L.lbdps_server_create(1000, 4, 8, ctypes.byref(small)) == lib.OK
+    assert L.lbdps_server_submit(small, ctypes.byref(lat), ctypes.byref(par), ctypes.byref(prm),
+                                 10, 0, ctypes.byref(rid)) == lib.ERR_CAPACITY
+    assert b"exceeds the HBM budget" in L.lbdps_last_error()
+    L.lbdps_server_destroy(small)
