@@ -260,6 +260,9 @@ MUTANTS = [
     ('freeboard counted',
      'if (top) continue;',
      'if (top && 0) continue;'),
+    ('set_inlet unscaled',
+     'b->inlet_u[j * 3 + a] = inlet_si[j * b->dim + a] * b->uscale;',
+     'b->inlet_u[j * 3 + a] = inlet_si[j * b->dim + a];'),
 ]
 
 

@@ -300,21 +300,33 @@ def test_inlet_populations_follow_the_profile(dim):
     inlet = rng.uniform(-2e-3, 2e-3, (nface, dim))
     inlet[:, -1] = rng.uniform(1e-3, 4e-3, nface)
     pos = np.zeros((0, dim))
-    bed = O.OracleBed(_bed(dim=dim, n=n, bc=bc, mu_g=0.2, inlet_u=inlet, pos=pos, vel=pos))
+    # h = 2, dt = 1/2: lattice velocities are the SI ones times dt / h = 1/4
+    bed = O.OracleBed(_bed(dim=dim, n=n, bc=bc, h=2.0, dt=0.5, mu_g=0.2, inlet_u=4 * inlet,
+                           pos=pos, vel=pos))
+
+    def check(profile):
+        f = bed.populations()
+        checked = 0
+        for j in range(nface):
+            q = np.array([j % n[0], j // n[0]])[: dim - 1]
+            for i in range(len(w)):
+                src = q - c[i][: dim - 1]
+                if c[i][-1] != 1 or np.any(src < 0) or np.any(src >= np.array(n[: dim - 1])):
+                    continue
+                cu = c[i] @ profile[j]
+                want = w[i] * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * profile[j] @ profile[j])
+                assert f[i, j] == pytest.approx(want, rel=1e-14), (j, i)
+                checked += 1
+        assert checked > 2 * nface
+
     bed.step(1)
-    f = bed.populations()
-    checked = 0
-    for j in range(nface):
-        q = np.array([j % n[0], j // n[0]])[: dim - 1]
-        for i in range(len(w)):
-            src = q - c[i][: dim - 1]
-            if c[i][-1] != 1 or np.any(src < 0) or np.any(src >= np.array(n[: dim - 1])):
-                continue
-            cu = c[i] @ inlet[j]
-            want = w[i] * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * inlet[j] @ inlet[j])
-            assert f[i, j] == pytest.approx(want, rel=1e-14), (j, i)
-            checked += 1
-    assert checked > 2 * nface
+    check(inlet)
+    # a new profile (the end of a jet pulse, §3.1), given in SI, applies from
+    # the next step
+    inlet2 = inlet[::-1].copy() * 0.5
+    bed.set_inlet(4 * inlet2)
+    bed.step(1)
+    check(inlet2)
 
 
 # -------------------------------------------------------- coupled-step invariants
