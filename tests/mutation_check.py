@@ -260,6 +260,12 @@ MUTANTS = [
     ('freeboard counted',
      'if (top) continue;',
      'if (top && 0) continue;'),
+    ('open faces at local density',
+     'b->fnew[(size_t)i * nc + x] = feq(b, i, 1.0, uin);',
+     'b->fnew[(size_t)i * nc + x] = feq(b, i, b->rho[x], uin);'),
+    ('guo second order',
+     '+ 9.0 * cu * b->c[i][a]) * b->k.fb[a];',
+     '+ 3.0 * cu * b->c[i][a]) * b->k.fb[a];'),
     ('set_inlet unscaled',
      'b->inlet_u[j * 3 + a] = inlet_si[j * b->dim + a] * b->uscale;',
      'b->inlet_u[j * 3 + a] = inlet_si[j * b->dim + a];'),
