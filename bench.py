@@ -189,6 +189,28 @@ def collide_stream_bytes(w, storage):
     return w.ncell * per_cell + w.n_particles * per_particle, per_cell, per_particle
 
 
+def drag_step_bytes(w, storage):
+    """Algorithmic bytes of one drag_step launch: per particle the cell key,
+    the FP64 position and the velocity and in-cell offset read, the same
+    three written, the new key and its histogram count; per cell the node
+    fields of the interpolation and the Eq. 28 rescale (rho, u_act[dim],
+    F_p->g[dim], beta, 1 - eps) and the cell-list offset, each read once."""
+    s_r = 8 if storage == "f64" else 4
+    d = w.dim
+    per_particle = 4 + 2 * (d * 8 + 2 * d * s_r) + 4 + 4
+    per_cell = (3 + 2 * d) * s_r + 4
+    return w.ncell * per_cell + w.n_particles * per_particle, per_cell, per_particle
+
+
+def kernel_roofline(alg_bytes, ms, peak):
+    """Achieved GB/s of a launch moving alg_bytes in ms, and its fraction of
+    the peak (None when the kernel was not timed)."""
+    if not ms or ms <= 0:
+        return None
+    achieved = alg_bytes / (ms / 1e3) / 1e9
+    return {"achieved": achieved, "frac": achieved / peak, "ms": ms, "algorithmic_bytes": alg_bytes}
+
+
 def profiled_traffic(workload_name):
     """DRAM bytes per collide_stream launch from the committed ncu summary of
     this workload, if it was taken on the current kernel source."""
@@ -406,6 +428,10 @@ def main():
                 "traffic": traffic, "algorithmic_bytes": alg_bytes,
                 "bytes_per_cell": per_cell, "bytes_per_particle": per_particle,
                 "per_kernel_ms": per_kernel_ms}
+    # the particle-side kernel of about the same time in 2D, against the same
+    # HBM peak (it is bound by the latency of dependent loads, not by bytes)
+    roofline["drag"] = kernel_roofline(drag_step_bytes(w, args.storage)[0],
+                                       per_kernel_ms.get("drag", 0.0), peak)
 
     # ---- end to end through the C ABI from host buffers ----
     e2e = None

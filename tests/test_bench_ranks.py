@@ -73,3 +73,20 @@ def test_oracle_sample_is_a_slab_of_large_beds():
     assert s.bc == big.bc and s.storage == W.STORE_F64
     assert abs(s.n_particles / s.ncell - big.n_particles / big.ncell) <= 1.0 / s.ncell
     assert s.h == pytest.approx(big.h, rel=0.02) and s.d_p == big.d_p
+
+
+def test_drag_step_bytes_and_kernel_roofline():
+    # per particle: cell key 4 + P, v, off read (2D FP32: 16 + 8 + 8) and
+    # written + new key 4 + histogram count 4; per cell: rho, u_act[2],
+    # F_p->g[2], beta, 1 - eps (7 x 4) + the cell-list offset 4
+    import bench
+    from paper_1303_2653_gb300 import workloads as W
+    w = W.scaled_riser2d(nx=32, ny=64)
+    total, per_cell, per_particle = bench.drag_step_bytes(w, "f32")
+    assert (per_cell, per_particle) == (32, 76)
+    assert total == 32 * 32 * 64 + 76 * w.n_particles
+    w3 = W.scaled_riser3d(nx=8, ny=8, nz=16)
+    assert bench.drag_step_bytes(w3, "f64")[1:] == (9 * 8 + 4, 4 + 2 * (24 + 48) + 8)
+    r = bench.kernel_roofline(2e9, 1.0, 4000.0)     # 2 GB in 1 ms: 2,000 GB/s
+    assert r["achieved"] == pytest.approx(2000.0) and r["frac"] == pytest.approx(0.5)
+    assert bench.kernel_roofline(2e9, 0.0, 4000.0) is None
