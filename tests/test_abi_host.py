@@ -294,3 +294,21 @@ def test_server_reports_a_request_it_cannot_create(lib):
                                  10, 0, ctypes.byref(rid)) == lib.ERR_CAPACITY
     assert b"exceeds the HBM budget" in L.lbdps_last_error()
     L.lbdps_server_destroy(small)
+
+
+def test_binding_constants_match_the_header(lib):
+    # every integer constant of include/lbdps.h is in the binding under the
+    # same name without the LBDPS_ prefix, with the same value
+    text = open(os.path.join(ROOT, "include", "lbdps.h")).read()
+    found = 0
+    for name, val in re.findall(r"^#define (LBDPS_[A-Z0-9_]+)[ \t]+([^/\n]+)", text, flags=re.M):
+        val = val.strip()
+        m = re.fullmatch(r"\(?(-?\d+)\)?", val) or re.fullmatch(r"\((\d+)\s*<<\s*(\d+)\)", val)
+        if not m:
+            continue
+        value = int(m.group(1)) << int(m.group(2)) if m.lastindex == 2 else int(m.group(1))
+        py = name[len("LBDPS_"):]
+        assert hasattr(lib, py), name
+        assert getattr(lib, py) == value, (name, getattr(lib, py), value)
+        found += 1
+    assert found >= 35
