@@ -2,9 +2,9 @@
 
 Each entry plants one plausible mistake in a copy of ``oracle/lbdps_oracle.c``
 (a dropped term, a wrong sign, index, stride or constant, a branch limit moved),
-builds the copy into a library of its own in a temporary folder, and runs
-``tests/test_oracle_pins.py`` against it (``LBDPS_ORACLE_LIB`` makes the oracle
-load that library).  A mutant that passes every pin marks a part of the oracle
+builds the copy into a library of its own in a temporary folder under
+``_build/``, and runs ``tests/test_oracle_pins.py`` against it
+(``LBDPS_ORACLE_LIB`` makes the oracle load that library).  A mutant that passes every pin marks a part of the oracle
 that the pins do not fix.  The committed source is never modified.
 
     python tests/mutation_check.py [-j JOBS] [-k SUBSTRING ...]
@@ -300,7 +300,9 @@ def main():
     args = ap.parse_args()
     todo = [(i, *m) for i, m in enumerate(MUTANTS)
             if not args.k or any(k in m[0] for k in args.k)]
-    with tempfile.TemporaryDirectory() as tmp:
+    scratch = os.path.join(ROOT, "_build")     # git-ignored, inside the repository
+    os.makedirs(scratch, exist_ok=True)
+    with tempfile.TemporaryDirectory(dir=scratch) as tmp:
         with ThreadPoolExecutor(max_workers=max(1, args.jobs)) as pool:
             results = list(pool.map(lambda t: run_one(*t, tmp), todo))
     missed = 0

@@ -312,3 +312,37 @@ def test_binding_constants_match_the_header(lib):
         assert getattr(lib, py) == value, (name, getattr(lib, py), value)
         found += 1
     assert found >= 35
+
+
+def test_binding_structs_match_the_header_layout(lib):
+    # offsets and sizes of the ctypes structures equal those a C compiler
+    # gives the header's structs (a C program built against include/lbdps.h
+    # prints them)
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    structs = {"lbdps_lattice_desc": lib.LatticeDesc, "lbdps_particle_desc": lib.ParticleDesc,
+               "lbdps_params": lib.Params, "lbdps_stats_t": lib.Stats, "lbdps_done_t": lib.DoneRec}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbdps.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    scratch = os.path.join(ROOT, "_build", "layout")
+    os.makedirs(scratch, exist_ok=True)
+    src, exe = os.path.join(scratch, "layout.c"), os.path.join(scratch, "layout")
+    with open(src, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", exe, src],
+                   check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    want = {}
+    for ln in filter(None, out):
+        parts = ln.split()
+        want[tuple(parts[:-1])] = int(parts[-1])
+    for cname, cls in structs.items():
+        assert ctypes.sizeof(cls) == want[(cname, "size")], cname
+        for field, _ in cls._fields_:
+            assert getattr(cls, field).offset == want[(cname, field)], (cname, field)
