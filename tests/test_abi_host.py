@@ -229,10 +229,10 @@ def test_memory_estimate_on_host(lib):
     assert rc == lib.ERR_INVALID and b"bad storage" in L.lbdps_last_error()
 
 
-def test_missing_library_fails_loudly(lib, monkeypatch, tmp_path):
+def test_missing_library_fails_loudly(lib, monkeypatch):
     # no fallback: without liblbdps.so every entry point raises
     from paper_1303_2653_gb300 import workloads as W
-    monkeypatch.setattr(lib, "LIB_PATH", str(tmp_path / "liblbdps.so"))
+    monkeypatch.setattr(lib, "LIB_PATH", os.path.join(ROOT, "_build", "absent", "liblbdps.so"))
     monkeypatch.setattr(lib, "_LIB", None)
     with pytest.raises(RuntimeError, match="missing"):
         lib.lib()
