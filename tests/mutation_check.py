@@ -266,6 +266,12 @@ MUTANTS = [
     ('guo second order',
      '+ 9.0 * cu * b->c[i][a]) * b->k.fb[a];',
      '+ 3.0 * cu * b->c[i][a]) * b->k.fb[a];'),
+    ('in-cell order by id reversed',
+     'if (a->id != b->id) return a->id < b->id ? -1 : 1;',
+     'if (a->id != b->id) return a->id < b->id ? 1 : -1;'),
+    ('bed voidage from the deposition',
+     'se += voidage_of_count(b, b->cell_start[x + 1] - b->cell_start[x], &es, &e2);',
+     'se += voidage_of_count(b, b->ntot[x], &es, &e2);'),
     ('set_inlet unscaled',
      'b->inlet_u[j * 3 + a] = inlet_si[j * b->dim + a] * b->uscale;',
      'b->inlet_u[j * 3 + a] = inlet_si[j * b->dim + a];'),
