@@ -386,13 +386,16 @@ void lbdps_server_destroy(lbdps_server_t *s);
  * path, for np particles with ids 0..np-1:
  *   dim          2 or 3;  n: cells per axis (n[2] ignored in 2D)
  *   pos[a]       DEVICE array of np FP64 coordinates along axis a, lattice
- *                units; positions outside [0, n[a]) are clamped to the
- *                first/last cell
+ *                units; a coordinate below 0 (or NaN) counts in the first
+ *                cell of its axis, one at or above n[a] in the last
  *   cell_start   DEVICE output, ncell + 1 ints: particles of cell c occupy
  *                sorted slots cell_start[c] .. cell_start[c+1]-1
  *   order        DEVICE output, np ints: the particle id in each sorted slot
  *   stream       cudaStream_t (NULL = legacy default stream); asynchronous
- * Temporaries live in one fixed device array of about 12 MB, created on each
+ * The order inside a cell comes from a stable radix sort of the cell keys
+ * (at most three 8-bit passes), so the work is linear in np whatever the
+ * occupancy of the cells.  np < 0 returns LBDPS_ERR_INVALID.
+ * Temporaries live in one fixed device array of about 28 MB, created on each
  * GPU that loads the library and kept until the process exits; this function
  * calls no cudaMalloc, cudaFree or allocating library routine.  Limits:
  * ncell <= 1048576 and np <= 1048576, otherwise LBDPS_ERR_CAPACITY with no

@@ -137,6 +137,16 @@ def test_noalloc_sort_rejects_oversize_on_host(lib):
     assert b"exceed" in lib.lib().lbdps_last_error()
 
 
+def test_noalloc_sort_rejects_negative_count_on_host(lib):
+    # a negative particle count is an invalid argument, not a capacity error
+    nn = (ctypes.c_int * 3)(8, 8, 1)
+    pp = (ctypes.c_void_p * 3)(1, 1, None)
+    rc = lib.lib().lbdps_bin_sort_noalloc(2, nn, -5, pp, ctypes.c_void_p(1), ctypes.c_void_p(1),
+                                          None)
+    assert rc == lib.ERR_INVALID
+    assert b"bad arguments" in lib.lib().lbdps_last_error()
+
+
 def test_handle_calls_reject_null_arguments_on_host(lib):
     # every call on a bed or a server answers LBDPS_ERR_INVALID for a NULL
     # handle (or a NULL output) without touching the device
