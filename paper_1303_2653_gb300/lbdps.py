@@ -463,10 +463,12 @@ class Server:
         self._callbacks = []
 
     def submit(self, w, steps: int, storage: Optional[int] = None, keep: bool = False,
-               alloc=None, free=None) -> int:
+               alloc=None, free=None, diagnostics: bool = False) -> int:
         """Queue a bed for `steps` steps.  `alloc(nbytes) -> int|None` and
-        `free(ptr)` optionally replace cudaMalloc/cudaFree for this bed."""
-        lat, par, prm, keepalive = describe(w, storage)
+        `free(ptr)` optionally replace cudaMalloc/cudaFree for this bed;
+        `diagnostics` keeps the node diagnostics (needed for the mean slip
+        of the completion record)."""
+        lat, par, prm, keepalive = describe(w, storage, diagnostics)
         if alloc is not None:
             cb_a = ALLOC_FN(lambda n, ctx: alloc(n))
             cb_f = FREE_FN(lambda ptr, ctx: free(ptr) if free else None)
@@ -490,7 +492,7 @@ class Server:
             out.append({"id": r.id, "status": r.status, "steps": r.steps, "cells": r.cells,
                         "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done,
                         "mass": r.stats.mass, "mean_eps_g": r.stats.mean_eps_g,
-                        "health": r.stats.health})
+                        "mean_slip": r.stats.mean_slip, "health": r.stats.health})
         return out
 
     def load(self):
