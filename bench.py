@@ -1,12 +1,16 @@
 #!/usr/bin/env python3
 """Benchmark of the coupled LB-DPS step on GB300.
 
-Default workload: the periodic riser section, D2Q9 256 x 2048 cells, 200,000
-particles of 54 um at mean 2D solid fraction 0.05, FP32 deviation storage
-(the riser configuration in the shape of the paper's Table 2).  A "step" is
-one coupled time step: deposition + modified-LBE collide-stream, interpolated
-EMMS drag with the third-law rescale and integration, cell sort, hard-sphere
-collision detection and resolution.
+Default workload: the 3D riser, D3Q19 256 x 256 x 1024 cells (walls in x
+and y, periodic in z), 4,000,000 particles of 54 um at volume fraction 0.03,
+FP32 deviation storage (about 10 GB of populations): the largest
+single-GPU configuration of the riser of the paper's §3.2 / Table 2,
+extended to 3D as §4 suggests.  A "step" is one coupled time step:
+deposition + modified-LBE collide-stream, interpolated EMMS drag with the
+third-law rescale and integration, cell sort, hard-sphere collision
+detection and resolution.  The same line carries the 2D riser section
+(D2Q9 256 x 2048, 200,000 particles, mean 2D solid fraction 0.05) under
+"riser2d", measured the same way.
 
 Prints one JSON line (rank 0).  Metric: coupled-step MLUPS (cell updates per
 second / 1e6), whole job over all ranks.  Multi-GPU runs are independent
@@ -14,8 +18,8 @@ replicas of the bed (weak scaling, no data-path collective).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Other modes, one JSON line each: --workload riser3d | bubbling2d (the D3Q19
-riser, the small FP64 bubbling bed), --storage f16 | bf16 | f64, --serving
+Other modes, one JSON line each: --workload riser2d | bubbling2d (the 2D
+riser alone, the small FP64 bubbling bed), --storage f16 | bf16 | f64, --serving
 (continuous batching of a Poisson stream of beds against one-by-one FP32),
 --precision (per-field error of each storage format against the FP64
 oracle), --cfb (solids flux of the circulating-bed riser), --bubble (bubble
@@ -57,7 +61,9 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only build the bed and run this many steps (for ncu captures); "
                          "no timing, no JSON line")
-    ap.add_argument("--workload", default="riser2d",
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="with the 3D riser: skip the 2D riser line beside it")
+    ap.add_argument("--workload", default="riser3d",
                     choices=["riser2d", "riser3d", "riser3d-128x128x512", "bubbling2d"])
     ap.add_argument("--serving", action="store_true",
                     help="serving benchmark: Poisson stream of independent beds")
@@ -265,6 +271,34 @@ def oracle_rate(w, budget_s):
     return w.ncell * steps / dt / 1e6, steps, dt
 
 
+def _oracle_worker(args):
+    """One process of the all-cores oracle timing: build the bed, step it for
+    about budget_s seconds, return (cell updates, seconds)."""
+    w, budget_s = args
+    from oracle import oracle as O
+    bed = O.OracleBed(w)
+    t0 = time.perf_counter()
+    bed.step(1)
+    per = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(per, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    bed.step(steps)
+    return w.ncell * steps, time.perf_counter() - t0, steps
+
+
+def oracle_rate_all_cores(w, budget_s, cores):
+    """The FP64 oracle on every host core at once: `cores` independent
+    one-thread processes (started with spawn), each stepping its own copy of
+    the bed; returns (aggregate MLUPS, steps of one process, the slowest
+    process's seconds)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(w, budget_s)] * cores)
+    slowest = max(r[1] for r in res)
+    return sum(r[0] for r in res) / slowest / 1e6, min(r[2] for r in res), slowest
+
+
 def max_over_ranks(x, dist=None, device="cuda"):
     """Max over all ranks of a per-rank figure (a time); barrier after."""
     if dist is None:
@@ -372,6 +406,73 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w = workload(args.storage, args.workload)
+    peak, peak_kind = measured_peaks()
+    res = measure_bed(L, torch, w, args, dist, world, peak, peak_kind, with_e2e=not args.no_e2e)
+
+    # the 2D riser beside the 3D headline: same timing rules, its own roofline
+    secondary = None
+    if args.workload == "riser3d" and not args.no_secondary:
+        w2 = workload(args.storage, "riser2d")
+        r2 = measure_bed(L, torch, w2, args, dist, world, peak, peak_kind, with_e2e=False)
+        secondary = {"workload": config_dict(w2, world, args.storage)["workload"],
+                     "value": r2["value"], "unit": UNIT, "ms_per_step": r2["ms_per_step"],
+                     "particle_updates_per_s": r2["particle_updates_per_s"],
+                     "roofline": r2["roofline"], "whole_step": r2["whole_step"],
+                     "health": r2["health"]}
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample, what = oracle_sample(w)
+        rate, n_st, secs = oracle_rate(sample, 15.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n_st} FP64 oracle steps of {what} ({secs:.1f} s, one thread)"}
+        cores = os.cpu_count() or 1
+        if cores > 1:
+            agg, steps_each, secs_all = oracle_rate_all_cores(sample, 10.0, cores)
+            cpu["all_cores"] = {
+                "value": agg, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"{cores} independent one-thread oracle processes, each stepping "
+                          f"{what} ({steps_each} steps in {secs_all:.1f} s); the aggregate "
+                          f"cell updates per second"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.storage == "f64" else "f32",
+                "data": "synthetic", "config": config_dict(w, world, args.storage),
+                "roofline": res["roofline"], "whole_step": res["whole_step"],
+                "cpu_baseline": cpu, "e2e": res["e2e"],
+                "gpu_launches": KERNELS_PER_STEP * args.steps * world,
+                "clocks": res["clocks"], "health": res["health"],
+                "particle_updates_per_s": res["particle_updates_per_s"]}
+        if secondary:
+            line["riser2d"] = secondary
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def whole_step_bytes(w, storage):
+    """Algorithmic bytes of one coupled step: populations read and written
+    once, per cell the cell-list offset and the node outputs read by the drag,
+    per particle its state read and written in the drag and again in the
+    sort.  Neighbour, stencil and halo re-reads are cache traffic, not
+    counted."""
+    q = 9 if w.dim == 2 else 19
+    s_f = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}[storage]
+    s_r = 8 if storage == "f64" else 4
+    c_cell = 4 + (1 + 2 * w.dim) * s_r
+    s_p = w.dim * 8 + w.dim * s_r
+    return w.ncell * (2 * q * s_f + c_cell) + w.n_particles * 4 * s_p
+
+
+def measure_bed(L, torch, w, args, dist, world, peak, peak_kind, with_e2e=True):
+    """K timed steps of bed w (L2 flushed before each), the per-kernel-class
+    times of profiled steps, and (optionally) the end-to-end run through the
+    C ABI from host arrays."""
     bed = L.Bed(w)
     st = bed.stream
     # L2 flush between timed steps: write a buffer larger than L2, then read
@@ -393,7 +494,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
     time.sleep(0.3)
     with torch.cuda.stream(st):
@@ -419,7 +520,6 @@ def main():
                 acc[k] = acc.get(k, 0.0) + v
     per_kernel_ms = {k: v / prof_steps for k, v in acc.items()}
     alg_bytes, per_cell, per_particle = collide_stream_bytes(w, args.storage)
-    peak, peak_kind = measured_peaks()
     cs_ms = per_kernel_ms["collide_stream"]
     achieved = alg_bytes / (cs_ms / 1e3) / 1e9
     traffic = profiled_traffic(w.name.split("-")[0] + "_" + "x".join(str(v) for v in w.n))
@@ -428,14 +528,20 @@ def main():
                 "traffic": traffic, "algorithmic_bytes": alg_bytes,
                 "bytes_per_cell": per_cell, "bytes_per_particle": per_particle,
                 "per_kernel_ms": per_kernel_ms}
-    # the particle-side kernel of about the same time in 2D, against the same
-    # HBM peak (it is bound by the latency of dependent loads, not by bytes)
+    # the drag kernel against the same peak (in 3D the second largest share of
+    # the step; in 2D about as long as collide_stream and bound by the
+    # latency of dependent loads, not by bytes)
     roofline["drag"] = kernel_roofline(drag_step_bytes(w, args.storage)[0],
                                        per_kernel_ms.get("drag", 0.0), peak)
+    ms_step = total_ms / args.steps
+    ws_bytes = whole_step_bytes(w, args.storage)
+    whole_step = {"algorithmic_bytes": ws_bytes, "ideal_ms": ws_bytes / (peak * 1e9) * 1e3,
+                  "achieved": ws_bytes / (ms_step / 1e3) / 1e9,
+                  "frac": ws_bytes / (ms_step / 1e3) / 1e9 / peak, "unit": "GB/s"}
 
     # ---- end to end through the C ABI from host buffers ----
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b2 = L.Bed(w)                      # H2D of the particle state from host arrays
@@ -456,30 +562,12 @@ def main():
                "d2h_bytes_per_step": d2h_step + d2h_final / args.steps,
                "includes": "create from host arrays, K x (step + FP64 statistics copied to "
                            "host, pipelined: lbdps_step_monitored), final particle readback"}
-
-    # ---- CPU oracle on the host cores (rank 0, N = 1) ----
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample, what = oracle_sample(w)
-        rate, n_st, secs = oracle_rate(sample, 15.0)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{n_st} FP64 oracle steps of {what} ({secs:.1f} s, one thread)"}
-
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if args.storage == "f64" else "f32",
-                "data": "synthetic", "config": config_dict(w, world, args.storage),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": KERNELS_PER_STEP * args.steps * world,
-                "clocks": clock_info, "health": health,
-                "particle_updates_per_s": world * w.n_particles * args.steps / (total_ms / 1e3)}
-        print(json.dumps(line), flush=True)
     bed.close()
-    if dist:
-        dist.destroy_process_group()
+    del flush, flush_rd
+    torch.cuda.empty_cache()
+    return {"value": value, "ms_per_step": ms_step, "roofline": roofline,
+            "whole_step": whole_step, "e2e": e2e, "clocks": clock_info, "health": health,
+            "particle_updates_per_s": world * w.n_particles * args.steps / (total_ms / 1e3)}
 
 
 
