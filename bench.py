@@ -609,8 +609,85 @@ def serving_requests(count, rate, seed=1303004):
     return reqs
 
 
-def serving_main(args):
+def serve(L, reqs, budget, max_active, steps_per_tick, batching):
+    """Run the request stream through the server (arrivals replayed in real
+    time); returns per-request latency (submit to completion), the records,
+    the makespan and the batch counters."""
     import numpy as np
+    server = L.Server(hbm_budget=budget, max_active=max_active, steps_per_tick=steps_per_tick,
+                      batching=batching)
+    ids, done, lat = {}, {}, {}
+    nxt = 0
+    t0 = time.perf_counter()
+    while len(done) < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt][0] <= now:
+            w = reqs[nxt][1]
+            ids[server.submit(w, w.steps)] = nxt
+            nxt += 1
+        for r in server.poll(wait_s=0.0005):
+            i = ids[r["id"]]
+            done[i] = r
+            lat[i] = (time.perf_counter() - t0) - reqs[i][0]
+    makespan = time.perf_counter() - t0 - reqs[0][0]
+    info = server.batch_info()
+    server.close()
+    return np.array([lat[i] for i in range(len(reqs))]), done, makespan, info
+
+
+def one_by_one(L, W, reqs):
+    """The same requests one by one in plain FP32 (FIFO in arrival order):
+    latencies, mean voidage of each result, makespan."""
+    import numpy as np
+    import torch
+    t_free, lat, eps = 0.0, [], []
+    for arrival, w in reqs:
+        b = L.Bed(w, storage=W.STORE_F32)
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        b.step(w.steps)
+        b.sync()
+        dt = time.perf_counter() - s0
+        eps.append(b.stats()["mean_eps_g"])
+        b.close()
+        begin = max(t_free, arrival)
+        t_free = begin + dt
+        lat.append(t_free - arrival)
+    return np.array(lat), np.array(eps), t_free - reqs[0][0]
+
+
+def serving_summary(L, W, reqs, budget, max_active, steps_per_tick, compare_streams=True):
+    """Served (batched and, optionally, every bed on its own stream) against
+    one by one in plain FP32, on the same request stream."""
+    import numpy as np
+    work = sum(w.ncell * w.steps for _, w in reqs)
+    out = {"requests": len(reqs), "cell_updates": work,
+           "fp16_requests": sum(1 for _, w in reqs if w.storage == W.STORE_F16)}
+    modes = [("served_batched", True)] + ([("served_streams", False)] if compare_streams else [])
+    eps_b = ok = None
+    for key, batching in modes:
+        lat, done, makespan, info = serve(L, reqs, budget, max_active, steps_per_tick, batching)
+        failed = [{"request": i, "workload": reqs[i][1].name, "status": done[i]["status"],
+                   "health": done[i].get("health")}
+                  for i in range(len(reqs)) if done[i]["status"] != 0]
+        out[key] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                    "aggregate_mlups": work / makespan / 1e6, "makespan_s": makespan,
+                    "failed": len(failed), "failed_requests": failed}
+        if batching:
+            out[key]["batch_ticks"], out[key]["graph_captures"] = info[0], info[1]
+            eps_b = np.array([done[i]["mean_eps_g"] for i in range(len(reqs))])
+            ok = np.array([done[i]["status"] == 0 for i in range(len(reqs))])
+    lat1, eps1, make1 = one_by_one(L, W, reqs)
+    out["one_by_one_fp32"] = {"p50_s": float(np.percentile(lat1, 50)),
+                              "p99_s": float(np.percentile(lat1, 99)),
+                              "aggregate_mlups": work / make1 / 1e6, "makespan_s": make1}
+    rel = (np.abs(eps_b - eps1) / eps1)[ok]
+    out["served_vs_fp32_alone"] = {"mean_voidage_rel_err_max": float(rel.max()),
+                                   "mean_voidage_rel_err_mean": float(rel.mean())}
+    return out
+
+
+def serving_main(args):
     import torch
     import __graft_entry__ as ge
     ge.build()
@@ -621,67 +698,11 @@ def serving_main(args):
     reqs = serving_requests(args.requests, args.rate)
     free, total = torch.cuda.mem_get_info()
     budget = int(0.5 * free)
-    work = sum(w.ncell * w.steps for _, w in reqs)
-
-    # served: continuous batching, mixed storage
-    server = L.Server(hbm_budget=budget, max_active=args.max_active,
-                      steps_per_tick=args.steps_per_tick)
-    ids, done, lat = {}, {}, {}
-    nxt = 0
-    t0 = time.perf_counter()
-    while len(done) < len(reqs):
-        now = time.perf_counter() - t0
-        while nxt < len(reqs) and reqs[nxt][0] <= now:
-            ids[server.submit(reqs[nxt][1], reqs[nxt][1].steps)] = nxt
-            nxt += 1
-        for r in server.poll(wait_s=0.0005):
-            i = ids[r["id"]]
-            done[i] = r
-            lat[i] = (time.perf_counter() - t0) - reqs[i][0]
-    makespan = time.perf_counter() - t0 - reqs[0][0]
-    server.close()
-    served_lat = np.array([lat[i] for i in range(len(reqs))])
-    eps_served = np.array([done[i]["mean_eps_g"] for i in range(len(reqs))])
-    failed = [{"request": i, "workload": reqs[i][1].name, "storage": reqs[i][1].storage,
-               "status": done[i]["status"], "health": done[i].get("health")}
-              for i in range(len(reqs)) if done[i]["status"] != 0]
-    ok = np.array([done[i]["status"] == 0 for i in range(len(reqs))])
-
-    # baseline: the same requests one by one in plain FP32 (FIFO in arrival order)
-    t_free, base_lat, eps_fp32 = 0.0, [], []
-    t_start = time.perf_counter()
-    for arrival, w in reqs:
-        b = L.Bed(w, storage=W.STORE_F32)
-        torch.cuda.synchronize()
-        s0 = time.perf_counter()
-        b.step(w.steps)
-        b.sync()
-        dt = time.perf_counter() - s0
-        eps_fp32.append(b.stats()["mean_eps_g"])
-        b.close()
-        begin = max(t_free, arrival)
-        t_free = begin + dt
-        base_lat.append(t_free - arrival)
-    base_lat = np.array(base_lat)
-    base_makespan = t_free - reqs[0][0]
-    eps_fp32 = np.array(eps_fp32)
-    rel = (np.abs(eps_served - eps_fp32) / eps_fp32)[ok]
-    solid_rel = (np.abs(eps_served - eps_fp32) / np.maximum(1 - eps_fp32, 1e-12))[ok]
+    summ = serving_summary(L, W, reqs, budget, args.max_active, args.steps_per_tick)
     line = {"metric": "served p50/p99 time-to-K-steps and aggregate MLUPS", "unit": "s / MLUPS",
-            "requests": len(reqs), "rate_per_s": args.rate, "cell_updates": work,
-            "data": "synthetic",
-            "served": {"p50_s": float(np.percentile(served_lat, 50)),
-                       "p99_s": float(np.percentile(served_lat, 99)),
-                       "aggregate_mlups": work / makespan / 1e6, "makespan_s": makespan,
-                       "failed": len(failed), "failed_requests": failed, "budget_bytes": budget, "max_active": args.max_active,
-                       "steps_per_tick": args.steps_per_tick,
-                       "fp16_requests": sum(1 for _, w in reqs if w.storage == W.STORE_F16)},
-            "one_by_one_fp32": {"p50_s": float(np.percentile(base_lat, 50)),
-                                "p99_s": float(np.percentile(base_lat, 99)),
-                                "aggregate_mlups": work / base_makespan / 1e6,
-                                "makespan_s": base_makespan},
-            "mean_voidage_rel_err": {"max": float(rel.max()), "mean": float(rel.mean()),
-                                     "max_rel_to_solid_fraction": float(solid_rel.max())}}
+            "rate_per_s": args.rate, "data": "synthetic", "budget_bytes": budget,
+            "max_active": args.max_active, "steps_per_tick": args.steps_per_tick}
+    line.update(summ)
     print(json.dumps(line), flush=True)
 
 

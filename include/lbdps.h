@@ -374,6 +374,20 @@ int lbdps_server_poll(lbdps_server_t *s, double wait_s, lbdps_done_t *out, int c
 int lbdps_server_load(lbdps_server_t *s, int *queued, int *active, size_t *used);
 /* Hand over a finished kept bed; the caller then owns the handle (lbdps_destroy). */
 int lbdps_server_take(lbdps_server_t *s, uint64_t req_id, lbdps_t **out);
+/* Batched stepping (on by default).  Small beds of the batched kind (2D,
+ * FP32 arithmetic, FP32 / FP16 / BF16 population storage, hard spheres, at
+ * most max_cells cells and at most one particle per cell on average) advance
+ * together: each kernel of a coupled step is one launch over all of them, a
+ * device work table of (bed, tile) entries walked by persistent thread
+ * blocks, and a tick of steps_per_tick steps is one replay of a captured
+ * CUDA graph.  Each bed's arithmetic is that of the bed run alone.  Larger
+ * or denser beds, and beds of other kinds, advance on streams of their own
+ * by replays of their own step graphs.  on = 0: every bed on its own stream.
+ * max_cells = 0 keeps the default (131072 cells).  Applies to beds admitted
+ * afterwards; LBDPS_ERR_INVALID for max_cells < 0. */
+int lbdps_server_set_batching(lbdps_server_t *s, int on, int64_t max_cells);
+/* Counters of the batch: ticks launched, graph captures, current members. */
+int lbdps_server_batch_info(lbdps_server_t *s, int64_t *ticks, int64_t *captures, int *members);
 void lbdps_server_destroy(lbdps_server_t *s);
 
 /* Cell binning without device allocation.  The paper has no counterpart:

@@ -12,6 +12,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 using namespace lbdpsk;
@@ -220,6 +221,9 @@ struct Engine {
     virtual size_t checkpoint_bytes() const = 0;
     virtual int save(char *buf) = 0;
     virtual int load(const char *buf) = 0;
+    // the bed's buffers and parameters for a batch of the serving loop
+    // (2D, FP32 arithmetic, hard spheres only)
+    virtual int batch_describe(BatchBed *) { return LBDPS_ERR_INVALID; }
 };
 
 }  // namespace
@@ -1095,6 +1099,43 @@ template <class L, class Real, class S> struct EngineT : Engine {
         CU(cudaStreamSynchronize(st));
         return LBDPS_OK;
     }
+
+    int batch_describe(BatchBed *out) override
+    {
+        if constexpr (D == 2 && std::is_same<Real, float>::value) {
+            if (H->soft) return LBDPS_ERR_INVALID;
+            BatchBed b{};
+            b.sp = sp;
+            b.lay = lay;
+            for (int p = 0; p < 2; ++p) {
+                b.f[p] = f[p];
+                b.cl_local[p] = cl_local[p];
+                b.cl_base[p] = cl_base[p];
+                b.part[p] = part[p];
+            }
+            b.tile_total = tile_total;
+            b.ticket = ticket;
+            b.stage = stage;
+            b.fld = fld;
+            b.key = key;
+            b.counts = counts;
+            b.idslot = idslot;
+            b.slot = slot;
+            b.best = best;
+            b.wall = wall;
+            b.diag_fpre = diag_fpre;
+            b.diag_fd = diag_fd;
+            b.np = H->np;
+            b.ncell = H->ncell;
+            b.storage = std::is_same<S, __half>::value ? ST_F16
+                        : std::is_same<S, __nv_bfloat16>::value ? ST_BF16 : ST_F32;
+            *out = b;
+            return LBDPS_OK;
+        } else {
+            (void)out;
+            return LBDPS_ERR_INVALID;
+        }
+    }
 };
 
 template <class L>
@@ -1346,6 +1387,21 @@ void free_graphs(lbdps *h)
 // lbdps_last_error().
 namespace lbdpsk {
 void set_last_error(const char *msg) { g_last_error = msg; }
+
+int batch_describe(lbdps *h, BatchBed *out)
+{
+    if (!h || !h->eng || !out) return LBDPS_ERR_INVALID;
+    return h->eng->batch_describe(out);
+}
+
+void batch_advanced(lbdps *h, long long nsteps)
+{
+    h->parity ^= (int)(nsteps & 1);
+    h->steps += nsteps;
+}
+
+cudaStream_t bed_stream(lbdps *h) { return h->stream; }
+int bed_parity(lbdps *h) { return h->parity; }
 }  // namespace lbdpsk
 
 namespace {

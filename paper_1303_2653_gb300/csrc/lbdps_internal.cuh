@@ -380,4 +380,66 @@ void launch_reduce_all(const PopLayout &lay, int ncell, const S *f, Particles<Re
 
 int reduce_block_count(int n);
 
+// ---------------------------------------------------------------------------
+// Batched stepping of many beds (the serving loop).  Every buffer and
+// parameter one coupled step of a bed reads, for both buffer parities; the
+// kernels of a batch read these records from device memory.  Beds of a batch
+// are 2D with FP32 arithmetic and hard spheres; their populations may be
+// stored in FP32, FP16 or BF16 (storage).
+// ---------------------------------------------------------------------------
+struct BatchBed {
+    StepParams<float> sp;
+    PopLayout lay;
+    const void *f[2];              // population buffers in the bed's storage type
+    int *cl_local[2], *cl_base[2];
+    int *tile_total;
+    unsigned *ticket;
+    Particles<float> part[2], stage;
+    Fields<float> fld;
+    int *key, *counts, *idslot;
+    int2 *slot;
+    int *best, *wall;
+    float *diag_fpre, *diag_fd;
+    int np, ncell, storage;
+    int parity0;                   // buffer parity at the start of the tick
+    int nsteps;                    // steps this bed takes in the tick (<= the tick's length)
+};
+
+// Work tables of a batch: (bed, tile) per thread block of each kernel class.
+// Cell tiles cover kBatchTile consecutive cells of a bed, scan tiles the
+// kCellTile-cell tiles of the cell list, particle tiles kBatchTile
+// consecutive sorted particles.  The entry counts live in device memory
+// (count[0..2]: cell, scan, particle tiles), so a captured tick stays valid
+// when the tables are rewritten for another set of beds.
+constexpr int kBatchTile = 256;
+struct BatchWork {
+    const int2 *cell_tiles;
+    const int2 *scan_tiles;
+    const int2 *part_tiles;
+    const int *count;   // device; null: launch nothing
+};
+
+// One coupled step of every bed of the batch whose nsteps exceeds `step`
+// (step = 0 .. tick length - 1): the seven kernels of the single-bed step,
+// each one launch over all beds (persistent blocks walking the work table).
+// The first call of each launcher sizes its grid (call it outside stream
+// capture; a null count launches nothing).
+void launch_collide_stream_batched(const BatchBed *beds, BatchWork work, int step, cudaStream_t st);
+void launch_particles_batched(const BatchBed *beds, BatchWork work, int step, cudaStream_t st);
+// Blocks of `threads` threads of kernel `kern` that fit on the whole GPU at
+// once (at least 1, at most nwork).
+int resident_grid(const void *kern, int threads, int nwork);
+
+}  // namespace lbdpsk
+
+// Internal hooks of the handle API used by the serving loop.
+struct lbdps;
+namespace lbdpsk {
+// Fills *out for a bed that can join a batch (2D, FP32 arithmetic, hard
+// spheres), else returns LBDPS_ERR_INVALID.  parity0 / nsteps are left 0.
+int batch_describe(struct lbdps *h, BatchBed *out);
+// The bed's parity and step count after the batch advanced it nsteps steps.
+void batch_advanced(struct lbdps *h, long long nsteps);
+cudaStream_t bed_stream(struct lbdps *h);
+int bed_parity(struct lbdps *h);
 }  // namespace lbdpsk

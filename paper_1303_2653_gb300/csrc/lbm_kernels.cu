@@ -3,6 +3,8 @@
 // import/export.
 #include "lbdps_internal.cuh"
 
+#include <algorithm>
+
 namespace lbdpsk {
 
 // ---------------------------------------------------------------------------
@@ -273,18 +275,17 @@ __device__ __forceinline__ void face_streaming_x(const StepParams<Real> &p, cons
     }
 }
 
+// The work of one cell (idx: its coordinates): deposition, collision,
+// node outputs and streaming.  Shared by the single-bed kernel and the
+// batched kernel of the serving loop, so that a bed's arithmetic does not
+// depend on how its cells are mapped to threads.
 template <class L, class Real, class S, bool LES, bool FB>
-__global__ void __launch_bounds__(256, K2Occupancy<L, Real>::value)
-k_collide_stream(StepParams<Real> p, PopLayout lay, PopPtrs<S> pp, CellList cells,
-                 Particles<Real> parts, Fields<Real> fld)
+__device__ __forceinline__ void collide_stream_cell(const StepParams<Real> &p, const PopLayout &lay,
+                                                    const PopPtrs<S> &pp, const CellList &cells,
+                                                    const Particles<Real> &parts,
+                                                    const Fields<Real> &fld, const int *idx)
 {
     constexpr int D = L::D, Q = L::Q;
-    // grid: x along blockIdx.x/threadIdx.x, y = blockIdx.y, z = blockIdx.z
-    int idx[3];
-    idx[0] = blockIdx.x * blockDim.x + threadIdx.x;
-    idx[1] = blockIdx.y;
-    idx[2] = blockIdx.z;
-    if (idx[0] >= p.n[0]) return;
     const int x = idx[0] + p.n[0] * (idx[1] + p.n[1] * idx[2]);
     const int xe = lay.ext(idx);
 
@@ -465,6 +466,20 @@ k_collide_stream(StepParams<Real> p, PopLayout lay, PopPtrs<S> pp, CellList cell
     else if (xhi) face_streaming_x<L, Real, S, 1>(p, lay, pp, xe, idx, rho, u);
 }
 
+template <class L, class Real, class S, bool LES, bool FB>
+__global__ void __launch_bounds__(256, K2Occupancy<L, Real>::value)
+k_collide_stream(StepParams<Real> p, PopLayout lay, PopPtrs<S> pp, CellList cells,
+                 Particles<Real> parts, Fields<Real> fld)
+{
+    // grid: x along blockIdx.x/threadIdx.x, y = blockIdx.y, z = blockIdx.z
+    int idx[3];
+    idx[0] = blockIdx.x * blockDim.x + threadIdx.x;
+    idx[1] = blockIdx.y;
+    idx[2] = blockIdx.z;
+    if (idx[0] >= p.n[0]) return;
+    collide_stream_cell<L, Real, S, LES, FB>(p, lay, pp, cells, parts, fld, idx);
+}
+
 template <class L, class Real, class S>
 void launch_collide_stream(const StepParams<Real> &p, const PopLayout &lay, const S *fin, S *fout,
                            CellList cells, Particles<Real> parts, Fields<Real> fld, cudaStream_t st)
@@ -486,6 +501,80 @@ void launch_collide_stream(const StepParams<Real> &p, const PopLayout &lay, cons
         k_collide_stream<L, Real, S, false, true><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
     else
         k_collide_stream<L, Real, S, false, false><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
+}
+
+// ---------------------------------------------------------------------------
+// Batched collide-stream of the serving loop: persistent blocks walk the
+// work table of (bed, tile) entries; each entry is kBatchTile consecutive
+// cells of one bed (rows follow each other, so narrow lattices fill the
+// block).  Each cell runs collide_stream_cell with its bed's parameters and
+// the instantiation of its bed's storage type and LES / body-force flags.
+// ---------------------------------------------------------------------------
+template <class S>
+__device__ __forceinline__ void batched_cell(const BatchBed &b, int a, const int *idx)
+{
+    PopPtrs<S> pp;
+    const S *fin = static_cast<const S *>(b.f[a]);
+    S *fout = const_cast<S *>(static_cast<const S *>(b.f[1 - a]));
+#pragma unroll
+    for (int i = 0; i < D2Q9::Q; ++i) {
+        pp.pull[i] = fin + (long long)i * b.lay.nce - b.lay.off<D2Q9>(i);
+        pp.own[i] = fout + (long long)i * b.lay.nce;
+    }
+    const CellList cells{b.cl_local[a], b.cl_base[a]};
+    const bool les = b.sp.les_k > 0.0f, fb = b.sp.has_fb != 0;
+    if (les && fb)
+        collide_stream_cell<D2Q9, float, S, true, true>(b.sp, b.lay, pp, cells, b.part[a], b.fld, idx);
+    else if (les)
+        collide_stream_cell<D2Q9, float, S, true, false>(b.sp, b.lay, pp, cells, b.part[a], b.fld, idx);
+    else if (fb)
+        collide_stream_cell<D2Q9, float, S, false, true>(b.sp, b.lay, pp, cells, b.part[a], b.fld, idx);
+    else
+        collide_stream_cell<D2Q9, float, S, false, false>(b.sp, b.lay, pp, cells, b.part[a], b.fld, idx);
+}
+
+// two blocks per SM: the three storage types and four flag combinations
+// inlined in one kernel need up to 128 registers without spilling
+constexpr int kBatchCsBlocksPerSm = 2;
+
+__global__ void __launch_bounds__(kBatchTile, kBatchCsBlocksPerSm)
+k_collide_stream_batched(const BatchBed *__restrict__ beds, const int2 *__restrict__ work,
+                         const int *__restrict__ count, int step)
+{
+    const int nwork = *count;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int2 e = work[w];
+        const BatchBed &b = beds[e.x];
+        if (step >= b.nsteps) continue;
+        const int c = e.y * kBatchTile + threadIdx.x;
+        if (c >= b.ncell) continue;
+        const int idx[3] = {c % b.sp.n[0], c / b.sp.n[0], 0};
+        const int a = (b.parity0 + step) & 1;
+        if (b.storage == ST_F16) batched_cell<__half>(b, a, idx);
+        else if (b.storage == ST_BF16) batched_cell<__nv_bfloat16>(b, a, idx);
+        else batched_cell<float>(b, a, idx);
+    }
+}
+
+int resident_grid(const void *kern, int threads, int nwork)
+{
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        nsm = 1;
+        per_sm = 1;
+    }
+    const long long slots = (long long)std::max(per_sm, 1) * std::max(nsm, 1);
+    return (int)std::max(1LL, std::min<long long>(slots, nwork));
+}
+
+void launch_collide_stream_batched(const BatchBed *beds, BatchWork work, int step, cudaStream_t st)
+{
+    static const int grid = resident_grid((const void *)k_collide_stream_batched, kBatchTile, 1 << 30);
+    if (!work.count) return;
+    k_collide_stream_batched<<<grid, kBatchTile, 0, st>>>(beds, work.cell_tiles, work.count, step);
 }
 
 // ---------------------------------------------------------------------------

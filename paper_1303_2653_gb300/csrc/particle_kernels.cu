@@ -9,6 +9,8 @@
 // only for pairs that an FP32 test with a safety margin cannot exclude.
 #include "particle_common.cuh"
 
+#include <algorithm>
+
 namespace lbdpsk {
 
 // Cell of an FP64 position and the offset inside it (floor in FP64, clamped
@@ -162,20 +164,71 @@ template <int D, class Real> struct DetectOccupancy { static constexpr int value
 template <> struct DetectOccupancy<2, float> { static constexpr int value = 6; };
 template <> struct DetectOccupancy<3, float> { static constexpr int value = 5; };
 
-// SOFT: add the soft-sphere contact force of the step (p.fc) in Eq. 16
+// Members of cells that straddle a block boundary and lie in other blocks
+// ("foreign" members) are taken into the Eq. 27 sums of this block's members.
+// Up to kForeignPerThread of them, each member recomputes their pre-drags
+// itself; beyond that the block computes each one once, in chunks of
+// kForeignChunk in sorted order, into shared memory (crowded cells: a cell of
+// n members spread over several blocks then costs O(n) pre-drags instead of
+// O(n^2)).  Both give the same values in the same order.
+constexpr int kForeignPerThread = 8;
+constexpr int kForeignChunk = 256;
+
+// Adds to S and A (Eq. 27) the pre-drags of the foreign members [lo, hi) of
+// cell `cell`, computed once per block; `mine`: this thread's particle is a
+// member of that cell.  Block-uniform (every thread calls it).
+template <int D, class Real>
+__device__ __forceinline__ void foreign_sums(const StepParams<Real> &p, const Particles<Real> &parts,
+                                             const Fields<Real> &fld, int cell, int lo, int hi,
+                                             bool mine, Real (*sfor)[kForeignChunk], Real *S, Real *A)
+{
+    int idx[3] = {0, 0, 0};
+    cell_coords(D, p.n, cell, idx);
+    for (int base = lo; base < hi; base += kForeignChunk) {
+        const int cnt = min(kForeignChunk, hi - base);
+        __syncthreads();   // the previous chunk has been read
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            Real val[3], g2[3], vj[3], oj[3];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                vj[a] = __ldg(parts.v[a] + base + t);
+                oj[a] = __ldg(parts.off[a] + base + t);
+            }
+            drag_pre_one<D, Real>(p, parts, fld, idx, oj, vj, val, g2);
+#pragma unroll
+            for (int a = 0; a < D; ++a) sfor[a][t] = val[a];
+        }
+        __syncthreads();
+        if (mine) {
+            for (int t = 0; t < cnt; ++t) {
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    S[a] += sfor[a][t];
+                    A[a] += fabs(sfor[a][t]);
+                }
+            }
+        }
+    }
+}
+
+// SOFT: add the soft-sphere contact force of the step (p.fc) in Eq. 16.
+// The work of particle k in a thread block holding sorted slots
+// [block_first, block_end) (at most 256, block_first < np), whose pre-drags
+// it shares through sfp (sfor: room for foreign pre-drags); every thread of
+// the block calls it (it synchronises the block).
 template <int D, class Real, bool SOFT>
-__global__ void __launch_bounds__(256, DragOccupancy<D, Real>::value)
-k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, CellList cells,
-            Fields<Real> fld, int *__restrict__ key, int *__restrict__ counts, Real *diag_fpre,
-            Real *diag_fd, int np)
+__device__ __forceinline__ void drag_step_particle(const StepParams<Real> &p,
+                                                   const Particles<Real> &parts,
+                                                   const Particles<Real> &out, const CellList &cells,
+                                                   const Fields<Real> &fld, int *__restrict__ key,
+                                                   int *__restrict__ counts, Real *diag_fpre,
+                                                   Real *diag_fd, int np, int k, int block_first,
+                                                   int block_end, Real (*sfp)[256],
+                                                   Real (*sfor)[kForeignChunk])
 {
     // the integrated state goes to `out` (same slots): other blocks may still
     // read this particle's pre-step state to complete their cell sums
-    __shared__ Real sfp[D][256];   // pre-drag of the block's particles (blockDim <= 256)
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = k < np;
-    const int block_first = k - (int)threadIdx.x;
-    const int block_end = block_first + (int)blockDim.x;
     int c = -1, s0 = 0, s1 = 0;
     int idx[3] = {0, 0, 0};
     Real fp[3] = {Real(0), Real(0), Real(0)}, gp[3] = {Real(0), Real(0), Real(0)};
@@ -198,34 +251,56 @@ k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, Cell
         cell_coords(D, p.n, c, idx);
         drag_pre_one<D, Real>(p, parts, fld, idx, o0, v0, fp, gp);
 #pragma unroll
-        for (int a = 0; a < D; ++a) sfp[a][threadIdx.x] = fp[a];
+        for (int a = 0; a < D; ++a) sfp[a][k - block_first] = fp[a];
     }
     __syncthreads();
-    if (!active) return;
     // Eq. 27 in sorted order: members held by this block come from shared
-    // memory, the others are recomputed (bit-identical)
+    // memory, the others are recomputed (bit-identical).  Only the cells of
+    // the block's first and last particles can have foreign members.
+    const int last = min(block_end, np) - 1;
+    const int ch = __ldg(parts.cell + block_first), ct = __ldg(parts.cell + last);
+    const int h0 = cells.begin(ch), t1 = cells.begin(ct + 1);
+    const bool shared_foreign = (block_first - h0) + (t1 - (last + 1)) > kForeignPerThread;
     Real S[3] = {Real(0), Real(0), Real(0)}, A[3] = {Real(0), Real(0), Real(0)};
-    for (int j = s0; j < s1; ++j) {
-        Real val[3];
-        if (j >= block_first && j < block_end) {
+    if (shared_foreign) {
+        // head cell's foreign members (before the block), the block's own,
+        // then the tail cell's (after it): the sorted order of every cell
+        foreign_sums<D, Real>(p, parts, fld, ch, h0, block_first, active && c == ch, sfor, S, A);
+        if (active) {
+            const int lo = max(s0, block_first), hi = min(s1, last + 1);
+            for (int j = lo; j < hi; ++j) {
 #pragma unroll
-            for (int a = 0; a < D; ++a) val[a] = sfp[a][j - block_first];
-        } else {
-            Real g2[3], vj[3], oj[3];
+                for (int a = 0; a < D; ++a) {
+                    S[a] += sfp[a][j - block_first];
+                    A[a] += fabs(sfp[a][j - block_first]);
+                }
+            }
+        }
+        foreign_sums<D, Real>(p, parts, fld, ct, last + 1, t1, active && c == ct, sfor, S, A);
+        if (!active) return;
+    } else {
+        if (!active) return;
+        for (int j = s0; j < s1; ++j) {
+            Real val[3];
+            if (j >= block_first && j < block_end) {
+#pragma unroll
+                for (int a = 0; a < D; ++a) val[a] = sfp[a][j - block_first];
+            } else {
+                Real g2[3], vj[3], oj[3];
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    vj[a] = __ldg(parts.v[a] + j);
+                    oj[a] = __ldg(parts.off[a] + j);
+                }
+                drag_pre_one<D, Real>(p, parts, fld, idx, oj, vj, val, g2);
+            }
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                vj[a] = __ldg(parts.v[a] + j);
-                oj[a] = __ldg(parts.off[a] + j);
+                S[a] += val[a];
+                A[a] += fabs(val[a]);
             }
-            drag_pre_one<D, Real>(p, parts, fld, idx, oj, vj, val, g2);
-        }
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            S[a] += val[a];
-            A[a] += fabs(val[a]);
         }
     }
-    if (!active) return;
 
     Real v[3] = {Real(0), Real(0), Real(0)}, off[3] = {Real(0), Real(0), Real(0)};
     int q[3] = {0, 0, 0};
@@ -298,6 +373,20 @@ k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, Cell
     const int nk = q[0] + p.n[0] * (q[1] + p.n[1] * q[2]);
     key[k] = nk;
     atomicAdd(&counts[nk], 1);
+}
+
+template <int D, class Real, bool SOFT>
+__global__ void __launch_bounds__(256, DragOccupancy<D, Real>::value)
+k_drag_step(StepParams<Real> p, Particles<Real> parts, Particles<Real> out, CellList cells,
+            Fields<Real> fld, int *__restrict__ key, int *__restrict__ counts, Real *diag_fpre,
+            Real *diag_fd, int np)
+{
+    __shared__ Real sfp[D][256];   // pre-drag of the block's particles (blockDim <= 256)
+    __shared__ Real sfor[D][kForeignChunk];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int block_first = k - (int)threadIdx.x;
+    drag_step_particle<D, Real, SOFT>(p, parts, out, cells, fld, key, counts, diag_fpre, diag_fd,
+                                      np, k, block_first, block_first + (int)blockDim.x, sfp, sfor);
 }
 
 template <int D, class Real>
@@ -385,13 +474,13 @@ constexpr int kCellScanItems = kCellTile / kCellScanThreads;
 constexpr int kCellScanVec = kCellScanItems / 4;   // int4 loads per thread
 static_assert(kCellScanItems % 4 == 0, "whole int4 per thread");
 
-__global__ void __launch_bounds__(kCellScanThreads)
-k_cell_scan(const int *__restrict__ counts, CellListOut out, int n)
+// Tile `tile` of `nt` (one block of kCellScanThreads threads; every thread
+// calls it).
+__device__ __forceinline__ void cell_scan_tile(const int *__restrict__ counts, const CellListOut &out,
+                                               int n, int tile, int nt, int *warp_tot, int &total,
+                                               bool &last)
 {
-    __shared__ int warp_tot[32];
-    __shared__ int total;
-    __shared__ bool last;
-    const int base = blockIdx.x * kCellTile + threadIdx.x * kCellScanItems;
+    const int base = tile * kCellTile + threadIdx.x * kCellScanItems;
     // all of the thread's loads are issued before any is used
     int4 c4[kCellScanVec];
     const bool whole = base + kCellScanItems <= n;
@@ -425,16 +514,15 @@ k_cell_scan(const int *__restrict__ counts, CellListOut out, int n)
         }
     }
     if (threadIdx.x == 0) {
-        out.tile_total[blockIdx.x] = total;
+        out.tile_total[tile] = total;
         __threadfence();
         const unsigned done = atomicAdd(out.ticket, 1u);
-        last = (done == gridDim.x - 1);
+        last = (done == (unsigned)nt - 1u);
     }
     __syncthreads();
     if (!last) return;
     // the last block: exclusive scan of the tile totals into base[]
     __threadfence();
-    const int nt = gridDim.x;
     int carry = 0;
     for (int b0 = 0; b0 < nt; b0 += blockDim.x) {
         const int e = b0 + threadIdx.x;
@@ -448,6 +536,15 @@ k_cell_scan(const int *__restrict__ counts, CellListOut out, int n)
         out.base[nt] = carry;
         *out.ticket = 0u;
     }
+}
+
+__global__ void __launch_bounds__(kCellScanThreads)
+k_cell_scan(const int *__restrict__ counts, CellListOut out, int n)
+{
+    __shared__ int warp_tot[32];
+    __shared__ int total;
+    __shared__ bool last;
+    cell_scan_tile(counts, out, n, blockIdx.x, gridDim.x, warp_tot, total, last);
 }
 
 void launch_cell_scan(const int *counts, CellListOut out, int ncell, cudaStream_t st)
@@ -530,12 +627,10 @@ void launch_scan(const int *counts, int *cell_start, int *block_sums, int ncell,
 // made canonical: each slot ranks its particle among the cell's members by id
 // and the payload is gathered to begin(cell) + rank, the (cell, id) order.
 // ---------------------------------------------------------------------------
-__global__ void k_scatter(const int *__restrict__ key, const int *__restrict__ id,
-                          int *__restrict__ counts, CellList cells, int2 *__restrict__ slot,
-                          int *__restrict__ idslot, int np)
+__device__ __forceinline__ void scatter_one(const int *__restrict__ key, const int *__restrict__ id,
+                                            int *__restrict__ counts, const CellList &cells,
+                                            int2 *__restrict__ slot, int *__restrict__ idslot, int k)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= np) return;
     const int c = key[k];
     const int old = atomicSub(&counts[c], 1);
     const int s = cells.begin(c) + old - 1;
@@ -543,15 +638,22 @@ __global__ void k_scatter(const int *__restrict__ key, const int *__restrict__ i
     idslot[s] = id[k];
 }
 
+__global__ void k_scatter(const int *__restrict__ key, const int *__restrict__ id,
+                          int *__restrict__ counts, CellList cells, int2 *__restrict__ slot,
+                          int *__restrict__ idslot, int np)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    scatter_one(key, id, counts, cells, slot, idslot, k);
+}
+
 // The payload of the particle in slot s is loaded before its rank is known
 // (the loads do not wait on the rank loop), then stored at begin(c) + rank.
 template <int D, class Real>
-__global__ void __launch_bounds__(256)
-k_gather(CellList cells, const int2 *__restrict__ slot, const int *__restrict__ idslot,
-         Particles<Real> src, Particles<Real> dst, int np)
+__device__ __forceinline__ void gather_one(const CellList &cells, const int2 *__restrict__ slot,
+                                           const int *__restrict__ idslot, const Particles<Real> &src,
+                                           const Particles<Real> &dst, int s)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= np) return;
     const int2 kc = slot[s];
     const int my = idslot[s];
     constexpr int NW = D == 2 ? 1 : 3;   // spin components
@@ -587,6 +689,16 @@ k_gather(CellList cells, const int2 *__restrict__ slot, const int *__restrict__ 
     dst.cell[d] = kc.y;
 }
 
+template <int D, class Real>
+__global__ void __launch_bounds__(256)
+k_gather(CellList cells, const int2 *__restrict__ slot, const int *__restrict__ idslot,
+         Particles<Real> src, Particles<Real> dst, int np)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= np) return;
+    gather_one<D, Real>(cells, slot, idslot, src, dst, s);
+}
+
 template <class Real>
 void launch_place(int dim, const int *key, int *counts, CellList cells, int2 *slot, int *idslot,
                   Particles<Real> src, Particles<Real> dst, int np, cudaStream_t st)
@@ -615,13 +727,11 @@ void launch_place(int dim, const int *key, int *counts, CellList cells, int2 *sl
 // moving toward it).
 // ---------------------------------------------------------------------------
 template <int D, class Real>
-__global__ void __launch_bounds__(256, DetectOccupancy<D, Real>::value)
-k_detect(StepParams<Real> p, Particles<Real> parts, CellList cells, int *__restrict__ best_out,
-         int *__restrict__ wall_out, long long *pairs, unsigned long long *npairs,
-         long long pair_cap, int np)
+__device__ __forceinline__ void detect_one(const StepParams<Real> &p, const Particles<Real> &parts,
+                                           const CellList &cells, int *__restrict__ best_out,
+                                           int *__restrict__ wall_out, long long *pairs,
+                                           unsigned long long *npairs, long long pair_cap, int i)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np) return;
     int idx[3];
     cell_coords(D, p.n, parts.cell[i], idx);
     float oi[3] = {0.f, 0.f, 0.f};
@@ -693,6 +803,17 @@ k_detect(StepParams<Real> p, Particles<Real> parts, CellList cells, int *__restr
 }
 
 template <int D, class Real>
+__global__ void __launch_bounds__(256, DetectOccupancy<D, Real>::value)
+k_detect(StepParams<Real> p, Particles<Real> parts, CellList cells, int *__restrict__ best_out,
+         int *__restrict__ wall_out, long long *pairs, unsigned long long *npairs,
+         long long pair_cap, int np)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    detect_one<D, Real>(p, parts, cells, best_out, wall_out, pairs, npairs, pair_cap, i);
+}
+
+template <int D, class Real>
 void launch_detect(const StepParams<Real> &p, Particles<Real> parts, CellList cells, int *best,
                    int *wall, long long *pairs, unsigned long long *npairs, long long pair_cap,
                    int np, cudaStream_t st)
@@ -711,12 +832,10 @@ void launch_detect(const StepParams<Real> &p, Particles<Real> parts, CellList ce
 // v_n -> -e v_n).
 // ---------------------------------------------------------------------------
 template <int D, class Real>
-__global__ void __launch_bounds__(256)
-k_resolve(StepParams<Real> p, Particles<Real> parts, const int *__restrict__ best,
-          const int *__restrict__ wall, int np)
+__device__ __forceinline__ void resolve_one(const StepParams<Real> &p, const Particles<Real> &parts,
+                                            const int *__restrict__ best,
+                                            const int *__restrict__ wall, int i)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np) return;
     const int j = best[i];
     const bool mutual = (j >= 0) && (best[j] == i);
     if (mutual) {
@@ -745,6 +864,16 @@ k_resolve(StepParams<Real> p, Particles<Real> parts, const int *__restrict__ bes
 #pragma unroll
     for (int a = 0; a < D; ++a)
         if (bits & (3 << (2 * a))) parts.v[a][i] = -p.e * parts.v[a][i];
+}
+
+template <int D, class Real>
+__global__ void __launch_bounds__(256)
+k_resolve(StepParams<Real> p, Particles<Real> parts, const int *__restrict__ best,
+          const int *__restrict__ wall, int np)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    resolve_one<D, Real>(p, parts, best, wall, i);
 }
 
 template <int D, class Real>
@@ -803,6 +932,160 @@ void launch_overlaps(const StepParams<Real> &p, Particles<Real> parts, CellList 
 {
     if (np == 0) return;
     k_overlaps<D, Real><<<(np + 255) / 256, 256, 0, st>>>(p, parts, cells, count, first, np);
+}
+
+// ---------------------------------------------------------------------------
+// Batched particle kernels of the serving loop.  Persistent blocks walk a
+// work table of (bed, tile) entries; a block takes the whole entry, so the
+// block-wide steps (the drag's shared pre-drags, the scan's tile) see one
+// bed only.  Each entry runs the per-particle (per-tile) work of the
+// single-bed kernels with its bed's buffers for the parity of this step, so a
+// bed's results do not depend on the other beds of the batch.
+// ---------------------------------------------------------------------------
+struct BatchEntry {
+    const BatchBed *b;
+    int a;       // parity of the step's input buffers
+    int tile;
+};
+
+__device__ __forceinline__ bool batch_entry(const BatchBed *__restrict__ beds,
+                                            const int2 *__restrict__ work, int w, int step,
+                                            BatchEntry &out)
+{
+    const int2 e = work[w];
+    const BatchBed &b = beds[e.x];
+    if (step >= b.nsteps) return false;
+    out.b = &b;
+    out.a = (b.parity0 + step) & 1;
+    out.tile = e.y;
+    return true;
+}
+
+__global__ void __launch_bounds__(kBatchTile, DragOccupancy<2, float>::value)
+k_drag_batched(const BatchBed *__restrict__ beds, const int2 *__restrict__ work,
+               const int *__restrict__ count, int step)
+{
+    __shared__ float sfp[2][256];
+    __shared__ float sfor[2][kForeignChunk];
+    const int nwork = *count;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        BatchEntry e;
+        if (!batch_entry(beds, work, w, step, e)) continue;   // the same for the whole block
+        const BatchBed &b = *e.b;
+        const int first = e.tile * kBatchTile;
+        const CellList cells{b.cl_local[e.a], b.cl_base[e.a]};
+        __syncthreads();   // the previous entry's readers of sfp are done
+        drag_step_particle<2, float, false>(b.sp, b.part[e.a], b.stage, cells, b.fld, b.key,
+                                            b.counts, b.diag_fpre, b.diag_fd, b.np,
+                                            first + (int)threadIdx.x, first, first + kBatchTile, sfp,
+                                            sfor);
+    }
+}
+
+__global__ void __launch_bounds__(kCellScanThreads)
+k_cell_scan_batched(const BatchBed *__restrict__ beds, const int2 *__restrict__ work,
+                    const int *__restrict__ count, int step)
+{
+    __shared__ int warp_tot[32];
+    __shared__ int total;
+    __shared__ bool last;
+    const int nwork = *count;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        BatchEntry e;
+        if (!batch_entry(beds, work, w, step, e)) continue;
+        const BatchBed &b = *e.b;
+        const int nb = 1 - e.a;
+        const CellListOut out{b.cl_local[nb], b.cl_base[nb], b.tile_total, b.ticket};
+        const int nt = (b.ncell + 1 + kCellTile - 1) / kCellTile;
+        __syncthreads();   // the previous entry's users of the shared words are done
+        cell_scan_tile(b.counts, out, b.ncell + 1, e.tile, nt, warp_tot, total, last);
+    }
+}
+
+__global__ void __launch_bounds__(kBatchTile)
+k_scatter_batched(const BatchBed *__restrict__ beds, const int2 *__restrict__ work,
+                  const int *__restrict__ count, int step)
+{
+    const int nwork = *count;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        BatchEntry e;
+        if (!batch_entry(beds, work, w, step, e)) continue;
+        const BatchBed &b = *e.b;
+        const int k = e.tile * kBatchTile + (int)threadIdx.x;
+        if (k >= b.np) continue;
+        const int nb = 1 - e.a;
+        scatter_one(b.key, b.part[e.a].id, b.counts, CellList{b.cl_local[nb], b.cl_base[nb]}, b.slot,
+                    b.idslot, k);
+    }
+}
+
+__global__ void __launch_bounds__(kBatchTile)
+k_gather_batched(const BatchBed *__restrict__ beds, const int2 *__restrict__ work,
+                 const int *__restrict__ count, int step)
+{
+    const int nwork = *count;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        BatchEntry e;
+        if (!batch_entry(beds, work, w, step, e)) continue;
+        const BatchBed &b = *e.b;
+        const int s = e.tile * kBatchTile + (int)threadIdx.x;
+        if (s >= b.np) continue;
+        const int nb = 1 - e.a;
+        Particles<float> src = b.stage;
+        src.id = b.part[e.a].id;
+        gather_one<2, float>(CellList{b.cl_local[nb], b.cl_base[nb]}, b.slot, b.idslot, src,
+                             b.part[nb], s);
+    }
+}
+
+__global__ void __launch_bounds__(kBatchTile, DetectOccupancy<2, float>::value)
+k_detect_batched(const BatchBed *__restrict__ beds, const int2 *__restrict__ work,
+                 const int *__restrict__ count, int step)
+{
+    const int nwork = *count;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        BatchEntry e;
+        if (!batch_entry(beds, work, w, step, e)) continue;
+        const BatchBed &b = *e.b;
+        const int i = e.tile * kBatchTile + (int)threadIdx.x;
+        if (i >= b.np) continue;
+        const int nb = 1 - e.a;
+        detect_one<2, float>(b.sp, b.part[nb], CellList{b.cl_local[nb], b.cl_base[nb]}, b.best,
+                             b.wall, nullptr, nullptr, 0, i);
+    }
+}
+
+__global__ void __launch_bounds__(kBatchTile)
+k_resolve_batched(const BatchBed *__restrict__ beds, const int2 *__restrict__ work,
+                  const int *__restrict__ count, int step)
+{
+    const int nwork = *count;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        BatchEntry e;
+        if (!batch_entry(beds, work, w, step, e)) continue;
+        const BatchBed &b = *e.b;
+        const int i = e.tile * kBatchTile + (int)threadIdx.x;
+        if (i >= b.np) continue;
+        resolve_one<2, float>(b.sp, b.part[1 - e.a], b.best, b.wall, i);
+    }
+}
+
+void launch_particles_batched(const BatchBed *beds, BatchWork work, int step, cudaStream_t st)
+{
+    static const int g_drag = resident_grid((const void *)k_drag_batched, kBatchTile, 1 << 30);
+    static const int g_scan = resident_grid((const void *)k_cell_scan_batched, kCellScanThreads, 1 << 30);
+    static const int g_scat = resident_grid((const void *)k_scatter_batched, kBatchTile, 1 << 30);
+    static const int g_gath = resident_grid((const void *)k_gather_batched, kBatchTile, 1 << 30);
+    static const int g_det = resident_grid((const void *)k_detect_batched, kBatchTile, 1 << 30);
+    static const int g_res = resident_grid((const void *)k_resolve_batched, kBatchTile, 1 << 30);
+    if (!work.count) return;
+    const int *n_scan = work.count + 1, *n_part = work.count + 2;
+    k_drag_batched<<<g_drag, kBatchTile, 0, st>>>(beds, work.part_tiles, n_part, step);
+    k_cell_scan_batched<<<g_scan, kCellScanThreads, 0, st>>>(beds, work.scan_tiles, n_scan, step);
+    k_scatter_batched<<<g_scat, kBatchTile, 0, st>>>(beds, work.part_tiles, n_part, step);
+    k_gather_batched<<<g_gath, kBatchTile, 0, st>>>(beds, work.part_tiles, n_part, step);
+    k_detect_batched<<<g_det, kBatchTile, 0, st>>>(beds, work.part_tiles, n_part, step);
+    k_resolve_batched<<<g_res, kBatchTile, 0, st>>>(beds, work.part_tiles, n_part, step);
 }
 
 // ---------------------------------------------------------------------------

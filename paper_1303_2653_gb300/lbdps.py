@@ -134,6 +134,9 @@ def lib():
             "lbdps_server_load": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz)], i),
             "lbdps_server_take": ([vp, ctypes.c_uint64, ctypes.POINTER(vp)], i),
             "lbdps_server_destroy": ([vp], None),
+            "lbdps_server_set_batching": ([vp, i, i64], i),
+            "lbdps_server_batch_info": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                         ctypes.POINTER(i)], i),
             "lbdps_bin_sort_noalloc": ([i, ctypes.POINTER(i), i64, ctypes.POINTER(vp), vp, vp, vp], i),
             "lbdps_strerror": ([i], ctypes.c_char_p),
             "lbdps_last_error": ([], ctypes.c_char_p),
@@ -454,11 +457,14 @@ class Server:
     include/lbdps.h).  Beds get their own CUDA streams and device memory from
     cudaMalloc inside the library; the budget bounds their total footprint."""
 
-    def __init__(self, hbm_budget: int, max_active: int = 64, steps_per_tick: int = 16):
+    def __init__(self, hbm_budget: int, max_active: int = 64, steps_per_tick: int = 16,
+                 batching: bool = True, batch_max_cells: int = 0):
         h = ctypes.c_void_p()
         _check(lib().lbdps_server_create(int(hbm_budget), int(max_active), int(steps_per_tick),
                                          ctypes.byref(h)), "lbdps_server_create")
         self._h = h
+        _check(lib().lbdps_server_set_batching(self._h, int(bool(batching)), int(batch_max_cells)),
+               "lbdps_server_set_batching")
         self._workloads = {}
         self._callbacks = []
 
@@ -500,6 +506,13 @@ class Server:
         _check(lib().lbdps_server_load(self._h, ctypes.byref(q), ctypes.byref(a), ctypes.byref(u)),
                "lbdps_server_load")
         return q.value, a.value, u.value
+
+    def batch_info(self):
+        """(ticks launched, graph captures, current members) of the batch."""
+        t, c, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(lib().lbdps_server_batch_info(self._h, ctypes.byref(t), ctypes.byref(c),
+                                             ctypes.byref(m)), "lbdps_server_batch_info")
+        return t.value, c.value, m.value
 
     def take(self, req_id: int) -> Bed:
         h = ctypes.c_void_p()

@@ -294,6 +294,50 @@ def test_detection_pairs_bit_exact(dim, storage):
 
 
 @pytest.mark.parametrize("storage", [W.STORE_F64, W.STORE_F32])
+def test_one_step_parity_piled_cells(storage):
+    # hard spheres piled into a few cells (hundreds of centres each, as in a
+    # settled bubbling bed): a cell's members then span several thread
+    # blocks of the drag kernel, whose Eq. 27 sums take the pre-drags of the
+    # other blocks' members from a block-shared pass; one step against the
+    # oracle, every particle at the stated bound in FP64
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from test_oracle_pins import _counted_bed
+    L = _lb()
+    rng = np.random.default_rng(21)
+    counts = rng.integers(0, 5, size=(24, 16))
+    w = _counted_bed(counts, storage=storage)
+    spread = w.pos / w.h
+    piles = [((5, 3), 700), ((6, 3), 300), ((12, 9), 520), ((0, 20), 280)]
+    P = [spread]
+    for (cx, cy), m in piles:
+        P.append(np.array([cx, cy]) + rng.uniform(0.02, 0.98, size=(m, 2)))
+    P = np.concatenate(P)
+    V = rng.normal(scale=3e-3, size=P.shape)
+    # created apart (no overlaps at creation), then moved into the piles
+    n_total = len(P)
+    apart = np.array([[x + 0.125 + 0.25 * (k % 4), y + 0.125 + 0.25 * (k // 4)]
+                      for y in range(24) for x in range(16) for k in range(16)])[:n_total]
+    assert len(apart) == n_total
+    w = w.with_(pos=apart * w.h, vel=np.zeros_like(apart))
+    bed = L.Bed(w, storage=storage, diagnostics=True)
+    bed.set_particles(P, V)
+    ob = O.OracleBed(w)
+    ob.set_populations(bed.populations())
+    Pg, Vg = bed.particles()
+    ob.set_particles(Pg, Vg)
+    c0 = np.floor(Pg).astype(np.int64)
+    cell0 = c0[:, 0] + w.n[0] * c0[:, 1]
+    assert np.bincount(cell0).max() >= 700
+    _compare_step(bed, ob, storage)
+    Pg, vg, Po, vo, fd_g, fd_o, kappa_cell = _particle_compare(bed, ob, storage)
+    _check_drag_and_motion(w, storage, cell0, Pg, vg, Po, vo, fd_g, fd_o, kappa_cell)
+    assert bed.check_guards() == 0
+    bed.close()
+
+
+@pytest.mark.parametrize("storage", [W.STORE_F64, W.STORE_F32])
 def test_partner_ties_on_gpu(storage):
     # Reading R14 on the device: among approaching contacts at exactly the
     # same distance the partner of smaller id is chosen.  Coordinates and

@@ -46,7 +46,12 @@ def _drain(server, want, max_polls=200000):
     raise AssertionError("server did not finish")
 
 
-def test_result_alone_equals_mix_and_direct():
+@pytest.mark.parametrize("batching", [True, False])
+def test_result_alone_equals_mix_and_direct(batching):
+    # batching on: the 2D FP32 / FP16 beds advance in the batched kernels
+    # (one launch per kernel class over all of them), the 3D bed on its own
+    # stream; off: every bed on its own stream.  A tick of 5 steps (odd) moves
+    # the buffer parity at every tick.
     L = _lb()
     beds = _mix()
     target, K = beds[0], 47
@@ -56,7 +61,7 @@ def test_result_alone_equals_mix_and_direct():
     P_d, v_d = direct.particles()
     direct.close()
 
-    s = L.Server(hbm_budget=4 << 30, max_active=8, steps_per_tick=5)
+    s = L.Server(hbm_budget=4 << 30, max_active=8, steps_per_tick=5, batching=batching)
     rid = s.submit(target, K, keep=True)
     assert _drain(s, {rid})[rid]["status"] == 0
     alone = s.take(rid)
@@ -77,8 +82,71 @@ def test_result_alone_equals_mix_and_direct():
     P_m, v_m = mixed.particles()
     np.testing.assert_array_equal(P_m, P_d)
     np.testing.assert_array_equal(v_m, v_d)
+    # the handle taken from the server steps on by itself like the direct bed
+    mixed.step(3)
+    direct = L.Bed(target)
+    direct.step(K + 3)
+    np.testing.assert_array_equal(mixed.populations(), direct.populations())
+    direct.close()
     mixed.close()
+    ticks, captures, members = s.batch_info()
+    if batching:
+        assert ticks > 0 and captures >= 1
+    else:
+        assert ticks == 0
     s.close()
+
+
+def test_batched_beds_equal_beds_alone():
+    # many small beds of both kinds, three storage formats, LES on and off,
+    # particle counts from 0 up, different step counts, all admitted at once
+    # into the batch: each equals the same bed stepped alone, bit for bit
+    L = _lb()
+    beds = [W.scaled_riser2d(nx=48, ny=64, seed=51),
+            W.scaled_riser2d(nx=40, ny=96, seed=52, storage=W.STORE_F16, cs_smag=0.1),
+            W.scaled_riser2d(nx=64, ny=32, seed=53, storage=W.STORE_BF16),
+            W.bubbling2d(nx=32, ny=64, n_particles=400, seed=54, storage=W.STORE_F32, cs_smag=0.1),
+            W.bubbling2d(nx=24, ny=40, n_particles=150, seed=55, storage=W.STORE_F16),
+            W.channel2d(nx=16, ny=8, h=1.0, dt=1.0, nu=0.05, body_accel=1e-6, storage=W.STORE_F32),
+            W.riser2d(nx=100, ny=130, n_particles=3000, seed=56, storage=W.STORE_F32)]
+    steps = [37, 64, 20, 45, 9, 30, 33]
+    s = L.Server(hbm_budget=8 << 30, max_active=16, steps_per_tick=8)
+    ids = [s.submit(w, k, keep=True) for w, k in zip(beds, steps)]
+    done = _drain(s, set(ids))
+    assert all(done[i]["status"] == 0 for i in ids)
+    ticks, captures, members = s.batch_info()
+    assert ticks >= 8 and captures == 1
+    for w, k, rid in zip(beds, steps, ids):
+        got = s.take(rid)
+        ref = L.Bed(w)
+        ref.step(k)
+        np.testing.assert_array_equal(got.populations(), ref.populations(), err_msg=w.name)
+        Pg, vg = got.particles()
+        Pr, vr = ref.particles()
+        np.testing.assert_array_equal(Pg, Pr)
+        np.testing.assert_array_equal(vg, vr)
+        assert got.stats()["steps"] == k
+        got.close()
+        ref.close()
+    s.close()
+
+
+def test_batch_membership_rule():
+    # a bed above the size limit, or with more particles than cells, keeps its
+    # own stream; lowering the limit sends the small bed there too
+    L = _lb()
+    small = W.scaled_riser2d(nx=48, ny=64, seed=61)
+    dense = W.riser2d(nx=32, ny=32, n_particles=1100, seed=62, h=1.322e-4)
+    assert dense.n_particles > dense.ncell
+    for max_cells, batched in ((0, True), (1000, False)):
+        s = L.Server(hbm_budget=4 << 30, max_active=8, steps_per_tick=4, batch_max_cells=max_cells)
+        ids = [s.submit(small, 12), s.submit(dense, 12)]
+        s.poll(wait_s=0.0)
+        _, _, members = s.batch_info()
+        assert members == (1 if batched else 0)
+        done = _drain(s, set(ids))
+        assert all(done[i]["status"] == 0 for i in ids)
+        s.close()
 
 
 def test_admission_stays_within_budget():
