@@ -70,7 +70,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=96)
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--max-active", type=int, default=128)
-    ap.add_argument("--steps-per-tick", type=int, default=32)
+    ap.add_argument("--steps-per-tick", type=int, default=8)
+    ap.add_argument("--no-serving", action="store_true",
+                    help="leave the short serving summary out of the default bench line")
     ap.add_argument("--precision", action="store_true",
                     help="per-field error of FP32/FP16/BF16 storage against the FP64 oracle")
     ap.add_argument("--precision-steps", type=int, default=1000)
@@ -391,6 +393,7 @@ def main():
     import __graft_entry__ as ge
     ge.build()
     from paper_1303_2653_gb300 import lbdps as L
+    from paper_1303_2653_gb300 import workloads as W
 
     torch.cuda.set_device(local)
     if args.profile_steps:
@@ -419,6 +422,15 @@ def main():
                      "particle_updates_per_s": r2["particle_updates_per_s"],
                      "roofline": r2["roofline"], "whole_step": r2["whole_step"],
                      "health": r2["health"]}
+
+    # ---- a short serving run (rank 0, N = 1): 32 requests of the serving
+    # stream, batched, on per-bed streams, and one by one in plain FP32 ----
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        reqs = serving_requests(32, args.rate)
+        free, _ = torch.cuda.mem_get_info()
+        serving = serving_summary(L, W, reqs, int(0.5 * free), args.max_active,
+                                  args.steps_per_tick)
 
     # ---- CPU oracle on the host cores (rank 0, N = 1) ----
     cpu = None
@@ -450,6 +462,8 @@ def main():
                 "particle_updates_per_s": res["particle_updates_per_s"]}
         if secondary:
             line["riser2d"] = secondary
+        if serving:
+            line["serving"] = serving
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -703,7 +717,24 @@ def serving_main(args):
             "rate_per_s": args.rate, "data": "synthetic", "budget_bytes": budget,
             "max_active": args.max_active, "steps_per_tick": args.steps_per_tick}
     line.update(summ)
+    line["small_beds"] = small_beds_summary(L, W, budget, args.max_active, args.steps_per_tick)
     print(json.dumps(line), flush=True)
+
+
+def small_beds_summary(L, W, budget, max_active, steps_per_tick, n=64, steps=500):
+    """n small riser beds (64 x 128, about 3,100 particles, FP32 and FP16
+    alternating, C_s = 0.1) submitted at once: the case the batched kernels
+    are for (each bed's own launches are latency-bound)."""
+    reqs = [(0.0, W.scaled_riser2d(nx=64, ny=128, seed=1303300 + i, steps=steps, cs_smag=0.1,
+                                   storage=W.STORE_F16 if i % 2 else W.STORE_F32))
+            for i in range(n)]
+    work = sum(w.ncell * w.steps for _, w in reqs)
+    out = {"beds": n, "cells_per_bed": reqs[0][1].ncell, "steps": steps}
+    for key, batching in (("batched", True), ("streams", False)):
+        lat, done, makespan, info = serve(L, reqs, budget, max_active, steps_per_tick, batching)
+        out[key] = {"aggregate_mlups": work / makespan / 1e6, "makespan_s": makespan,
+                    "failed": sum(1 for r in done.values() if r["status"] != 0)}
+    return out
 
 
 

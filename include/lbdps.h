@@ -383,7 +383,7 @@ int lbdps_server_take(lbdps_server_t *s, uint64_t req_id, lbdps_t **out);
  * CUDA graph.  Each bed's arithmetic is that of the bed run alone.  Larger
  * or denser beds, and beds of other kinds, advance on streams of their own
  * by replays of their own step graphs.  on = 0: every bed on its own stream.
- * max_cells = 0 keeps the default (131072 cells).  Applies to beds admitted
+ * max_cells = 0 keeps the default (32768 cells).  Applies to beds admitted
  * afterwards; LBDPS_ERR_INVALID for max_cells < 0. */
 int lbdps_server_set_batching(lbdps_server_t *s, int on, int64_t max_cells);
 /* Counters of the batch: ticks launched, graph captures, current members. */

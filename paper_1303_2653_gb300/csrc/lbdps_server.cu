@@ -95,10 +95,12 @@ struct Batch {
     int64_t done_ticks = 0;            // ticks known to have completed
 };
 
-// Beds up to this many cells may join the batch: above it a bed's own
-// kernels fill the GPU, and the batched kernels (which load each bed's
-// parameters from device memory) only add to its cost.
-constexpr int kBatchMaxCells = 1 << 17;
+// Beds up to this many cells may join the batch.  The batched kernels load
+// each bed's parameters from device memory and cost 1.3-1.9x the single-bed
+// kernels per bed-step, so batching pays where a bed's own launches are
+// dominated by launch and dependent-load latency: on a GB300 the crossover
+// measured on the mixed serving stream lies between 32,768 and 131,072 cells.
+constexpr int kBatchMaxCells = 1 << 15;
 
 int sfail(int code, const char *msg)
 {
