@@ -253,16 +253,19 @@ __device__ __forceinline__ void drag_step_particle(const StepParams<Real> &p,
 #pragma unroll
         for (int a = 0; a < D; ++a) sfp[a][k - block_first] = fp[a];
     }
-    __syncthreads();
     // Eq. 27 in sorted order: members held by this block come from shared
-    // memory, the others are recomputed (bit-identical).  Only the cells of
-    // the block's first and last particles can have foreign members.
-    const int last = min(block_end, np) - 1;
-    const int ch = __ldg(parts.cell + block_first), ct = __ldg(parts.cell + last);
-    const int h0 = cells.begin(ch), t1 = cells.begin(ct + 1);
-    const bool shared_foreign = (block_first - h0) + (t1 - (last + 1)) > kForeignPerThread;
+    // memory, the others are recomputed (bit-identical).  The block shares
+    // the foreign pre-drags when a member's cell has more than a few (only
+    // the cells of the block's first and last particles can have any).
+    const int last = min(block_end, np) - 1;   // the block's last particle
+    const int own_foreign = active ? (s0 < block_first ? block_first - s0 : 0) +
+                                         (s1 > last + 1 ? s1 - (last + 1) : 0)
+                                   : 0;
+    const bool shared_foreign = __syncthreads_or(own_foreign > kForeignPerThread) != 0;
     Real S[3] = {Real(0), Real(0), Real(0)}, A[3] = {Real(0), Real(0), Real(0)};
     if (shared_foreign) {
+        const int ch = __ldg(parts.cell + block_first), ct = __ldg(parts.cell + last);
+        const int h0 = cells.begin(ch), t1 = cells.begin(ct + 1);
         // head cell's foreign members (before the block), the block's own,
         // then the tail cell's (after it): the sorted order of every cell
         foreign_sums<D, Real>(p, parts, fld, ch, h0, block_first, active && c == ch, sfor, S, A);
