@@ -176,6 +176,30 @@ struct DeviceAlloc {
         *bad = n;
         return 0;
     }
+    // a block for the duration of one call (no guard zone); give it back
+    // with put_temp once the stream no longer uses it
+    void *get_temp(size_t bytes)
+    {
+        bytes = (bytes + 255) & ~size_t(255);
+        void *p = nullptr;
+        if (alloc) {
+            p = alloc(bytes, ctx);
+            if (p && ((uintptr_t)p & 255u)) {
+                release(p, ctx);
+                p = nullptr;
+            }
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return p;
+    }
+    void put_temp(void *p)
+    {
+        if (!p) return;
+        if (release) release(p, ctx);
+        else cudaFree(p);
+    }
     void release_all()
     {
         if (count_only) return;
@@ -525,6 +549,32 @@ template <class L, class Real, class S> struct EngineT : Engine {
         const int np = H->np;
         const int cur = H->parity, nxt = 1 - cur;
         if (np == 0) return LBDPS_OK;
+        // one copy per array from the caller's memory, split per axis on the
+        // device (ids in order, spins at rest), then sorted into the current
+        // buffers
+        const size_t bytes = sizeof(double) * (size_t)np * D;
+        double *dp = (double *)H->mem.get_temp(bytes);
+        double *dv = dp ? (double *)H->mem.get_temp(bytes) : nullptr;
+        if (dp && dv) {
+            cudaError_t e = cudaMemcpyAsync(dp, pos, bytes, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dv, vel, bytes, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) {
+                launch_particles_from_host_order<D, Real>(dp, dv, np, part[nxt], st);
+                e = cudaGetLastError();
+            }
+            const cudaError_t e2 = cudaStreamSynchronize(st);
+            H->mem.put_temp(dp);
+            H->mem.put_temp(dv);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                cudaGetLastError();
+                return fail(LBDPS_ERR_CUDA, "particle upload: %s",
+                            cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            return sort_from(nxt, cur);
+        }
+        // no room for the staging arrays: split per axis on the host
+        H->mem.put_temp(dp);
+        H->mem.put_temp(dv);
         std::vector<double> Pa((size_t)np);
         std::vector<Real> va((size_t)np);
         std::vector<int> ids((size_t)np);
@@ -782,13 +832,37 @@ template <class L, class Real, class S> struct EngineT : Engine {
         const int np = H->np, cur = H->parity;
         if (cap < np) return fail(LBDPS_ERR_CAPACITY, "need room for %d particles", np);
         if (np == 0) return LBDPS_OK;
+        const double ps = units == LBDPS_UNITS_SI ? H->h : 1.0;
+        const double vs = units == LBDPS_UNITS_SI ? H->h / H->dt : 1.0;
+        // on the device: id order, interleaved, scaled; one copy per array
+        // into the caller's memory
+        const size_t bytes = sizeof(double) * (size_t)np * D;
+        double *dp = pos ? (double *)H->mem.get_temp(bytes) : nullptr;
+        double *dv = vel ? (double *)H->mem.get_temp(bytes) : nullptr;
+        if ((!pos || dp) && (!vel || dv)) {
+            cudaStream_t st = H->stream;
+            launch_particles_to_host_order<D, Real>(part[cur], np, ps, vs, dp, dv, st);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess && pos) e = cudaMemcpyAsync(pos, dp, bytes, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess && vel) e = cudaMemcpyAsync(vel, dv, bytes, cudaMemcpyDeviceToHost, st);
+            const cudaError_t e2 = cudaStreamSynchronize(st);
+            H->mem.put_temp(dp);
+            H->mem.put_temp(dv);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                cudaGetLastError();
+                return fail(LBDPS_ERR_CUDA, "particle read-back: %s",
+                            cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            return LBDPS_OK;
+        }
+        // no room for the staging arrays: copy per axis and order on the host
+        H->mem.put_temp(dp);
+        H->mem.put_temp(dv);
         std::vector<int> ids;
         std::vector<double> Pd;
         std::vector<Real> vd;
         int rc = d2h(ids, part[cur].id, np);
         if (rc) return rc;
-        const double ps = units == LBDPS_UNITS_SI ? H->h : 1.0;
-        const double vs = units == LBDPS_UNITS_SI ? H->h / H->dt : 1.0;
         for (int a = 0; a < D; ++a) {
             if ((rc = d2h(Pd, part[cur].P[a], np))) return rc;
             if ((rc = d2h(vd, part[cur].v[a], np))) return rc;

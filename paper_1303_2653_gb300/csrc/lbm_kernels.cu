@@ -584,28 +584,33 @@ void launch_collide_stream_batched(const BatchBed *beds, BatchWork work, int ste
 // pulls).
 // ---------------------------------------------------------------------------
 template <class L, class Real, class S>
-__global__ void k_init_equilibrium(long long nce, Real u0x, Real u0y, Real u0z, S *f)
+__global__ void __launch_bounds__(256) k_init_equilibrium(long long nce, Real u0x, Real u0y,
+                                                          Real u0z, S *f)
 {
-    // a uniform state: every slot of direction i holds the same deviation
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nce) return;
-    const double u[3] = {(double)u0x, (double)u0y, (double)u0z};
-    double uu = 0.0;
-    for (int a = 0; a < L::D; ++a) uu += u[a] * u[a];
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        double cu = 0.0;
+    // a uniform state: every slot of direction i holds the same deviation,
+    // evaluated once per block in FP64 (slow on this part) and then stored
+    __shared__ S dev[L::Q];
+    if (threadIdx.x < L::Q) {
+        const int i = threadIdx.x;
+        const double u[3] = {(double)u0x, (double)u0y, (double)u0z};
+        double uu = 0.0, cu = 0.0;
+        for (int a = 0; a < L::D; ++a) uu += u[a] * u[a];
         for (int a = 0; a < L::D; ++a) cu += (double)L::c(i, a) * u[a];
-        double dev = L::w(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-        f[(long long)i * nce + k] = Store<S>::save((Real)dev);
+        dev[i] = Store<S>::save((Real)(L::w(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu)));
+    }
+    __syncthreads();
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nce;
+         k += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) f[(long long)i * nce + k] = dev[i];
     }
 }
 
 template <class L, class Real, class S>
 void launch_init_equilibrium(const PopLayout &lay, const Real *u0, S *f, cudaStream_t st)
 {
-    k_init_equilibrium<L, Real, S><<<(unsigned)((lay.nce + 255) / 256), 256, 0, st>>>(
-        lay.nce, u0[0], u0[1], u0[2], f);
+    const long long blocks = std::min<long long>((lay.nce + 255) / 256, 152LL * 16);
+    k_init_equilibrium<L, Real, S><<<(unsigned)blocks, 256, 0, st>>>(lay.nce, u0[0], u0[1], u0[2], f);
 }
 
 template <class L>

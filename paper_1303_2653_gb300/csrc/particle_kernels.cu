@@ -435,6 +435,56 @@ void launch_cell_keys(const int *n, Particles<Real> parts, int *key, int *counts
     k_cell_keys<D, Real><<<(np + 255) / 256, 256, 0, st>>>(n[0], n[1], n[2], parts, key, counts, np);
 }
 
+// The particle state in id order for the host (interleaved, scaled to the
+// caller's units), and back.
+template <int D, class Real>
+__global__ void k_particles_to_host_order(Particles<Real> parts, int np, double ps, double vs,
+                                          double *pos, double *vel)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const size_t o = (size_t)parts.id[k] * D;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        if (pos) pos[o + a] = parts.P[a][k] * ps;
+        if (vel) vel[o + a] = (double)parts.v[a][k] * vs;
+    }
+}
+
+template <int D, class Real>
+void launch_particles_to_host_order(Particles<Real> parts, int np, double ps, double vs,
+                                    double *pos, double *vel, cudaStream_t st)
+{
+    if (np == 0) return;
+    k_particles_to_host_order<D, Real><<<(np + 255) / 256, 256, 0, st>>>(parts, np, ps, vs, pos, vel);
+}
+
+template <int D, class Real>
+__global__ void k_particles_from_host_order(const double *pos, const double *vel, int np,
+                                            Particles<Real> dst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    constexpr int NW = D == 2 ? 1 : 3;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        dst.P[a][i] = pos[(size_t)i * D + a];
+        dst.v[a][i] = (Real)vel[(size_t)i * D + a];
+    }
+    dst.id[i] = i;
+    if (dst.w[0])
+#pragma unroll
+        for (int c = 0; c < NW; ++c) dst.w[c][i] = Real(0);
+}
+
+template <int D, class Real>
+void launch_particles_from_host_order(const double *pos, const double *vel, int np,
+                                      Particles<Real> dst, cudaStream_t st)
+{
+    if (np == 0) return;
+    k_particles_from_host_order<D, Real><<<(np + 255) / 256, 256, 0, st>>>(pos, vel, np, dst);
+}
+
 // ---------------------------------------------------------------------------
 // Block-wide exclusive scan helper (warp shuffles, then the warp totals).
 // ---------------------------------------------------------------------------
@@ -1103,6 +1153,10 @@ void launch_particles_batched(const BatchBed *beds, BatchWork work, int step, cu
                                        const int *, int, cudaStream_t);                            \
     template void launch_cell_keys<D, R>(const int *, Particles<R>, int *, int *, int,              \
                                          cudaStream_t);                                             \
+    template void launch_particles_to_host_order<D, R>(Particles<R>, int, double, double, double *, \
+                                                       double *, cudaStream_t);                    \
+    template void launch_particles_from_host_order<D, R>(const double *, const double *, int,       \
+                                                         Particles<R>, cudaStream_t);              \
     template void launch_overlaps<D, R>(const StepParams<R> &, Particles<R>, CellList,              \
                                         unsigned long long *, unsigned long long *, int,            \
                                         cudaStream_t);
