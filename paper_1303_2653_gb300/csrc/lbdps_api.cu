@@ -431,8 +431,11 @@ template <class L, class Real, class S> struct EngineT : Engine {
         return LBDPS_OK;
     }
 
-    CellList cells(int b) const { return CellList{cl_local[b], cl_base[b]}; }
-    CellListOut cells_out(int b) { return CellListOut{cl_local[b], cl_base[b], tile_total, ticket}; }
+    CellList cells(int b) const { return CellList{cl_local[b], cl_base[b], cell_tile_log2(H->ncell)}; }
+    CellListOut cells_out(int b)
+    {
+        return CellListOut{cl_local[b], cl_base[b], tile_total, ticket, cell_tile_log2(H->ncell)};
+    }
 
     int clear_cells(int b)
     {
@@ -982,7 +985,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
             std::vector<int> loc, bas;
             if ((rc = d2h(loc, cl_local[cur], (size_t)H->ncell + 1))) return rc;
             if ((rc = d2h(bas, cl_base[cur], (size_t)cell_tiles(H->ncell) + 1))) return rc;
-            auto begin = [&](int c) { return loc[c] + bas[c >> kCellTileLog2]; };
+            const int shift = cell_tile_log2(H->ncell);
+            auto begin = [&](int c) { return loc[c] + bas[c >> shift]; };
             for (int c = 0; c < H->ncell; ++c)
                 for (int k = begin(c); k < begin(c + 1); ++k) out[ids[k]] = (double)c;
         } else {
@@ -1185,6 +1189,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
                 b.f[p] = f[p];
                 b.cl_local[p] = cl_local[p];
                 b.cl_base[p] = cl_base[p];
+                b.cl_shift = cell_tile_log2(H->ncell);
                 b.part[p] = part[p];
             }
             b.tile_total = tile_total;

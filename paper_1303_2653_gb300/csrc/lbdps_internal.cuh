@@ -258,22 +258,33 @@ template <class Real> struct Particles {
 // Cell list after a sort: particles of cell c occupy sorted slots
 // begin(c) .. begin(c + 1) - 1.  It is kept in two levels so that one kernel
 // can produce it: an exclusive prefix of the per-cell counts inside each tile
-// of 4096 cells, and the exclusive prefix of the tile totals.
+// of 2^shift cells, and the exclusive prefix of the tile totals.  Tiles hold
+// 4,096 cells, or 16,384 on lattices of at least 2^22 cells, where the last
+// block of the scan would otherwise add up tens of thousands of tile totals
+// one block-width at a time.
 constexpr int kCellTileLog2 = 12;
-constexpr int kCellTile = 1 << kCellTileLog2;
+constexpr int kCellTileLog2Large = 14;
+constexpr int kLargeLatticeCells = 1 << 22;
+inline int cell_tile_log2(int ncell) { return ncell >= kLargeLatticeCells ? kCellTileLog2Large : kCellTileLog2; }
+inline int cell_tiles(int ncell)
+{
+    const int s = cell_tile_log2(ncell);
+    return (ncell + 1 + (1 << s) - 1) >> s;
+}
 struct CellList {
     const int *local;   // ncell + 1 entries
     const int *base;    // cell_tiles(ncell) + 1 entries
+    int shift;          // cell_tile_log2(ncell)
     __device__ __forceinline__ int begin(int c) const
     {
-        return __ldg(local + c) + __ldg(base + (c >> kCellTileLog2));
+        return __ldg(local + c) + __ldg(base + (c >> shift));
     }
 };
 struct CellListOut {
     int *local, *base, *tile_total;
     unsigned *ticket;   // zero between launches
+    int shift;
 };
-inline int cell_tiles(int ncell) { return (ncell + 1 + kCellTile - 1) / kCellTile; }
 
 // Scratch of the bubble labelling (one int per cell for parent, size and
 // top flags; three counters; the count limit; an error word).
@@ -403,6 +414,7 @@ struct BatchBed {
     PopLayout lay;
     const void *f[2];              // population buffers in the bed's storage type
     int *cl_local[2], *cl_base[2];
+    int cl_shift;                  // tile size of the cell list (cell_tile_log2)
     int *tile_total;
     unsigned *ticket;
     Particles<float> part[2], stage;
@@ -418,7 +430,7 @@ struct BatchBed {
 
 // Work tables of a batch: (bed, tile) per thread block of each kernel class.
 // Cell tiles cover kBatchTile consecutive cells of a bed, scan tiles the
-// kCellTile-cell tiles of the cell list, particle tiles kBatchTile
+// tiles of the cell list, particle tiles kBatchTile
 // consecutive sorted particles.  The entry counts live in device memory
 // (count[0..2]: cell, scan, particle tiles), so a captured tick stays valid
 // when the tables are rewritten for another set of beds.

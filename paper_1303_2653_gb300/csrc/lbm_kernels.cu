@@ -521,7 +521,7 @@ __device__ __forceinline__ void batched_cell(const BatchBed &b, int a, const int
         pp.pull[i] = fin + (long long)i * b.lay.nce - b.lay.off<D2Q9>(i);
         pp.own[i] = fout + (long long)i * b.lay.nce;
     }
-    const CellList cells{b.cl_local[a], b.cl_base[a]};
+    const CellList cells{b.cl_local[a], b.cl_base[a], b.cl_shift};
     const bool les = b.sp.les_k > 0.0f, fb = b.sp.has_fb != 0;
     if (les && fb)
         collide_stream_cell<D2Q9, float, S, true, true>(b.sp, b.lay, pp, cells, b.part[a], b.fld, idx);

@@ -508,23 +508,24 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot, int *t
 
 // ---------------------------------------------------------------------------
 // One-launch scan of counts[0..ncell] into a two-level cell list.  Each block
-// scans one tile of 4096 counts (four consecutive counts per thread, one
-// 16-byte load and store) and writes its total; the block that finishes last
-// (ticket counter, nothing waits) scans the tile totals and resets the ticket
-// for the next launch.
+// scans one tile of 4,096 (or 16,384) counts, ITEMS consecutive counts per
+// thread in 16-byte loads and stores, and writes its total; the block that
+// finishes last (ticket counter, nothing waits) scans the tile totals and
+// resets the ticket for the next launch.
 // ---------------------------------------------------------------------------
 constexpr int kCellScanThreads = 1024;
-constexpr int kCellScanItems = kCellTile / kCellScanThreads;
-constexpr int kCellScanVec = kCellScanItems / 4;   // int4 loads per thread
-static_assert(kCellScanItems % 4 == 0, "whole int4 per thread");
 
 // Tile `tile` of `nt` (one block of kCellScanThreads threads; every thread
-// calls it).
+// calls it); ITEMS = tile cells / kCellScanThreads.
+template <int ITEMS>
 __device__ __forceinline__ void cell_scan_tile(const int *__restrict__ counts, const CellListOut &out,
                                                int n, int tile, int nt, int *warp_tot, int &total,
                                                bool &last)
 {
-    const int base = tile * kCellTile + threadIdx.x * kCellScanItems;
+    constexpr int kCellScanItems = ITEMS;
+    constexpr int kCellScanVec = ITEMS / 4;   // int4 loads per thread
+    static_assert(ITEMS % 4 == 0, "whole int4 per thread");
+    const int base = tile * (kCellScanThreads * ITEMS) + threadIdx.x * kCellScanItems;
     // all of the thread's loads are issued before any is used
     int4 c4[kCellScanVec];
     const bool whole = base + kCellScanItems <= n;
@@ -582,20 +583,27 @@ __device__ __forceinline__ void cell_scan_tile(const int *__restrict__ counts, c
     }
 }
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kCellScanThreads)
 k_cell_scan(const int *__restrict__ counts, CellListOut out, int n)
 {
     __shared__ int warp_tot[32];
     __shared__ int total;
     __shared__ bool last;
-    cell_scan_tile(counts, out, n, blockIdx.x, gridDim.x, warp_tot, total, last);
+    cell_scan_tile<ITEMS>(counts, out, n, blockIdx.x, gridDim.x, warp_tot, total, last);
 }
+
+static_assert((kCellScanThreads << 2) == (1 << kCellTileLog2), "4 counts per thread in small tiles");
+static_assert((kCellScanThreads << 4) == (1 << kCellTileLog2Large), "16 in large ones");
 
 void launch_cell_scan(const int *counts, CellListOut out, int ncell, cudaStream_t st)
 {
     const int n = ncell + 1;
     const int nt = cell_tiles(ncell);
-    k_cell_scan<<<nt, kCellScanThreads, 0, st>>>(counts, out, n);
+    if (out.shift == kCellTileLog2Large)
+        k_cell_scan<16><<<nt, kCellScanThreads, 0, st>>>(counts, out, n);
+    else
+        k_cell_scan<4><<<nt, kCellScanThreads, 0, st>>>(counts, out, n);
 }
 
 // ---------------------------------------------------------------------------
@@ -1017,7 +1025,7 @@ k_drag_batched(const BatchBed *__restrict__ beds, const int2 *__restrict__ work,
         if (!batch_entry(beds, work, w, step, e)) continue;   // the same for the whole block
         const BatchBed &b = *e.b;
         const int first = e.tile * kBatchTile;
-        const CellList cells{b.cl_local[e.a], b.cl_base[e.a]};
+        const CellList cells{b.cl_local[e.a], b.cl_base[e.a], b.cl_shift};
         __syncthreads();   // the previous entry's readers of sfp are done
         drag_step_particle<2, float, false>(b.sp, b.part[e.a], b.stage, cells, b.fld, b.key,
                                             b.counts, b.diag_fpre, b.diag_fd, b.np,
@@ -1039,10 +1047,13 @@ k_cell_scan_batched(const BatchBed *__restrict__ beds, const int2 *__restrict__ 
         if (!batch_entry(beds, work, w, step, e)) continue;
         const BatchBed &b = *e.b;
         const int nb = 1 - e.a;
-        const CellListOut out{b.cl_local[nb], b.cl_base[nb], b.tile_total, b.ticket};
-        const int nt = (b.ncell + 1 + kCellTile - 1) / kCellTile;
+        const CellListOut out{b.cl_local[nb], b.cl_base[nb], b.tile_total, b.ticket, b.cl_shift};
+        const int nt = (b.ncell + 1 + (1 << b.cl_shift) - 1) >> b.cl_shift;
         __syncthreads();   // the previous entry's users of the shared words are done
-        cell_scan_tile(b.counts, out, b.ncell + 1, e.tile, nt, warp_tot, total, last);
+        if (b.cl_shift == kCellTileLog2Large)
+            cell_scan_tile<16>(b.counts, out, b.ncell + 1, e.tile, nt, warp_tot, total, last);
+        else
+            cell_scan_tile<4>(b.counts, out, b.ncell + 1, e.tile, nt, warp_tot, total, last);
     }
 }
 
@@ -1058,7 +1069,7 @@ k_scatter_batched(const BatchBed *__restrict__ beds, const int2 *__restrict__ wo
         const int k = e.tile * kBatchTile + (int)threadIdx.x;
         if (k >= b.np) continue;
         const int nb = 1 - e.a;
-        scatter_one(b.key, b.part[e.a].id, b.counts, CellList{b.cl_local[nb], b.cl_base[nb]}, b.slot,
+        scatter_one(b.key, b.part[e.a].id, b.counts, CellList{b.cl_local[nb], b.cl_base[nb], b.cl_shift}, b.slot,
                     b.idslot, k);
     }
 }
@@ -1077,7 +1088,7 @@ k_gather_batched(const BatchBed *__restrict__ beds, const int2 *__restrict__ wor
         const int nb = 1 - e.a;
         Particles<float> src = b.stage;
         src.id = b.part[e.a].id;
-        gather_one<2, float>(CellList{b.cl_local[nb], b.cl_base[nb]}, b.slot, b.idslot, src,
+        gather_one<2, float>(CellList{b.cl_local[nb], b.cl_base[nb], b.cl_shift}, b.slot, b.idslot, src,
                              b.part[nb], s);
     }
 }
@@ -1094,7 +1105,7 @@ k_detect_batched(const BatchBed *__restrict__ beds, const int2 *__restrict__ wor
         const int i = e.tile * kBatchTile + (int)threadIdx.x;
         if (i >= b.np) continue;
         const int nb = 1 - e.a;
-        detect_one<2, float>(b.sp, b.part[nb], CellList{b.cl_local[nb], b.cl_base[nb]}, b.best,
+        detect_one<2, float>(b.sp, b.part[nb], CellList{b.cl_local[nb], b.cl_base[nb], b.cl_shift}, b.best,
                              b.wall, nullptr, nullptr, 0, i);
     }
 }
