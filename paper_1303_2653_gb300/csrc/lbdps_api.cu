@@ -12,6 +12,10 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <thread>
+#include <mutex>
+#include <climits>
+#include <cstdint>
 #include <type_traits>
 #include <vector>
 
@@ -1230,17 +1234,57 @@ Engine *make_engine_l(lbdps *h)
 }
 
 // ---------------------------------------------------------------------------
+// Host loops over particle arrays, split over the host's cores: f(lo, hi) for
+// consecutive chunks of [0, n).  Large beds hold millions of coordinates, and
+// one core spends tens of milliseconds converting and checking them.
+// ---------------------------------------------------------------------------
+template <class F> void host_parallel(size_t n, F &&f)
+{
+    constexpr size_t kMinChunk = 1 << 16;
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t nt = std::min<size_t>({(size_t)hw, (size_t)16, (n + kMinChunk - 1) / kMinChunk});
+    if (nt <= 1) {
+        f((size_t)0, n);
+        return;
+    }
+    std::vector<std::thread> pool;
+    pool.reserve(nt - 1);
+    const size_t chunk = (n + nt - 1) / nt;
+    for (size_t t = 1; t < nt; ++t) {
+        const size_t lo = std::min(n, t * chunk), hi = std::min(n, lo + chunk);
+        try {
+            pool.emplace_back([&f, lo, hi] { f(lo, hi); });
+        } catch (...) {   // no thread to be had: run the chunk here
+            f(lo, hi);
+        }
+    }
+    f((size_t)0, std::min(n, chunk));
+    for (auto &th : pool) th.join();
+}
+
+// ---------------------------------------------------------------------------
 // Validation helpers.
 // ---------------------------------------------------------------------------
 int validate_positions(const lbdps *h, const double *pos)
 {
     const int D = h->dim, np = h->np;
-    for (int i = 0; i < np; ++i)
-        for (int a = 0; a < D; ++a) {
-            const double p = pos[(size_t)i * D + a];
-            if (!(p >= 0.0 && p < (double)h->n[a]))
-                return fail(LBDPS_ERR_INVALID, "particle %d lies outside the domain on axis %d", i, a);
+    // the first particle (smallest index) outside the domain, as one loop
+    // in index order would find it
+    std::mutex mu;
+    size_t first = SIZE_MAX;
+    host_parallel((size_t)np * D, [&](size_t lo, size_t hi) {
+        for (size_t e = lo; e < hi; ++e) {
+            const double p = pos[e];
+            if (!(p >= 0.0 && p < (double)h->n[e % D])) {
+                std::lock_guard<std::mutex> lock(mu);
+                first = std::min(first, e);
+                return;
+            }
         }
+    });
+    if (first != SIZE_MAX)
+        return fail(LBDPS_ERR_INVALID, "particle %d lies outside the domain on axis %d",
+                    (int)(first / D), (int)(first % D));
     return LBDPS_OK;
 }
 
@@ -1501,11 +1545,22 @@ extern "C" {
 
 }  // extern "C"
 
+// A host array of doubles whose pages are first touched by whoever fills it.
+struct HostArray {
+    std::unique_ptr<double[]> p;
+    bool allocate(size_t n)
+    {
+        p.reset(new (std::nothrow) double[std::max<size_t>(n, 1)]);
+        return p != nullptr;
+    }
+    double *data() const { return p.get(); }
+};
+
 // Validation, derived constants and lattice-unit particles of a description
 // (no device work).  Shared by lbdps_create and lbdps_memory_estimate.
 static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
                        const lbdps_params *prm, std::unique_ptr<lbdps> &hout,
-                       std::vector<double> &pos, std::vector<double> &vel)
+                       HostArray &pos, HostArray &vel)
 {
     if (!lat || !par || !prm) return fail(LBDPS_ERR_INVALID, "NULL description");
     const int D = lat->dim;
@@ -1620,14 +1675,18 @@ static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc 
             }
         }
     }
-    // particles in lattice units
-    pos.assign((size_t)h->np * D, 0.0);
-    vel.assign((size_t)h->np * D, 0.0);
+    // particles in lattice units (the arrays are filled by the threads that
+    // convert them, so their pages are first touched in parallel too)
+    const size_t ne = (size_t)h->np * D;
+    if (!pos.allocate(ne) || !vel.allocate(ne)) return fail(LBDPS_ERR_OOM, "host allocation failed");
     const double vscale = lat->dt / lat->h;
-    for (size_t i = 0; i < pos.size(); ++i) {
-        pos[i] = par->pos[i] / lat->h;
-        vel[i] = par->vel[i] * vscale;
-    }
+    double *pd = pos.data(), *vd = vel.data();
+    host_parallel(ne, [&](size_t lo, size_t hi) {
+        for (size_t i = lo; i < hi; ++i) {
+            pd[i] = par->pos[i] / lat->h;
+            vd[i] = par->vel[i] * vscale;
+        }
+    });
     int rc = validate_positions(h.get(), pos.data());
     if (rc) return rc;
     hout = std::move(h);
@@ -1641,7 +1700,7 @@ int lbdps_memory_estimate(const lbdps_lattice_desc *lat, const lbdps_particle_de
 {
     if (!bytes) return fail(LBDPS_ERR_INVALID, "bytes is NULL");
     std::unique_ptr<lbdps> h;
-    std::vector<double> pos, vel;
+    HostArray pos, vel;
     int rc = prepare_bed(lat, par, prm, h, pos, vel);
     if (rc) return rc;
     h->mem.count_only = true;
@@ -1659,7 +1718,7 @@ int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
     if (!out) return fail(LBDPS_ERR_INVALID, "out is NULL");
     *out = nullptr;
     std::unique_ptr<lbdps> h;
-    std::vector<double> pos, vel;
+    HostArray pos, vel;
     // the pairwise overlap test of hard spheres runs on the device once the
     // particles are sorted (below); the host checks the domain only
     int rc = prepare_bed(lat, par, prm, h, pos, vel);
