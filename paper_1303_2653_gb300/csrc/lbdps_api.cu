@@ -221,7 +221,9 @@ struct Engine {
     virtual ~Engine() {}
     virtual int allocate(DeviceAlloc &A) = 0;
     virtual int upload_initial(const double *pos_lat, const double *vel_lat) = 0;
-    virtual int enqueue_step(int parity, cudaEvent_t *ev) = 0;
+    // gas_stats: the collision also writes the per-block moment sums of the
+    // state it reads (parity `parity`) into that parity's gas partials
+    virtual int enqueue_step(int parity, cudaEvent_t *ev, bool gas_stats = false) = 0;
     virtual int fields(int mask, int units, double *out, size_t cap) = 0;
     virtual int particles(int units, double *pos, double *vel, int64_t cap) = 0;
     virtual int set_particles(const double *pos, const double *vel) = 0;
@@ -238,10 +240,11 @@ struct Engine {
     // reductions of the current state, written by the kernel into mapped
     // pinned host memory `dst` (kStatOut doubles) on the stream, no wait
     virtual int enqueue_stats(double *dst) = 0;
-    // the same on stream st, with the health word and outlet count taken from
-    // snapshot slot `slot` (written by enqueue_snapshot at the end of a step)
-    // instead of the live words
-    virtual int enqueue_stats_snap(double *dst, cudaStream_t st, int slot) = 0;
+    // the reductions of the state of parity q after the next step's collision
+    // wrote its gas partials, with the health word and outlet count of
+    // snapshot slot `slot` (written by enqueue_snapshot at the end of the
+    // step that produced the state) instead of the live words
+    virtual int enqueue_stats_of(double *dst, int q, int slot) = 0;
     virtual int enqueue_snapshot(int slot) = 0;
     virtual int health(unsigned *out) = 0;
     virtual int bubbles(double threshold, int voidage, int64_t *out) = 0;
@@ -280,12 +283,10 @@ struct lbdps {
     unsigned *health_host = nullptr;   // pinned: the health word, then 16 doubles of statistics
     double *stats_host = nullptr;      // inside the same pinned block
     double *mon_host = nullptr;        // pinned: kMonSteps statistics records (lbdps_step_monitored)
-    // monitored steps with the reductions beside the next step: graphs of one
-    // step plus the snapshot of its health word and outlet count (per
-    // starting parity), the reductions' stream and the events that order them
+    // monitored steps: graphs of one step whose collision also sums the
+    // moments of its input state, plus the snapshot of the step's health word
+    // and outlet count (per starting parity)
     cudaGraphExec_t mon_graph[2] = {nullptr, nullptr};
-    cudaStream_t stats_stream = nullptr;
-    cudaEvent_t ev_step[2] = {nullptr, nullptr}, ev_red[2] = {nullptr, nullptr};
     std::vector<double> inlet_lat;     // face cells x dim
 };
 
@@ -325,6 +326,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
     unsigned long long *npairs_dev = nullptr;
     unsigned long long *ovl_dev = nullptr;      // overlap check: count, smallest pair
     unsigned long long *snap_dev = nullptr;     // 2 slots x (health word, outlet count)
+    double *gas_part[2] = {nullptr, nullptr};   // per parity: moment sums of the collision's warps
+    long long gas_blocks = 0;
     StepParams<Real> sp{};
     PopLayout lay{};          // extended lattice of the population arrays
     int packed_limit = 0;     // more particle centres per cell cannot all be apart
@@ -413,6 +416,11 @@ template <class L, class Real, class S> struct EngineT : Engine {
         npairs_dev = (unsigned long long *)get(sizeof(unsigned long long));
         ovl_dev = (unsigned long long *)get(2 * sizeof(unsigned long long));
         snap_dev = (unsigned long long *)get(4 * sizeof(unsigned long long));
+        gas_blocks = collide_warps(D, H->n);
+        for (int b = 0; b < 2; ++b) {
+            gas_part[b] = (double *)get(sizeof(double) * 4 * (size_t)gas_blocks);
+            if (!gas_part[b]) return fail(LBDPS_ERR_OOM, "device allocation failed");
+        }
         void *must[] = {f[0], f[1], cl_local[0], cl_local[1], cl_base[0], cl_base[1], fld.rho,
                         fld.node4, key, counts, slot, idslot, tile_total, ticket,
                         best, wall, tab_branch, inlet_dev, health_dev,
@@ -518,6 +526,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
             packed_limit = (int)std::ceil(cap * std::pow(1.0 + k.d, D) / unit);
         }
         for (int c = 0; c < 3; ++c) p.spin_out[c] = H->friction && c < NW ? stage.w[c] : nullptr;
+        p.gas_partials = nullptr;
     }
 
     int upload_initial(const double *pos_lat, const double *vel_lat) override
@@ -623,13 +632,15 @@ template <class L, class Real, class S> struct EngineT : Engine {
     // ev (optional, kStepEvents events) brackets the kernels for profiling:
     // collide_stream, soft-sphere contacts, drag, sort, hard-sphere
     // collisions (kStepEventClass maps each interval to its class).
-    int enqueue_step(int parity, cudaEvent_t *ev) override
+    int enqueue_step(int parity, cudaEvent_t *ev, bool gas_stats) override
     {
         cudaStream_t st = H->stream;
         const int a = parity, b = 1 - parity;
         const int np = H->np;
         if (ev) CU(cudaEventRecord(ev[0], st));
-        launch_collide_stream<L, Real, S>(sp, lay, f[a], f[b], cells(a), part[a], fld, st);
+        StepParams<Real> spc = sp;
+        if (gas_stats) spc.gas_partials = gas_part[a];
+        launch_collide_stream<L, Real, S>(spc, lay, f[a], f[b], cells(a), part[a], fld, st);
         CHECK_LAUNCH();
         if (ev) CU(cudaEventRecord(ev[1], st));
         if (H->soft) {
@@ -1009,26 +1020,26 @@ template <class L, class Real, class S> struct EngineT : Engine {
         // host link itself: no copy node follows the kernel on the stream
         double *dev = nullptr;
         CU(cudaHostGetDevicePointer((void **)&dev, dst, 0));
-        launch_reduce_all<L, Real, S>(lay, H->ncell, f[cur], part[cur], H->k.mp, H->np, cells(cur),
-                                      sp.tab.eps_g, H->ntab, bed ? &fld : nullptr, red_partials,
-                                      red_ticket, health_dev, solids_out, dev, health_dev,
-                                      packed_limit, H->stream);
+        launch_gas_moments<L, Real, S>(lay, f[cur], H->n, gas_part[cur], H->stream);
+        CHECK_LAUNCH();
+        launch_reduce_all<L, Real>(H->ncell, gas_part[cur], gas_blocks, part[cur], H->k.mp, H->np,
+                                   sp.tab.eps_g, H->ntab, bed ? &fld : nullptr,
+                                   red_partials, red_ticket, health_dev, solids_out, dev, health_dev,
+                                   packed_limit, H->stream);
         CHECK_LAUNCH();
         return LBDPS_OK;
     }
 
-    int enqueue_stats_snap(double *dst, cudaStream_t st, int slot) override
+    int enqueue_stats_of(double *dst, int q, int slot) override
     {
-        const int cur = H->parity;
         double *dev = nullptr;
         CU(cudaHostGetDevicePointer((void **)&dev, dst, 0));
         const unsigned long long *sn = snap_dev + 2 * slot;
-        // no node diagnostics: those arrays are rewritten by the step that
-        // runs beside this reduction
-        launch_reduce_all<L, Real, S>(lay, H->ncell, f[cur], part[cur], H->k.mp, H->np, cells(cur),
-                                      sp.tab.eps_g, H->ntab, nullptr, red_partials, red_ticket,
-                                      reinterpret_cast<const unsigned *>(sn), sn + 1, dev, health_dev,
-                                      packed_limit, st);
+        // no node diagnostics: the next step has rewritten those arrays
+        launch_reduce_all<L, Real>(H->ncell, gas_part[q], gas_blocks, part[q], H->k.mp, H->np,
+                                   sp.tab.eps_g, H->ntab, nullptr, red_partials, red_ticket,
+                                   reinterpret_cast<const unsigned *>(sn), sn + 1, dev, health_dev,
+                                   packed_limit, H->stream);
         CHECK_LAUNCH();
         return LBDPS_OK;
     }
@@ -1315,7 +1326,7 @@ int capture_monitored_step(lbdps *h, cudaGraphExec_t *out)
 {
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = h->eng->enqueue_step(h->parity, nullptr);
+    int rc = h->eng->enqueue_step(h->parity, nullptr, true);
     if (rc == LBDPS_OK) rc = h->eng->enqueue_snapshot(h->parity);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (rc) {
@@ -1404,49 +1415,51 @@ void decode_stats(lbdps *h, const double *v, bool bed, int64_t steps, lbdps_stat
 // once per kMonSteps steps.
 constexpr int kMonSteps = 1024;
 
-// The reduction of the state after step s reads f, the particles and the
-// cell list of that state, which step s + 1 only reads (it writes the other
-// buffers); step s + 2 overwrites them.  So the reduction runs on its own
-// stream beside step s + 1, and step s + 2 waits for it.  The health word and
-// the outlet count, which step s + 1 updates, come from a snapshot taken at
-// the end of step s.
-int run_monitored_overlapped(lbdps *h, int64_t nsteps, lbdps_stats_t *out)
+// Monitored steps with the statistics fused into the next collision.  The
+// statistics of the state after step s need the gas mass and momentum of
+// that state, which the collision of step s + 1 reads anyway: its graph
+// (capture_monitored_step) has the collision write the per-block moment
+// sums of its input state into that parity's gas partials.  The reduction of
+// the state after step s then runs right after step s + 1 on the same
+// stream; it reads only those partials, the cell list and the particles of
+// that state (step s + 1 writes the other buffers) and the health word and
+// outlet count that the graph of step s snapshotted at its end.  The state
+// after the last step gets its gas partials from one k_gas_moments pass.
+int run_monitored_fused(lbdps *h, int64_t nsteps, lbdps_stats_t *out)
 {
-    if (!h->stats_stream) {
-        CU(cudaStreamCreateWithFlags(&h->stats_stream, cudaStreamNonBlocking));
-        for (int p = 0; p < 2; ++p) {
-            CU(cudaEventCreateWithFlags(&h->ev_step[p], cudaEventDisableTiming));
-            CU(cudaEventCreateWithFlags(&h->ev_red[p], cudaEventDisableTiming));
-        }
-    }
-    for (int64_t s = 0; s < nsteps;) {
-        const int k = (int)std::min<int64_t>(kMonSteps, nsteps - s);
-        bool pending[2] = {false, false};
+    int64_t done = 0;   // records written to out
+    while (done < nsteps) {
+        const int k = (int)std::min<int64_t>(kMonSteps, nsteps - done);
+        // states after steps done + 1 .. done + k; the first step of the
+        // batch also writes the partials of the state before it (unused)
+        int prev = -1;   // parity of the state whose reduction is due
         for (int t = 0; t < k; ++t) {
             const int p = h->parity;
             if (!h->mon_graph[p]) {
                 int rc = capture_monitored_step(h, &h->mon_graph[p]);
                 if (rc) return rc;
             }
-            if (pending[p]) CU(cudaStreamWaitEvent(h->stream, h->ev_red[p], 0));
             CU(cudaGraphLaunch(h->mon_graph[p], h->stream));
+            if (prev >= 0) {
+                // the state before this step (parity p), made by the step
+                // whose graph snapshotted into slot 1 - p
+                int rc = h->eng->enqueue_stats_of(h->mon_host + (size_t)(t - 1) * kStatOut, p, 1 - p);
+                if (rc) return rc;
+            }
             h->parity ^= 1;
             h->steps++;
-            CU(cudaEventRecord(h->ev_step[p], h->stream));
-            CU(cudaStreamWaitEvent(h->stats_stream, h->ev_step[p], 0));
-            int rc = h->eng->enqueue_stats_snap(h->mon_host + (size_t)t * kStatOut, h->stats_stream, p);
-            if (rc) return rc;
-            CU(cudaEventRecord(h->ev_red[p], h->stats_stream));
-            pending[p] = true;
+            prev = h->parity;
         }
-        CU(cudaStreamSynchronize(h->stats_stream));
+        // the state after the batch's last step: its own moment pass
+        int rc = h->eng->enqueue_stats(h->mon_host + (size_t)(k - 1) * kStatOut);
+        if (rc) return rc;
         CU(cudaStreamSynchronize(h->stream));
         for (int t = 0; t < k; ++t)
-            decode_stats(h, h->mon_host + (size_t)t * kStatOut, false, h->steps - k + 1 + t, out + s + t);
-        s += k;
+            decode_stats(h, h->mon_host + (size_t)t * kStatOut, false, h->steps - k + 1 + t, out + done + t);
+        done += k;
         // the health word of the last record, as lbdps_step checks it
         if (h->prm.check_every > 0) {
-            const int hw = out[s - 1].health;
+            const int hw = out[done - 1].health;
             if (hw & HEALTH_DIVERGED)
                 return fail(LBDPS_ERR_DIVERGED, "gas state diverged by step %lld", (long long)h->steps);
             if (hw & HEALTH_DOMAIN)
@@ -1468,7 +1481,7 @@ int run_monitored(lbdps *h, int64_t nsteps, lbdps_stats_t *out)
     }
     // node diagnostics are rewritten by every step: with them, each
     // reduction runs before the next step on the handle's stream
-    if (h->prm.use_graph && !h->prm.diagnostics) return run_monitored_overlapped(h, nsteps, out);
+    if (h->prm.use_graph && !h->prm.diagnostics) return run_monitored_fused(h, nsteps, out);
     for (int64_t s = 0; s < nsteps;) {
         const int k = (int)std::min<int64_t>(kMonSteps, nsteps - s);
         for (int t = 0; t < k; ++t) {
@@ -1784,13 +1797,7 @@ void lbdps_destroy(lbdps_t *h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    if (h->stats_stream) cudaStreamSynchronize(h->stats_stream);
     free_graphs(h);
-    if (h->stats_stream) cudaStreamDestroy(h->stats_stream);
-    for (int p = 0; p < 2; ++p) {
-        if (h->ev_step[p]) cudaEventDestroy(h->ev_step[p]);
-        if (h->ev_red[p]) cudaEventDestroy(h->ev_red[p]);
-    }
     h->eng.reset();
     h->mem.release_all();
     if (h->health_host) cudaFreeHost(h->health_host);

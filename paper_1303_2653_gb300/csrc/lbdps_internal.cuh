@@ -154,7 +154,20 @@ template <class Real> struct StepParams {
     // (mu_f = 0: none); the new spins go to spin_out (sorted slot order)
     Real mu_f, gamma_t, inv_inertia;
     Real *spin_out[3];
+    // with a monitored step: per-warp sums of the cell moments (mass
+    // deviation and momentum, Q-population sums of the state the collision
+    // reads) of the collision's warps, 4 FP64 values per warp (null: none)
+    double *gas_partials;
 };
+
+// Sum over a warp in a fixed order (butterfly of shuffles): every lane holds
+// the total.
+template <class T> __device__ __forceinline__ T warp_total(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // Layout of the population arrays: the lattice plus one ghost layer on every
 // face (x = -1 and n0, y = -1 and n1, and in 3D z = -1 and n2), rows padded to
@@ -310,6 +323,17 @@ void launch_collide_stream(const StepParams<Real> &p, const PopLayout &lay, cons
 template <class L, class Real, class S>
 void launch_init_equilibrium(const PopLayout &lay, const Real *u0, S *f, cudaStream_t st);
 
+// Warps of a collide_stream launch on a lattice of n cells per axis (the
+// size of the gas_partials array in groups of 4 doubles).
+long long collide_warps(int dim, const int *n);
+
+// The cell moments of the state held in f (as the next collision pulls it),
+// summed per warp of the collision's grid exactly as a collision with
+// gas_partials does: 4 doubles per warp into partials.
+template <class L, class Real, class S>
+void launch_gas_moments(const PopLayout &lay, const S *f, const int *n, double *partials,
+                        cudaStream_t st);
+
 template <class L, class Real, class S>
 void launch_export_populations(const PopLayout &lay, int ncell, const S *f, double *out,
                                cudaStream_t st);
@@ -382,21 +406,23 @@ void launch_resolve(const StepParams<Real> &p, Particles<Real> parts, const int 
 // kStatMaxBlocks blocks, each writing kStatValues partials; out holds
 // kStatValues values plus the health word and the outlet count.
 constexpr int kStatValues = 11;
-constexpr int kStatMaxBlocks = 152;
+constexpr int kStatMaxBlocks = 152 * 4;   // four blocks of 512 threads per SM
 constexpr int kStatPartials = kStatValues * kStatMaxBlocks;
 constexpr int kStatOut = kStatValues + 2;
 
-// All bed statistics in one launch (values listed in stats_kernels.cu); bed
-// = the diagnostic fields or null; ticket must be zero on entry and is zero
-// again on exit.
 // copies the health word and the outlet count to out[0], out[1]
 void launch_snapshot(const unsigned *health, const unsigned long long *solids_out,
                      unsigned long long *out, cudaStream_t st);
 
-template <class L, class Real, class S>
-void launch_reduce_all(const PopLayout &lay, int ncell, const S *f, Particles<Real> parts, double mp,
-                       int np, CellList cells, const Real *eps_tab, int ntab,
-                       const Fields<Real> *bed, double *partials, unsigned *ticket,
+// All bed statistics in one launch (values listed in stats_kernels.cu); gas
+// = ngas groups of 4 FP64 sums of the cell moments of the same state
+// (launch_gas_moments, or a collision with gas_partials); parts = the
+// particles of that state in sorted (cell) order; bed = the diagnostic
+// fields or null; ticket must be zero on entry and is zero again on exit.
+template <class L, class Real>
+void launch_reduce_all(int ncell, const double *gas, long long ngas, Particles<Real> parts, double mp,
+                       int np, const Real *eps_tab, int ntab, const Fields<Real> *bed,
+                       double *partials, unsigned *ticket,
                        const unsigned *health, const unsigned long long *solids_out, double *out,
                        unsigned *health_live, int packed_limit, cudaStream_t st);
 

@@ -275,24 +275,91 @@ __device__ __forceinline__ void face_streaming_x(const StepParams<Real> &p, cons
     }
 }
 
-// The work of one cell (idx: its coordinates): deposition, collision,
-// node outputs and streaming.  Shared by the single-bed kernel and the
-// batched kernel of the serving loop, so that a bed's arithmetic does not
-// depend on how its cells are mapped to threads.
-template <class L, class Real, class S, bool LES, bool FB>
+// Mass deviation and momentum of a cell, sum_i f_i and sum_i c_i f_i of
+// its deviations, added in direction order.  The collision and the
+// statistics of a state use this one function, so both add the same values
+// in the same order.
+template <class L, class Real>
+__device__ __forceinline__ void cell_moments(const Real *f, Real &drho, Real *m)
+{
+    constexpr int D = L::D, Q = L::Q;
+    drho = Real(0);
+    m[0] = m[1] = m[2] = Real(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += f[i];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            if (L::c(i, a) == 1) m[a] += f[i];
+            else if (L::c(i, a) == -1) m[a] -= f[i];
+        }
+    }
+}
+
+// Per-warp sums of the cell moments for the statistics of a state: each warp
+// adds its lanes' values in the arithmetic type (butterfly) and lane 0
+// stores the four totals in FP64.  Every lane of the warp calls it (mom:
+// zeros for a lane without a cell); nothing waits on other warps.
+template <class Real>
+__device__ __forceinline__ void warp_gas_partials(const Real *mom, double *out)
+{
+    Real t[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) t[k] = warp_total<Real>(mom[k]);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] = (double)t[k];
+    }
+}
+
+// The populations of cell idx as its collision pulls them: direction i from
+// x - c_i of the last step's stored values.
+template <class L, class Real, class S>
+__device__ __forceinline__ void pull_cell(const PopLayout &lay, const PopPtrs<S> &pp, const int *idx,
+                                          Real *f)
+{
+    const int xe = lay.ext(idx);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) f[i] = Store<S>::load(__ldg(pp.pull[i] + xe));
+}
+
+__device__ __forceinline__ long long grid_block_index()
+{
+    return blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+}
+
+// index of this warp in the collision's grid (blocks in launch order, warps
+// of a block in order)
+__device__ __forceinline__ long long grid_warp_index()
+{
+    return grid_block_index() * (blockDim.x >> 5) + (threadIdx.x >> 5);
+}
+
+// Nothing to do once a cell's moments are known (the plain step).
+struct NoMomentsHook {
+    template <class Real> __device__ __forceinline__ void operator()(Real, const Real *) const {}
+};
+
+// The work of one cell (idx: its coordinates) from its pulled populations
+// fin (pull_cell): deposition, collision, node outputs and streaming.
+// Shared by the single-bed kernel and the batched kernel of the serving
+// loop, so that a bed's arithmetic does not depend on how its cells are
+// mapped to threads.  hook(drho, m) receives the moments of fin once the
+// node outputs are written: by then every load of the cell has been issued
+// and the momentum is no longer needed.
+template <class L, class Real, class S, bool LES, bool FB, class Hook = NoMomentsHook>
 __device__ __forceinline__ void collide_stream_cell(const StepParams<Real> &p, const PopLayout &lay,
                                                     const PopPtrs<S> &pp, const CellList &cells,
                                                     const Particles<Real> &parts,
-                                                    const Fields<Real> &fld, const int *idx)
+                                                    const Fields<Real> &fld, const int *idx,
+                                                    const Real *fin, const Hook &hook = Hook())
 {
     constexpr int D = L::D, Q = L::Q;
     const int x = idx[0] + p.n[0] * (idx[1] + p.n[1] * idx[2]);
     const int xe = lay.ext(idx);
-
-    // pull: population i of this step left x - c_i in the last one
     Real f[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = Store<S>::load(__ldg(pp.pull[i] + xe));
+    for (int i = 0; i < Q; ++i) f[i] = fin[i];
 
     // ---- deposition (Eq. 8) ----
     const int s0 = cells.begin(x), s1 = cells.begin(x + 1);
@@ -314,16 +381,8 @@ __device__ __forceinline__ void collide_stream_cell(const StepParams<Real> &p, c
     const Real og = t0.x;
 
     // ---- moments ----
-    Real drho = Real(0), m[3] = {Real(0), Real(0), Real(0)};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        drho += f[i];
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            if (L::c(i, a) == 1) m[a] += f[i];
-            else if (L::c(i, a) == -1) m[a] -= f[i];
-        }
-    }
+    Real drho, m[3];
+    cell_moments<L, Real>(f, drho, m);
     const Real rho = Real(1) + drho;
 
     // ---- Eq. 24 in closed form ----
@@ -373,6 +432,7 @@ __device__ __forceinline__ void collide_stream_cell(const StepParams<Real> &p, c
         fld.node4[x] = {ua[0], ua[1], ua[2], beta};
         fld.solg[x] = solg;
     }
+    hook(drho, static_cast<const Real *>(m));
 
     // ---- LES (Eq. 13-15) ----
     Real inv_tau_t = p.inv_tau, gam_t = t0.y, tau_t = p.tau;
@@ -466,18 +526,110 @@ __device__ __forceinline__ void collide_stream_cell(const StepParams<Real> &p, c
     else if (xhi) face_streaming_x<L, Real, S, 1>(p, lay, pp, xe, idx, rho, u);
 }
 
-template <class L, class Real, class S, bool LES, bool FB>
+// The moments of one cell as a row of the per-warp sums (zeros for a lane
+// without a cell).
+template <class L, class Real, class S>
+__device__ __forceinline__ void lane_moments(bool active, const PopLayout &lay, const PopPtrs<S> &pp,
+                                             const int *idx, Real *mom)
+{
+    mom[0] = mom[1] = mom[2] = mom[3] = Real(0);
+    if (active) {
+        Real f[L::Q], m[3];
+        pull_cell<L, Real, S>(lay, pp, idx, f);
+        cell_moments<L, Real>(f, mom[0], m);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) mom[1 + a] = m[a];
+    }
+}
+
+// The per-warp moment sums of a monitored step, taken inside the collision
+// once its moments are known (every lane of the warp has a cell).
+template <class Real> struct WarpMomentsHook {
+    double *partials;
+    __device__ __forceinline__ void operator()(Real drho, const Real *m) const
+    {
+        const Real mom[4] = {drho, m[0], m[1], m[2]};
+        warp_gas_partials<Real>(mom, partials + 4 * grid_warp_index());
+    }
+};
+
+// STATS: also the per-warp moment sums of the state it reads (a monitored
+// step; see p.gas_partials).  A warp whose lanes all have a cell adds them
+// inside the collision, after the deposition's loads (cell list, particles,
+// tables) have gone out with the populations; a warp at the end of a row
+// with lanes past the lattice adds them first, from loads of its own.
+template <class L, class Real, class S, bool LES, bool FB, bool STATS>
 __global__ void __launch_bounds__(256, K2Occupancy<L, Real>::value)
 k_collide_stream(StepParams<Real> p, PopLayout lay, PopPtrs<S> pp, CellList cells,
                  Particles<Real> parts, Fields<Real> fld)
 {
+    constexpr int Q = L::Q;
     // grid: x along blockIdx.x/threadIdx.x, y = blockIdx.y, z = blockIdx.z
     int idx[3];
     idx[0] = blockIdx.x * blockDim.x + threadIdx.x;
     idx[1] = blockIdx.y;
     idx[2] = blockIdx.z;
-    if (idx[0] >= p.n[0]) return;
-    collide_stream_cell<L, Real, S, LES, FB>(p, lay, pp, cells, parts, fld, idx);
+    const bool active = idx[0] < p.n[0];
+    if (!STATS) {
+        if (!active) return;
+        Real f[Q];
+        pull_cell<L, Real, S>(lay, pp, idx, f);
+        collide_stream_cell<L, Real, S, LES, FB>(p, lay, pp, cells, parts, fld, idx, f);
+        return;
+    }
+    Real f[Q];
+    if (__all_sync(0xffffffffu, active)) {
+        pull_cell<L, Real, S>(lay, pp, idx, f);
+        collide_stream_cell<L, Real, S, LES, FB>(p, lay, pp, cells, parts, fld, idx, f,
+                                                 WarpMomentsHook<Real>{p.gas_partials});
+        return;
+    }
+    Real mom[4];
+    lane_moments<L, Real, S>(active, lay, pp, idx, mom);
+    warp_gas_partials<Real>(mom, p.gas_partials + 4 * grid_warp_index());
+    if (!active) return;
+    pull_cell<L, Real, S>(lay, pp, idx, f);
+    collide_stream_cell<L, Real, S, LES, FB>(p, lay, pp, cells, parts, fld, idx, f);
+}
+
+// The cell moments of a state without a collision, with the collision's
+// grid, loads and per-warp sums (the statistics of the last state of a run,
+// and of any state on demand).
+template <class L, class Real, class S>
+__global__ void __launch_bounds__(256)
+k_gas_moments(PopLayout lay, PopPtrs<S> pp, int n0, double *partials)
+{
+    int idx[3];
+    idx[0] = blockIdx.x * blockDim.x + threadIdx.x;
+    idx[1] = blockIdx.y;
+    idx[2] = blockIdx.z;
+    Real mom[4];
+    lane_moments<L, Real, S>(idx[0] < n0, lay, pp, idx, mom);
+    warp_gas_partials<Real>(mom, partials + 4 * grid_warp_index());
+}
+
+// the collision's launch shape: one block row per lattice row, up to 256
+// threads along x
+static inline int collide_tx(int n0) { return n0 >= 256 ? 256 : ((n0 + 31) / 32) * 32; }
+
+long long collide_warps(int dim, const int *n)
+{
+    const int tx = collide_tx(n[0]);
+    return (long long)((n[0] + tx - 1) / tx) * n[1] * (dim == 3 ? n[2] : 1) * (tx / 32);
+}
+
+template <class L, class Real, class S>
+void launch_gas_moments(const PopLayout &lay, const S *f, const int *n, double *partials,
+                        cudaStream_t st)
+{
+    PopPtrs<S> pp{};
+    for (int i = 0; i < L::Q; ++i) {
+        pp.pull[i] = f + (long long)i * lay.nce - lay.off<L>(i);
+        pp.own[i] = nullptr;
+    }
+    const int tx = collide_tx(n[0]);
+    const dim3 grid((n[0] + tx - 1) / tx, n[1], L::D == 3 ? n[2] : 1);
+    k_gas_moments<L, Real, S><<<grid, tx, 0, st>>>(lay, pp, n[0], partials);
 }
 
 template <class L, class Real, class S>
@@ -490,17 +642,28 @@ void launch_collide_stream(const StepParams<Real> &p, const PopLayout &lay, cons
         pp.own[i] = fout + (long long)i * lay.nce;
     }
     // one block row per lattice row; up to 256 threads along x
-    const int tx = p.n[0] >= 256 ? 256 : ((p.n[0] + 31) / 32) * 32;
+    const int tx = collide_tx(p.n[0]);
     const dim3 grid((p.n[0] + tx - 1) / tx, p.n[1], L::D == 3 ? p.n[2] : 1);
     const bool les = p.les_k > Real(0), fb = p.has_fb != 0;
+    if (p.gas_partials) {
+        if (les && fb)
+            k_collide_stream<L, Real, S, true, true, true><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
+        else if (les)
+            k_collide_stream<L, Real, S, true, false, true><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
+        else if (fb)
+            k_collide_stream<L, Real, S, false, true, true><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
+        else
+            k_collide_stream<L, Real, S, false, false, true><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
+        return;
+    }
     if (les && fb)
-        k_collide_stream<L, Real, S, true, true><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
+        k_collide_stream<L, Real, S, true, true, false><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
     else if (les)
-        k_collide_stream<L, Real, S, true, false><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
+        k_collide_stream<L, Real, S, true, false, false><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
     else if (fb)
-        k_collide_stream<L, Real, S, false, true><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
+        k_collide_stream<L, Real, S, false, true, false><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
     else
-        k_collide_stream<L, Real, S, false, false><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
+        k_collide_stream<L, Real, S, false, false, false><<<grid, tx, 0, st>>>(p, lay, pp, cells, parts, fld);
 }
 
 // ---------------------------------------------------------------------------
@@ -523,14 +686,16 @@ __device__ __forceinline__ void batched_cell(const BatchBed &b, int a, const int
     }
     const CellList cells{b.cl_local[a], b.cl_base[a], b.cl_shift};
     const bool les = b.sp.les_k > 0.0f, fb = b.sp.has_fb != 0;
+    float f[D2Q9::Q];
+    pull_cell<D2Q9, float, S>(b.lay, pp, idx, f);
     if (les && fb)
-        collide_stream_cell<D2Q9, float, S, true, true>(b.sp, b.lay, pp, cells, b.part[a], b.fld, idx);
+        collide_stream_cell<D2Q9, float, S, true, true>(b.sp, b.lay, pp, cells, b.part[a], b.fld, idx, f);
     else if (les)
-        collide_stream_cell<D2Q9, float, S, true, false>(b.sp, b.lay, pp, cells, b.part[a], b.fld, idx);
+        collide_stream_cell<D2Q9, float, S, true, false>(b.sp, b.lay, pp, cells, b.part[a], b.fld, idx, f);
     else if (fb)
-        collide_stream_cell<D2Q9, float, S, false, true>(b.sp, b.lay, pp, cells, b.part[a], b.fld, idx);
+        collide_stream_cell<D2Q9, float, S, false, true>(b.sp, b.lay, pp, cells, b.part[a], b.fld, idx, f);
     else
-        collide_stream_cell<D2Q9, float, S, false, false>(b.sp, b.lay, pp, cells, b.part[a], b.fld, idx);
+        collide_stream_cell<D2Q9, float, S, false, false>(b.sp, b.lay, pp, cells, b.part[a], b.fld, idx, f);
 }
 
 // two blocks per SM: the three storage types and four flag combinations
@@ -668,6 +833,8 @@ void launch_import_populations(const PopLayout &lay, int ncell, const double *in
                                                  cudaStream_t);                                     \
     template void launch_init_equilibrium<L, R, S>(const PopLayout &, const R *, S *,               \
                                                    cudaStream_t);                                   \
+    template void launch_gas_moments<L, R, S>(const PopLayout &, const S *, const int *, double *,  \
+                                              cudaStream_t);                                       \
     template void launch_export_populations<L, R, S>(const PopLayout &, int, const S *, double *,   \
                                                      cudaStream_t);                                 \
     template void launch_import_populations<L, R, S>(const PopLayout &, int, const double *, S *,   \

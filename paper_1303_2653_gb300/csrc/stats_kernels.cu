@@ -2,12 +2,19 @@
 // lattice-mean voidage of the current positions, and (with diagnostics) the
 // voidage and particle-weighted slip of the last collision.
 //
-// Each thread accumulates over a grid-stride range of cells and particles (in
-// FP64 in the FP64 engine; in FP32 with Kahan compensation otherwise, since
-// FP64 arithmetic is slow on this part), each warp sums its lanes in the
-// arithmetic type, each block adds its warp totals in FP64 in a fixed order,
-// and the block that finishes last (ticket counter, nothing waits) adds the
-// block partials in a fixed order.  The result does not depend on scheduling.
+// The gas mass and momentum come as per-warp FP64 sums of the cell moments
+// (written by the collision of a monitored step, which reads exactly this
+// state, or by k_gas_moments with the same grid and order); this kernel adds
+// them in FP64.  The lattice sum of eps_g follows the occupied cells (the
+// first particle of each, in sorted order, adds its cell's departure from
+// the empty-cell value), so without diagnostics no per-cell array is read.
+// The other values: each thread accumulates over a grid-stride range of
+// particles, and of cells for the diagnostics (in FP64 in the FP64 engine; in
+// FP32 with Kahan compensation otherwise, since FP64 arithmetic is slow on
+// this part), each warp sums its lanes in the arithmetic type, each block
+// adds its warp totals in FP64 in a fixed order, and the block that finishes
+// last (ticket counter, nothing waits) adds the block partials in a fixed
+// order.  The result does not depend on scheduling.
 // `out` is mapped pinned host memory: the last block's stores are the only
 // traffic to the host, so no copy has to follow the launch on the stream.
 #include "lbdps_internal.cuh"
@@ -49,63 +56,55 @@ template <class T> __device__ __forceinline__ T warp_sum(T v)
 // [7] sum of eps_g of the current counts, [8] sum of the diagnostic eps_g,
 // [9] sum n |u_act - v_s|, [10] sum n (kStatValues = 11)
 
-template <class L, class Real, class S, bool BED>
+template <class L, class Real, bool BED>
 __global__ void __launch_bounds__(kRedThreads)
-k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> parts, double mp,
-             int np, CellList cells, const Real *__restrict__ eps_tab, int ntab, Fields<Real> fld,
-             double *partials, unsigned *ticket, const unsigned *health,
+k_reduce_all(int ncell, const double *__restrict__ gas, long long ngas, Particles<Real> parts,
+             double mp, int np, const Real *__restrict__ eps_tab, int ntab,
+             Fields<Real> fld, double *partials, unsigned *ticket, const unsigned *health,
              const unsigned long long *solids_out, double *out, unsigned *health_live,
              int packed_limit)
 {
-    constexpr int D = L::D, Q = L::Q;
+    constexpr int D = L::D;
     Acc<Real> acc[kStatValues];
+    double gacc[4] = {0.0, 0.0, 0.0, 0.0};   // gas mass deviation and momentum
     int packed = 0;   // a cell held more centres than can be there without overlaps
     const int stride = gridDim.x * blockDim.x;
-    // cells in batches of kB per thread (x, x + stride, ...): the loads of
-    // a batch are all issued before any is used, so that each thread keeps
-    // kB cells' worth of memory requests in flight
-    constexpr int kB = Q <= 9 ? 2 : 1;
-    for (int x0 = blockIdx.x * blockDim.x + threadIdx.x; x0 < ncell; x0 += kB * stride) {
-        Real fv[kB][Q];
-        int nn[kB];
+    for (long long b = blockIdx.x * blockDim.x + threadIdx.x; b < ngas; b += stride) {
 #pragma unroll
-        for (int b = 0; b < kB; ++b) {
-            const int x = x0 + b * stride < ncell ? x0 + b * stride : x0;
-            int q[3];
-            q[0] = x % lay.n[0];
-            q[1] = (x / lay.n[0]) % lay.n[1];
-            q[2] = x / (lay.n[0] * lay.n[1]);
-            const int xe = lay.ext(q);
+        for (int k = 0; k < 4; ++k) gacc[k] += __ldg(gas + 4 * b + k);
+    }
+    // particles (sorted by cell): momentum, and the lattice sum of eps_g of
+    // the current counts.  Every cell adds eps_g(0) (added once, by the last
+    // block) and an occupied cell the difference eps_g(n) - eps_g(0), found
+    // at its first particle, which also flags an over-packed cell; first
+    // particle and count come from the neighbouring entries of the cell
+    // array, so no load waits on another.
+    const Real e0 = eps_tab[0];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride) {
+        const int c = parts.cell[k];
+        const int cp = k > 0 ? parts.cell[k - 1] : -1;
+        const int cn = k + 1 < np ? parts.cell[k + 1] : -1;
+        Real v[3];
 #pragma unroll
-            for (int i = 0; i < Q; ++i)   // population i as the next collision pulls it
-                fv[b][i] = Store<S>::load(f[(long long)i * lay.nce + xe - lay.off<L>(i)]);
-            nn[b] = cells.begin(x + 1) - cells.begin(x);
+        for (int a = 0; a < D; ++a) v[a] = parts.v[a][k];
+        if (cp != c) {
+            int n = 1;
+            if (cn == c)
+                for (n = 2; k + n < np && parts.cell[k + n] == c; ++n) {}
+            acc[7].add(eps_tab[n < ntab ? n : ntab - 1] - e0);
+            if (n > packed_limit) packed = 1;
         }
-        Real ev[kB];
 #pragma unroll
-        for (int b = 0; b < kB; ++b) {
-            ev[b] = eps_tab[nn[b] < ntab ? nn[b] : ntab - 1];
-            if (x0 + b * stride < ncell && nn[b] > packed_limit) packed = 1;
-        }
+        for (int a = 0; a < D; ++a) acc[4 + a].add(v[a]);
+    }
+    // diagnostics: the per-cell fields of the last collision
+    constexpr int kB = 4;
+    for (int x0 = blockIdx.x * blockDim.x + threadIdx.x; BED && x0 < ncell; x0 += kB * stride) {
 #pragma unroll
         for (int b = 0; b < kB; ++b) {
             const int x = x0 + b * stride;
             if (x >= ncell) break;
-            Real sm = Real(0), m[3] = {Real(0), Real(0), Real(0)};
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                sm += fv[b][i];
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    if (L::c(i, a) == 1) m[a] += fv[b][i];
-                    else if (L::c(i, a) == -1) m[a] -= fv[b][i];
-                }
-            }
-            acc[0].add(sm);
-#pragma unroll
-            for (int a = 0; a < D; ++a) acc[1 + a].add(m[a]);
-            acc[7].add(ev[b]);
-            if (BED) {
+            {
                 acc[8].add(fld.eps_g[x]);
                 const int nt = fld.ntot[x];
                 if (nt > 0) {
@@ -123,22 +122,6 @@ k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> 
             }
         }
     }
-    // particles in batches of two
-    for (int k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < np; k0 += 2 * stride) {
-        const int k1 = k0 + stride;
-        Real v0[3], v1[3];
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            v0[a] = parts.v[a][k0];
-            v1[a] = k1 < np ? parts.v[a][k1] : Real(0);
-        }
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            acc[4 + a].add(v0[a]);
-            if (k1 < np) acc[4 + a].add(v1[a]);
-        }
-    }
-
     // block partials: warp sums in the arithmetic type, then the eight warp
     // totals of each value added in FP64 in warp order (one barrier)
     constexpr int kWarps = kRedThreads / 32;
@@ -147,8 +130,13 @@ k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kStatValues; ++k) {
-        const Real t = warp_sum<Real>(acc[k].value());
-        if (lane == 0) sh[warp][k] = (double)t;
+        if (k < 4) {
+            const double t = warp_sum<double>(gacc[k]);
+            if (lane == 0) sh[warp][k] = t;
+        } else {
+            const Real t = warp_sum<Real>(acc[k].value());
+            if (lane == 0) sh[warp][k] = (double)t;
+        }
     }
     if (__syncthreads_or(packed) && threadIdx.x == 0) atomicOr(health_live, HEALTH_PACKED);
     if (threadIdx.x < kStatValues) {
@@ -172,7 +160,7 @@ k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> 
 #pragma unroll 8
         for (int b = lane; b < (int)gridDim.x; b += 32) u += __ldcg(partials + b * kStatValues + k);
         u = warp_sum<double>(u);
-        if (lane == 0) out[k] = (k >= 4 && k < 7) ? mp * u : u;
+        if (lane == 0) out[k] = (k >= 4 && k < 7) ? mp * u : (k == 7 ? u + (double)ncell * (double)e0 : u);
     }
     if (threadIdx.x == 0) {
         // the health word and the outlet count travel with the values, so
@@ -184,23 +172,25 @@ k_reduce_all(PopLayout lay, int ncell, const S *__restrict__ f, Particles<Real> 
     }
 }
 
-template <class L, class Real, class S>
-void launch_reduce_all(const PopLayout &lay, int ncell, const S *f, Particles<Real> parts, double mp,
-                       int np, CellList cells, const Real *eps_tab, int ntab,
+template <class L, class Real>
+void launch_reduce_all(int ncell, const double *gas, long long ngas, Particles<Real> parts, double mp,
+                       int np, const Real *eps_tab, int ntab,
                        const Fields<Real> *bed, double *partials, unsigned *ticket,
                        const unsigned *health, const unsigned long long *solids_out, double *out,
                        unsigned *health_live, int packed_limit, cudaStream_t st)
 {
-    const int n = ncell > np ? ncell : np;
-    int nb = (n + kRedThreads - 1) / kRedThreads;
+    // the cells are walked only for the diagnostics
+    long long n = bed ? (ncell > np ? ncell : np) : np;
+    n = n > ngas ? n : ngas;
+    long long nb = (n + kRedThreads - 1) / kRedThreads;
     nb = nb < 1 ? 1 : (nb > kRedMaxBlocks ? kRedMaxBlocks : nb);
     if (bed)
-        k_reduce_all<L, Real, S, true><<<nb, kRedThreads, 0, st>>>(
-            lay, ncell, f, parts, mp, np, cells, eps_tab, ntab, *bed, partials, ticket, health,
+        k_reduce_all<L, Real, true><<<(int)nb, kRedThreads, 0, st>>>(
+            ncell, gas, ngas, parts, mp, np, eps_tab, ntab, *bed, partials, ticket, health,
             solids_out, out, health_live, packed_limit);
     else
-        k_reduce_all<L, Real, S, false><<<nb, kRedThreads, 0, st>>>(
-            lay, ncell, f, parts, mp, np, cells, eps_tab, ntab, Fields<Real>{}, partials, ticket,
+        k_reduce_all<L, Real, false><<<(int)nb, kRedThreads, 0, st>>>(
+            ncell, gas, ngas, parts, mp, np, eps_tab, ntab, Fields<Real>{}, partials, ticket,
             health, solids_out, out, health_live, packed_limit);
 }
 
@@ -221,19 +211,15 @@ void launch_snapshot(const unsigned *health, const unsigned long long *solids_ou
     k_snapshot<<<1, 32, 0, st>>>(health, solids_out, out);
 }
 
-#define LBDPS_INST_RED(L, R, S)                                                                    \
-    template void launch_reduce_all<L, R, S>(const PopLayout &, int, const S *, Particles<R>,       \
-                                             double, int, CellList, const R *, int,                \
-                                             const Fields<R> *, double *, unsigned *,               \
-                                             const unsigned *, const unsigned long long *,          \
-                                             double *, unsigned *, int, cudaStream_t);
-LBDPS_INST_RED(D2Q9, double, double)
-LBDPS_INST_RED(D2Q9, float, float)
-LBDPS_INST_RED(D2Q9, float, __half)
-LBDPS_INST_RED(D2Q9, float, __nv_bfloat16)
-LBDPS_INST_RED(D3Q19, double, double)
-LBDPS_INST_RED(D3Q19, float, float)
-LBDPS_INST_RED(D3Q19, float, __half)
-LBDPS_INST_RED(D3Q19, float, __nv_bfloat16)
+#define LBDPS_INST_RED(L, R)                                                                       \
+    template void launch_reduce_all<L, R>(int, const double *, long long, Particles<R>, double,      \
+                                          int, const R *, int, const Fields<R> *,                    \
+                                          double *, unsigned *, const unsigned *,                    \
+                                          const unsigned long long *, double *, unsigned *, int,     \
+                                          cudaStream_t);
+LBDPS_INST_RED(D2Q9, double)
+LBDPS_INST_RED(D2Q9, float)
+LBDPS_INST_RED(D3Q19, double)
+LBDPS_INST_RED(D3Q19, float)
 
 }  // namespace lbdpsk
