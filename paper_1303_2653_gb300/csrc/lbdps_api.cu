@@ -112,6 +112,52 @@ Derived derive(const lbdps_lattice_desc &L, const lbdps_particle_desc &Pd, const
     return k;
 }
 
+// ---------------------------------------------------------------------------
+// Host loops over particle arrays, split over the host's cores: f(lo, hi) for
+// consecutive chunks of [0, n).  Large beds hold millions of coordinates, and
+// one core spends milliseconds checking them or taking the first touch of a
+// fresh output array's pages.
+// ---------------------------------------------------------------------------
+template <class F> void host_parallel(size_t n, F &&f, size_t min_chunk = 1 << 16)
+{
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t nt = std::min<size_t>({(size_t)hw, (size_t)16, (n + min_chunk - 1) / min_chunk});
+    if (nt <= 1) {
+        f((size_t)0, n);
+        return;
+    }
+    std::vector<std::thread> pool;
+    pool.reserve(nt - 1);
+    const size_t chunk = (n + nt - 1) / nt;
+    for (size_t t = 1; t < nt; ++t) {
+        const size_t lo = std::min(n, t * chunk), hi = std::min(n, lo + chunk);
+        try {
+            pool.emplace_back([&f, lo, hi] { f(lo, hi); });
+        } catch (...) {   // no thread to be had: run the chunk here
+            f(lo, hi);
+        }
+    }
+    f((size_t)0, std::min(n, chunk));
+    for (auto &th : pool) th.join();
+}
+
+// The first touch of every page of a caller's output array, on all host
+// cores.  A fresh array costs a page fault per page, which a copy from the
+// device would otherwise take one after the other; the stores go to memory
+// that the copy overwrites.
+void touch_pages(void *p, size_t bytes)
+{
+    if (!p || bytes == 0) return;
+    constexpr size_t kPage = 4096;   // the smallest page size: every page is touched
+    volatile char *c = static_cast<volatile char *>(p);
+    host_parallel(
+        (bytes + kPage - 1) / kPage,
+        [&](size_t lo, size_t hi) {
+            for (size_t k = lo; k < hi; ++k) c[k * kPage] = 0;
+        },
+        256);
+}
+
 // Every block carries a guard zone of kGuardBytes right after the bytes that
 // were asked for, filled with kGuardByte at allocation; lbdps_check_guards
 // reports blocks whose guard was overwritten (a kernel that wrote past the
@@ -129,14 +175,12 @@ struct DeviceAlloc {
     bool misaligned = false;     // params.alloc returned a block off a 256-byte boundary
     size_t counted = 0;
     cudaStream_t stream = nullptr;   // the handle's stream: guards are written on it
+    char *slab = nullptr;            // the block get() carves from (begin_slab), or null
+    size_t slab_size = 0, slab_used = 0;
 
-    void *get(size_t asked)
+    // a block of `bytes` from params.alloc or cudaMalloc (null on failure)
+    void *take(size_t bytes)
     {
-        size_t bytes = ((asked + kGuardBytes) + 255) & ~size_t(255);
-        if (count_only) {
-            counted += bytes;
-            return (void *)(uintptr_t)256;   // never dereferenced
-        }
         void *p = nullptr;
         if (alloc) {
             p = alloc(bytes, ctx);
@@ -149,8 +193,44 @@ struct DeviceAlloc {
             cudaGetLastError();
             p = nullptr;
         }
+        if (p) owned.push_back(p);
+        return p;
+    }
+    // Take all of a handle's buffers as one block of `total` bytes (what a
+    // count_only pass of the same get() calls added up): get() then hands
+    // out consecutive pieces of it, so creating a bed costs one allocator
+    // call instead of one per buffer.
+    bool begin_slab(size_t total)
+    {
+        slab = static_cast<char *>(take(total));
+        slab_size = slab ? total : 0;
+        slab_used = 0;
+        return slab != nullptr;
+    }
+    // later get() calls (buffers a bed takes on first use) allocate again
+    // (the block stays owned)
+    void end_slab()
+    {
+        slab = nullptr;
+        slab_size = slab_used = 0;
+    }
+    void *get(size_t asked)
+    {
+        size_t bytes = ((asked + kGuardBytes) + 255) & ~size_t(255);
+        if (count_only) {
+            counted += bytes;
+            return (void *)(uintptr_t)256;   // never dereferenced
+        }
+        void *p = nullptr;
+        if (slab) {
+            if (slab_used + bytes <= slab_size) {
+                p = slab + slab_used;
+                slab_used += bytes;
+            }
+        } else {
+            p = take(bytes);
+        }
         if (p) {
-            owned.push_back(p);
             char *g = static_cast<char *>(p) + asked;
             if (cudaMemsetAsync(g, kGuardByte, kGuardBytes, stream) != cudaSuccess) {
                 cudaGetLastError();
@@ -213,6 +293,7 @@ struct DeviceAlloc {
         }
         owned.clear();
         guards.clear();
+        end_slab();
     }
 };
 
@@ -220,13 +301,16 @@ struct DeviceAlloc {
 struct Engine {
     virtual ~Engine() {}
     virtual int allocate(DeviceAlloc &A) = 0;
-    virtual int upload_initial(const double *pos_lat, const double *vel_lat) = 0;
+    // particles as the caller holds them (id order, interleaved), converted
+    // on the device: positions / pos_div, velocities * vel_mul
+    virtual int upload_initial(const double *pos, const double *vel, double pos_div, double vel_mul) = 0;
     // gas_stats: the collision also writes the per-block moment sums of the
     // state it reads (parity `parity`) into that parity's gas partials
     virtual int enqueue_step(int parity, cudaEvent_t *ev, bool gas_stats = false) = 0;
     virtual int fields(int mask, int units, double *out, size_t cap) = 0;
     virtual int particles(int units, double *pos, double *vel, int64_t cap) = 0;
-    virtual int set_particles(const double *pos, const double *vel) = 0;
+    virtual int set_particles(const double *pos, const double *vel, double pos_div = 1.0,
+                              double vel_mul = 1.0) = 0;
     virtual int spin(int units, double *out, int64_t cap) = 0;
     virtual int set_spin(const double *in) = 0;
     virtual int populations(double *f, size_t cap) = 0;
@@ -529,7 +613,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
         p.gas_partials = nullptr;
     }
 
-    int upload_initial(const double *pos_lat, const double *vel_lat) override
+    int upload_initial(const double *pos, const double *vel, double pos_div, double vel_mul) override
     {
         cudaStream_t st = H->stream;
         const Derived &k = H->k;
@@ -555,11 +639,13 @@ template <class L, class Real, class S> struct EngineT : Engine {
             if (rc == LBDPS_OK) rc = clear_cells(1);
             return rc;
         }
-        return set_particles(pos_lat, vel_lat);
+        return set_particles(pos, vel, pos_div, vel_mul);
     }
 
-    // Load particles (lattice units, id order) into the current buffers and sort them.
-    int set_particles(const double *pos, const double *vel) override
+    // Load particles (id order; lattice units once positions are divided by
+    // pos_div and velocities multiplied by vel_mul) into the current buffers
+    // and sort them.
+    int set_particles(const double *pos, const double *vel, double pos_div, double vel_mul) override
     {
         cudaStream_t st = H->stream;
         const int np = H->np;
@@ -575,7 +661,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
             cudaError_t e = cudaMemcpyAsync(dp, pos, bytes, cudaMemcpyHostToDevice, st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(dv, vel, bytes, cudaMemcpyHostToDevice, st);
             if (e == cudaSuccess) {
-                launch_particles_from_host_order<D, Real>(dp, dv, np, part[nxt], st);
+                launch_particles_from_host_order<D, Real>(dp, dv, np, pos_div, vel_mul, part[nxt], st);
                 e = cudaGetLastError();
             }
             const cudaError_t e2 = cudaStreamSynchronize(st);
@@ -598,8 +684,8 @@ template <class L, class Real, class S> struct EngineT : Engine {
         // stage into the next buffers, then sort into the current ones
         for (int a = 0; a < D; ++a) {
             for (int i = 0; i < np; ++i) {
-                Pa[i] = pos[(size_t)i * D + a];
-                va[i] = (Real)vel[(size_t)i * D + a];
+                Pa[i] = pos[(size_t)i * D + a] / pos_div;
+                va[i] = (Real)(vel[(size_t)i * D + a] * vel_mul);
             }
             CU(cudaMemcpyAsync(part[nxt].P[a], Pa.data(), sizeof(double) * np,
                                cudaMemcpyHostToDevice, st));
@@ -861,6 +947,9 @@ template <class L, class Real, class S> struct EngineT : Engine {
             cudaStream_t st = H->stream;
             launch_particles_to_host_order<D, Real>(part[cur], np, ps, vs, dp, dv, st);
             cudaError_t e = cudaGetLastError();
+            // while the kernel runs
+            touch_pages(pos, bytes);
+            touch_pages(vel, bytes);
             if (e == cudaSuccess && pos) e = cudaMemcpyAsync(pos, dp, bytes, cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess && vel) e = cudaMemcpyAsync(vel, dv, bytes, cudaMemcpyDeviceToHost, st);
             const cudaError_t e2 = cudaStreamSynchronize(st);
@@ -1245,51 +1334,32 @@ Engine *make_engine_l(lbdps *h)
 }
 
 // ---------------------------------------------------------------------------
-// Host loops over particle arrays, split over the host's cores: f(lo, hi) for
-// consecutive chunks of [0, n).  Large beds hold millions of coordinates, and
-// one core spends tens of milliseconds converting and checking them.
-// ---------------------------------------------------------------------------
-template <class F> void host_parallel(size_t n, F &&f)
-{
-    constexpr size_t kMinChunk = 1 << 16;
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const size_t nt = std::min<size_t>({(size_t)hw, (size_t)16, (n + kMinChunk - 1) / kMinChunk});
-    if (nt <= 1) {
-        f((size_t)0, n);
-        return;
-    }
-    std::vector<std::thread> pool;
-    pool.reserve(nt - 1);
-    const size_t chunk = (n + nt - 1) / nt;
-    for (size_t t = 1; t < nt; ++t) {
-        const size_t lo = std::min(n, t * chunk), hi = std::min(n, lo + chunk);
-        try {
-            pool.emplace_back([&f, lo, hi] { f(lo, hi); });
-        } catch (...) {   // no thread to be had: run the chunk here
-            f(lo, hi);
-        }
-    }
-    f((size_t)0, std::min(n, chunk));
-    for (auto &th : pool) th.join();
-}
-
-// ---------------------------------------------------------------------------
 // Validation helpers.
 // ---------------------------------------------------------------------------
-int validate_positions(const lbdps *h, const double *pos)
+// positions of the caller (id order, interleaved) inside the lattice once
+// divided by pos_div (the cell size for SI positions, 1 for lattice units)
+int validate_positions(const lbdps *h, const double *pos, double pos_div)
 {
     const int D = h->dim, np = h->np;
+    // below safe[a] = (n_a - 1) pos_div a coordinate is inside without the
+    // division: x < fl((n - 1) h) gives fl(x / h) <= (n - 1)(1 + 2^-52)^2 < n
+    double safe[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < D; ++a) safe[a] = (double)(h->n[a] - 1) * pos_div;
     // the first particle (smallest index) outside the domain, as one loop
     // in index order would find it
     std::mutex mu;
     size_t first = SIZE_MAX;
-    host_parallel((size_t)np * D, [&](size_t lo, size_t hi) {
-        for (size_t e = lo; e < hi; ++e) {
-            const double p = pos[e];
-            if (!(p >= 0.0 && p < (double)h->n[e % D])) {
-                std::lock_guard<std::mutex> lock(mu);
-                first = std::min(first, e);
-                return;
+    host_parallel((size_t)np, [&](size_t lo, size_t hi) {
+        for (size_t i = lo; i < hi; ++i) {
+            for (int a = 0; a < D; ++a) {
+                const double x = pos[i * D + a];
+                if (x >= 0.0 && x < safe[a]) continue;
+                const double p = x / pos_div;
+                if (!(p >= 0.0 && p < (double)h->n[a])) {
+                    std::lock_guard<std::mutex> lock(mu);
+                    first = std::min(first, i * D + a);
+                    return;
+                }
             }
         }
     });
@@ -1558,22 +1628,12 @@ extern "C" {
 
 }  // extern "C"
 
-// A host array of doubles whose pages are first touched by whoever fills it.
-struct HostArray {
-    std::unique_ptr<double[]> p;
-    bool allocate(size_t n)
-    {
-        p.reset(new (std::nothrow) double[std::max<size_t>(n, 1)]);
-        return p != nullptr;
-    }
-    double *data() const { return p.get(); }
-};
-
-// Validation, derived constants and lattice-unit particles of a description
-// (no device work).  Shared by lbdps_create and lbdps_memory_estimate.
+// Validation and derived constants of a description, the particles checked
+// in place (no device work; the conversion to lattice units happens on the
+// device as they are loaded).  Shared by lbdps_create and
+// lbdps_memory_estimate.
 static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
-                       const lbdps_params *prm, std::unique_ptr<lbdps> &hout,
-                       HostArray &pos, HostArray &vel)
+                       const lbdps_params *prm, std::unique_ptr<lbdps> &hout)
 {
     if (!lat || !par || !prm) return fail(LBDPS_ERR_INVALID, "NULL description");
     const int D = lat->dim;
@@ -1688,19 +1748,8 @@ static int prepare_bed(const lbdps_lattice_desc *lat, const lbdps_particle_desc 
             }
         }
     }
-    // particles in lattice units (the arrays are filled by the threads that
-    // convert them, so their pages are first touched in parallel too)
-    const size_t ne = (size_t)h->np * D;
-    if (!pos.allocate(ne) || !vel.allocate(ne)) return fail(LBDPS_ERR_OOM, "host allocation failed");
-    const double vscale = lat->dt / lat->h;
-    double *pd = pos.data(), *vd = vel.data();
-    host_parallel(ne, [&](size_t lo, size_t hi) {
-        for (size_t i = lo; i < hi; ++i) {
-            pd[i] = par->pos[i] / lat->h;
-            vd[i] = par->vel[i] * vscale;
-        }
-    });
-    int rc = validate_positions(h.get(), pos.data());
+    // particles inside the lattice (positions in lattice units are pos / h)
+    int rc = validate_positions(h.get(), par->pos, lat->h);
     if (rc) return rc;
     hout = std::move(h);
     return LBDPS_OK;
@@ -1713,8 +1762,7 @@ int lbdps_memory_estimate(const lbdps_lattice_desc *lat, const lbdps_particle_de
 {
     if (!bytes) return fail(LBDPS_ERR_INVALID, "bytes is NULL");
     std::unique_ptr<lbdps> h;
-    HostArray pos, vel;
-    int rc = prepare_bed(lat, par, prm, h, pos, vel);
+    int rc = prepare_bed(lat, par, prm, h);
     if (rc) return rc;
     h->mem.count_only = true;
     h->eng.reset(h->dim == 2 ? make_engine_l<D2Q9>(h.get()) : make_engine_l<D3Q19>(h.get()));
@@ -1731,10 +1779,9 @@ int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
     if (!out) return fail(LBDPS_ERR_INVALID, "out is NULL");
     *out = nullptr;
     std::unique_ptr<lbdps> h;
-    HostArray pos, vel;
     // the pairwise overlap test of hard spheres runs on the device once the
     // particles are sorted (below); the host checks the domain only
-    int rc = prepare_bed(lat, par, prm, h, pos, vel);
+    int rc = prepare_bed(lat, par, prm, h);
     if (rc) return rc;
     const int D = h->dim;
 
@@ -1756,11 +1803,20 @@ int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
         if (h->own_stream) cudaStreamDestroy(h->stream);
         return code;
     };
-    if ((rc = h->eng->allocate(h->mem))) {
+    // one block for all of the bed's buffers, sized by a counting pass of
+    // the same allocation
+    h->mem.count_only = true;
+    rc = h->eng->allocate(h->mem);
+    h->mem.count_only = false;
+    if (rc) return cleanup(rc);
+    if (!h->mem.begin_slab(h->mem.counted)) {
         if (h->mem.misaligned)
-            rc = fail(LBDPS_ERR_INVALID, "params.alloc returned a block that is not 256-byte aligned");
-        return cleanup(rc);
+            return cleanup(fail(LBDPS_ERR_INVALID, "params.alloc returned a block that is not 256-byte aligned"));
+        return cleanup(fail(LBDPS_ERR_OOM, "device allocation of %zu bytes failed", h->mem.counted));
     }
+    rc = h->eng->allocate(h->mem);
+    h->mem.end_slab();
+    if (rc) return cleanup(rc);
     // mapped: the statistics reduction writes its results here directly
     if (cudaHostAlloc(&h->health_host, 256, cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
@@ -1768,7 +1824,7 @@ int lbdps_create(const lbdps_lattice_desc *lat, const lbdps_particle_desc *par,
     }
     static_assert(sizeof(double) * kStatOut <= 128, "statistics fit the pinned block");
     h->stats_host = reinterpret_cast<double *>(reinterpret_cast<char *>(h->health_host) + 128);
-    if ((rc = h->eng->upload_initial(pos.data(), vel.data()))) {
+    if ((rc = h->eng->upload_initial(par->pos, par->vel, lat->h, lat->dt / lat->h))) {
         cudaFreeHost(h->health_host);
         return cleanup(rc);
     }
@@ -1879,7 +1935,7 @@ int lbdps_set_particles(lbdps_t *h, int64_t n, const double *pos, const double *
 {
     if (!h || (n > 0 && (!pos || !vel))) return fail(LBDPS_ERR_INVALID, "bad arguments");
     if (n != h->np) return fail(LBDPS_ERR_INVALID, "particle count must stay %d", h->np);
-    int rc = validate_positions(h, pos);
+    int rc = validate_positions(h, pos, 1.0);
     if (rc) return rc;
     CU(cudaStreamSynchronize(h->stream));
     rc = h->eng->set_particles(pos, vel);

@@ -363,11 +363,12 @@ void launch_cell_keys(const int *n, Particles<Real> parts, int *key, int *counts
 template <int D, class Real>
 void launch_particles_to_host_order(Particles<Real> parts, int np, double ps, double vs,
                                     double *pos, double *vel, cudaStream_t st);
-// Interleaved id-order positions and velocities (np x D, lattice units) into
-// the SoA arrays of dst, with ids 0..np-1 and spins (if any) at rest.
+// Interleaved id-order positions and velocities (np x D) into the SoA arrays
+// of dst in lattice units (positions / pos_div, velocities * vel_mul, both
+// correctly rounded in FP64), with ids 0..np-1 and spins (if any) at rest.
 template <int D, class Real>
-void launch_particles_from_host_order(const double *pos, const double *vel, int np,
-                                      Particles<Real> dst, cudaStream_t st);
+void launch_particles_from_host_order(const double *pos, const double *vel, int np, double pos_div,
+                                      double vel_mul, Particles<Real> dst, cudaStream_t st);
 
 // one-launch scan of counts[0..ncell] (counts[ncell] = 0) into a CellList
 void launch_cell_scan(const int *counts, CellListOut out, int ncell, cudaStream_t st);

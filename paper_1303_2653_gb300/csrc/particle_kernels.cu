@@ -452,15 +452,16 @@ void launch_particles_to_host_order(Particles<Real> parts, int np, double ps, do
 
 template <int D, class Real>
 __global__ void k_particles_from_host_order(const double *pos, const double *vel, int np,
-                                            Particles<Real> dst)
+                                            double pos_div, double vel_mul, Particles<Real> dst)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
     constexpr int NW = D == 2 ? 1 : 3;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        dst.P[a][i] = pos[(size_t)i * D + a];
-        dst.v[a][i] = (Real)vel[(size_t)i * D + a];
+        // correctly rounded FP64 division and product, as on the host
+        dst.P[a][i] = __ddiv_rn(pos[(size_t)i * D + a], pos_div);
+        dst.v[a][i] = (Real)__dmul_rn(vel[(size_t)i * D + a], vel_mul);
     }
     dst.id[i] = i;
     if (dst.w[0])
@@ -469,11 +470,12 @@ __global__ void k_particles_from_host_order(const double *pos, const double *vel
 }
 
 template <int D, class Real>
-void launch_particles_from_host_order(const double *pos, const double *vel, int np,
-                                      Particles<Real> dst, cudaStream_t st)
+void launch_particles_from_host_order(const double *pos, const double *vel, int np, double pos_div,
+                                      double vel_mul, Particles<Real> dst, cudaStream_t st)
 {
     if (np == 0) return;
-    k_particles_from_host_order<D, Real><<<(np + 255) / 256, 256, 0, st>>>(pos, vel, np, dst);
+    k_particles_from_host_order<D, Real><<<(np + 255) / 256, 256, 0, st>>>(pos, vel, np, pos_div,
+                                                                           vel_mul, dst);
 }
 
 // ---------------------------------------------------------------------------
@@ -1158,7 +1160,8 @@ void launch_particles_batched(const BatchBed *beds, BatchWork work, int step, cu
     template void launch_particles_to_host_order<D, R>(Particles<R>, int, double, double, double *, \
                                                        double *, cudaStream_t);                    \
     template void launch_particles_from_host_order<D, R>(const double *, const double *, int,       \
-                                                         Particles<R>, cudaStream_t);              \
+                                                         double, double, Particles<R>,             \
+                                                         cudaStream_t);                            \
     template void launch_overlaps<D, R>(const StepParams<R> &, Particles<R>, CellList,              \
                                         unsigned long long *, unsigned long long *, int,            \
                                         cudaStream_t);

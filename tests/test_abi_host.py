@@ -128,6 +128,50 @@ def test_create_rejects_invalid_descriptions_on_host(lib, bad, msg):
     assert msg.encode() in lib.lib().lbdps_last_error()
 
 
+def _create(lib, **over):
+    lat, par, prm, keep = _desc(lib, **over)
+    h = ctypes.c_void_p()
+    rc = lib.lib().lbdps_create(ctypes.byref(lat), ctypes.byref(par), ctypes.byref(prm),
+                                ctypes.byref(h))
+    if h.value:
+        lib.lib().lbdps_destroy(h)
+    return rc, lib.lib().lbdps_last_error()
+
+
+def test_domain_check_at_the_fp64_boundary(lib):
+    # a particle is inside when its position in lattice units, the correctly
+    # rounded FP64 quotient x / h, lies in [0, n); the host check skips the
+    # division for coordinates well inside, so probe the exact edge: the
+    # smallest x whose quotient reaches n is rejected, the next double below
+    # passes the host check (what follows needs a device)
+    h, n = 1e-3, 8
+    x = n * h
+    while x / h >= n:
+        x = np.nextafter(x, 0.0)
+    edge = np.nextafter(x, np.inf)
+    assert edge / h >= n and x / h < n
+    rc, msg = _create(lib, pos=[[edge, 2.5e-3]])
+    assert rc == lib.ERR_INVALID and b"particle 0 lies outside the domain on axis 0" in msg
+    rc, msg = _create(lib, pos=[[x, 2.5e-3]])
+    assert b"outside the domain" not in msg
+    rc, msg = _create(lib, pos=[[2.5e-3, -0.0]])   # -0 / h = -0 >= 0: inside
+    assert b"outside the domain" not in msg
+
+
+def test_domain_check_reports_the_first_particle_outside(lib):
+    # the smallest index in (particle, axis) order, as one loop in index
+    # order finds it, whichever host thread meets which particle first
+    npart = 300000
+    pos = np.full((npart, 2), 2.5e-3)
+    pos[:, 0] = np.linspace(0.5e-3, 7.5e-3, npart)
+    pos[123457, 1] = -1e-300
+    pos[200001, 0] = 9e-3
+    pos[250000, 1] = 8e-3
+    rc, msg = _create(lib, pos=pos)
+    assert rc == lib.ERR_INVALID
+    assert b"particle 123457 lies outside the domain on axis 1" in msg
+
+
 def test_noalloc_sort_rejects_oversize_on_host(lib):
     nn = (ctypes.c_int * 3)(4096, 4096, 1)
     pp = (ctypes.c_void_p * 3)(1, 1, None)
