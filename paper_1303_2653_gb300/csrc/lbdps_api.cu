@@ -304,7 +304,7 @@ struct Engine {
     // particles as the caller holds them (id order, interleaved), converted
     // on the device: positions / pos_div, velocities * vel_mul
     virtual int upload_initial(const double *pos, const double *vel, double pos_div, double vel_mul) = 0;
-    // gas_stats: the collision also writes the per-block moment sums of the
+    // gas_stats: the collision also writes the per-warp moment sums of the
     // state it reads (parity `parity`) into that parity's gas partials
     virtual int enqueue_step(int parity, cudaEvent_t *ev, bool gas_stats = false) = 0;
     virtual int fields(int mask, int units, double *out, size_t cap) = 0;
@@ -411,7 +411,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
     unsigned long long *ovl_dev = nullptr;      // overlap check: count, smallest pair
     unsigned long long *snap_dev = nullptr;     // 2 slots x (health word, outlet count)
     double *gas_part[2] = {nullptr, nullptr};   // per parity: moment sums of the collision's warps
-    long long gas_blocks = 0;
+    long long gas_warps = 0;   // groups of 4 doubles in each gas_part buffer
     StepParams<Real> sp{};
     PopLayout lay{};          // extended lattice of the population arrays
     int packed_limit = 0;     // more particle centres per cell cannot all be apart
@@ -500,9 +500,9 @@ template <class L, class Real, class S> struct EngineT : Engine {
         npairs_dev = (unsigned long long *)get(sizeof(unsigned long long));
         ovl_dev = (unsigned long long *)get(2 * sizeof(unsigned long long));
         snap_dev = (unsigned long long *)get(4 * sizeof(unsigned long long));
-        gas_blocks = collide_warps(D, H->n);
+        gas_warps = collide_warps(D, H->n);
         for (int b = 0; b < 2; ++b) {
-            gas_part[b] = (double *)get(sizeof(double) * 4 * (size_t)gas_blocks);
+            gas_part[b] = (double *)get(sizeof(double) * 4 * (size_t)gas_warps);
             if (!gas_part[b]) return fail(LBDPS_ERR_OOM, "device allocation failed");
         }
         void *must[] = {f[0], f[1], cl_local[0], cl_local[1], cl_base[0], cl_base[1], fld.rho,
@@ -1111,7 +1111,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
         CU(cudaHostGetDevicePointer((void **)&dev, dst, 0));
         launch_gas_moments<L, Real, S>(lay, f[cur], H->n, gas_part[cur], H->stream);
         CHECK_LAUNCH();
-        launch_reduce_all<L, Real>(H->ncell, gas_part[cur], gas_blocks, part[cur], H->k.mp, H->np,
+        launch_reduce_all<L, Real>(H->ncell, gas_part[cur], gas_warps, part[cur], H->k.mp, H->np,
                                    sp.tab.eps_g, H->ntab, bed ? &fld : nullptr,
                                    red_partials, red_ticket, health_dev, solids_out, dev, health_dev,
                                    packed_limit, H->stream);
@@ -1125,7 +1125,7 @@ template <class L, class Real, class S> struct EngineT : Engine {
         CU(cudaHostGetDevicePointer((void **)&dev, dst, 0));
         const unsigned long long *sn = snap_dev + 2 * slot;
         // no node diagnostics: the next step has rewritten those arrays
-        launch_reduce_all<L, Real>(H->ncell, gas_part[q], gas_blocks, part[q], H->k.mp, H->np,
+        launch_reduce_all<L, Real>(H->ncell, gas_part[q], gas_warps, part[q], H->k.mp, H->np,
                                    sp.tab.eps_g, H->ntab, nullptr, red_partials, red_ticket,
                                    reinterpret_cast<const unsigned *>(sn), sn + 1, dev, health_dev,
                                    packed_limit, H->stream);
@@ -1488,7 +1488,7 @@ constexpr int kMonSteps = 1024;
 // Monitored steps with the statistics fused into the next collision.  The
 // statistics of the state after step s need the gas mass and momentum of
 // that state, which the collision of step s + 1 reads anyway: its graph
-// (capture_monitored_step) has the collision write the per-block moment
+// (capture_monitored_step) has the collision write the per-warp moment
 // sums of its input state into that parity's gas partials.  The reduction of
 // the state after step s then runs right after step s + 1 on the same
 // stream; it reads only those partials, the cell list and the particles of

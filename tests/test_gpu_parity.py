@@ -538,15 +538,23 @@ def test_monitored_steps_equal_step_and_stats():
     b.close()
 
 
-@pytest.mark.parametrize("name", ["riser2d", "cfb"])
+@pytest.mark.parametrize("name", ["riser2d", "cfb", "riser2d_ragged", "riser3d_odd"])
 def test_overlapped_monitored_steps_equal_step_and_stats(name):
-    # without node diagnostics each step's reduction runs beside the next
-    # step on a second stream, with the health word and outlet count taken
-    # from a snapshot at the end of its step: the records equal lbdps_stats
-    # taken after each step of a bed stepped one at a time
+    # without node diagnostics the collision of step s + 1 sums the gas
+    # moments of the state after step s per warp, and that state's reduction
+    # runs after it with the health word and outlet count taken from a
+    # snapshot at the end of step s: the records equal lbdps_stats (a
+    # moment-only pass with the same warps) taken after each step of a bed
+    # stepped one at a time.  Rows of 45 and 15 cells leave warps with lanes
+    # past the lattice, which sum their moments before the collision.
     L = _lb()
     if name == "riser2d":
         w = W.scaled_riser2d(nx=32, ny=64, seed=44)
+    elif name == "riser2d_ragged":
+        w = W.scaled_riser2d(nx=45, ny=64, seed=45)
+    elif name == "riser3d_odd":
+        w = W.scaled_riser3d(nx=15, ny=17, nz=33, n_particles=1700, solid_fraction=0.08,
+                             sigma_v=0.4, seed=46)
     else:   # particles leave through the outlet every few steps
         w = _cfb_column(W.STORE_F32, n=200)
     a = L.Bed(w)
@@ -571,8 +579,8 @@ def test_overlapped_monitored_steps_equal_step_and_stats(name):
 def test_no_kernel_writes_past_its_buffers():
     # every device block carries a guard zone; run each entry point that
     # launches kernels on beds large enough for the multi-block paths (the
-    # statistics reduction runs its maximum of 152 blocks of 512 threads
-    # above 77,824 cells or particles) and check that no guard was touched
+    # statistics reduction runs its maximum of 608 blocks of 512 threads
+    # above 311,296 cells or particles) and check that no guard was touched
     L = _lb()
     for w, st in [(W.riser2d(nx=256, ny=1536, n_particles=100000), W.STORE_F32),
                   (W.scaled_riser3d(nx=48, ny=48, nz=128), W.STORE_F16),
