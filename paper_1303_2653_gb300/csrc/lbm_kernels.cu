@@ -132,18 +132,22 @@ __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float sqrt_pos(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 __device__ __forceinline__ double sqrt_pos(double x) { return sqrt(x); }
 
-// Blocks per SM requested from the register allocator: D2Q9 in FP32 fits in
-// ~40 registers (6 blocks of 256 threads), D3Q19 and FP64 need more.
-template <class L, class Real> struct K2Occupancy { static constexpr int value = 4; };
+// The collision runs blocks of kCollideThreads threads (a row of up to that
+// many cells).  Blocks per SM requested from the register allocator: D2Q9 in
+// FP32 fits in ~40 registers (12 blocks); D3Q19 in FP32 takes 56 (9 blocks,
+// 36 warps per SM: against 8 blocks at 64 registers, the 16-bit storages
+// run 8-9 % faster, FP32 the same); FP64 needs more.
+constexpr int kCollideThreads = 128;
+template <class L, class Real> struct K2Occupancy { static constexpr int value = 8; };
 #ifndef LBDPS_K2_BLOCKS_D2Q9_F32
-#define LBDPS_K2_BLOCKS_D2Q9_F32 6
+#define LBDPS_K2_BLOCKS_D2Q9_F32 12
 #endif
 #ifndef LBDPS_K2_BLOCKS_D3Q19_F32
-#define LBDPS_K2_BLOCKS_D3Q19_F32 4
+#define LBDPS_K2_BLOCKS_D3Q19_F32 9
 #endif
 template <> struct K2Occupancy<D2Q9, float> { static constexpr int value = LBDPS_K2_BLOCKS_D2Q9_F32; };
 template <> struct K2Occupancy<D3Q19, float> { static constexpr int value = LBDPS_K2_BLOCKS_D3Q19_F32; };
-template <> struct K2Occupancy<D3Q19, double> { static constexpr int value = 2; };
+template <> struct K2Occupancy<D3Q19, double> { static constexpr int value = 4; };
 
 // Streaming across the faces of the lattice (Eq. 2 with the boundary rules),
 // run by the cells on a face after their own post-collision values are
@@ -559,7 +563,7 @@ template <class Real> struct WarpMomentsHook {
 // tables) have gone out with the populations; a warp at the end of a row
 // with lanes past the lattice adds them first, from loads of its own.
 template <class L, class Real, class S, bool LES, bool FB, bool STATS>
-__global__ void __launch_bounds__(256, K2Occupancy<L, Real>::value)
+__global__ void __launch_bounds__(kCollideThreads, K2Occupancy<L, Real>::value)
 k_collide_stream(StepParams<Real> p, PopLayout lay, PopPtrs<S> pp, CellList cells,
                  Particles<Real> parts, Fields<Real> fld)
 {
@@ -608,9 +612,12 @@ k_gas_moments(PopLayout lay, PopPtrs<S> pp, int n0, double *partials)
     warp_gas_partials<Real>(mom, partials + 4 * grid_warp_index());
 }
 
-// the collision's launch shape: one block row per lattice row, up to 256
+// the collision's launch shape: blocks along each lattice row, up to 128
 // threads along x
-static inline int collide_tx(int n0) { return n0 >= 256 ? 256 : ((n0 + 31) / 32) * 32; }
+static inline int collide_tx(int n0)
+{
+    return n0 >= kCollideThreads ? kCollideThreads : ((n0 + 31) / 32) * 32;
+}
 
 long long collide_warps(int dim, const int *n)
 {
@@ -641,7 +648,7 @@ void launch_collide_stream(const StepParams<Real> &p, const PopLayout &lay, cons
         pp.pull[i] = fin + (long long)i * lay.nce - lay.off<L>(i);
         pp.own[i] = fout + (long long)i * lay.nce;
     }
-    // one block row per lattice row; up to 256 threads along x
+    // blocks along each lattice row, up to kCollideThreads threads along x
     const int tx = collide_tx(p.n[0]);
     const dim3 grid((p.n[0] + tx - 1) / tx, p.n[1], L::D == 3 ? p.n[2] : 1);
     const bool les = p.les_k > Real(0), fb = p.has_fb != 0;
