@@ -98,28 +98,20 @@ k_reduce_all(int ncell, const double *__restrict__ gas, long long ngas, Particle
         for (int a = 0; a < D; ++a) acc[4 + a].add(v[a]);
     }
     // diagnostics: the per-cell fields of the last collision
-    constexpr int kB = 4;
-    for (int x0 = blockIdx.x * blockDim.x + threadIdx.x; BED && x0 < ncell; x0 += kB * stride) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; BED && x < ncell; x += stride) {
+        acc[8].add(fld.eps_g[x]);
+        const int nt = fld.ntot[x];
+        if (nt > 0) {
+            const auto r4 = fld.node4[x];
+            const Real ua[3] = {r4.x, r4.y, D == 3 ? r4.z : Real(0)};
+            Real s2 = Real(0);
 #pragma unroll
-        for (int b = 0; b < kB; ++b) {
-            const int x = x0 + b * stride;
-            if (x >= ncell) break;
-            {
-                acc[8].add(fld.eps_g[x]);
-                const int nt = fld.ntot[x];
-                if (nt > 0) {
-                    const auto r4 = fld.node4[x];
-                    const Real ua[3] = {r4.x, r4.y, D == 3 ? r4.z : Real(0)};
-                    Real s2 = Real(0);
-#pragma unroll
-                    for (int a = 0; a < D; ++a) {
-                        const Real d = ua[a] - fld.vs[a][x];
-                        s2 += d * d;
-                    }
-                    acc[9].add(Real(nt) * sqrt(s2));
-                    acc[10].add(Real(nt));
-                }
+            for (int a = 0; a < D; ++a) {
+                const Real d = ua[a] - fld.vs[a][x];
+                s2 += d * d;
             }
+            acc[9].add(Real(nt) * sqrt(s2));
+            acc[10].add(Real(nt));
         }
     }
     // block partials: warp sums in the arithmetic type, then the eight warp
