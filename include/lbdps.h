@@ -210,9 +210,11 @@ int lbdps_step(lbdps_t *h, int64_t nsteps);
  * after every one of them, without a host wait between steps: each step's
  * reduction writes its results straight into mapped pinned host memory and
  * the host waits once per 1,024 steps.  Without node diagnostics (and with
- * graphs) the reduction of step s runs on a second stream beside step s + 1,
- * reading the health word and outlet count from a snapshot taken at the end
- * of step s; mean_slip is then NaN.  out receives nsteps records (host
+ * graphs) the collision of step s + 1 also sums the gas mass and momentum of
+ * the state after step s, whose reduction then runs right after step s + 1
+ * on the handle's stream, reading the health word and outlet count from a
+ * snapshot taken at the end of step s; mean_slip is then NaN.  The records
+ * equal lbdps_stats taken after each step.  out receives nsteps records (host
  * array, caller-owned), record k describing the state after step k + 1 of the
  * call.  With check_every > 0, LBDPS_ERR_DIVERGED / _DOMAIN as lbdps_step;
  * LBDPS_ERR_OOM if the pinned buffer cannot be had. */

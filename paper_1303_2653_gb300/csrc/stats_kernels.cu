@@ -186,8 +186,8 @@ void launch_reduce_all(int ncell, const double *gas, long long ngas, Particles<R
             health, solids_out, out, health_live, packed_limit);
 }
 
-// The health word and the outlet count at the end of a step, for a
-// reduction that runs beside the next step on another stream.
+// The health word and the outlet count at the end of a step, for the
+// reduction of that step's state, which runs after the next step.
 __global__ void k_snapshot(const unsigned *health, const unsigned long long *solids_out,
                            unsigned long long *out)
 {
