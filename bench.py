@@ -327,16 +327,25 @@ def reference_main(args, rank, world):
     full = workload(args.storage, args.workload)
     total = args.steps + args.warmup
     per_step_budget = 120.0 / max(total, 1)
-    # oracle cost is close to 1.2 us per cell (2D) at these densities
+    # oracle cost is close to 1.2 us per cell (2D) and at most 3 us (3D) at
+    # these densities; the sample keeps the full cross-section and takes
+    # fewer rows (planes) along the vertical axis, and only once that is at
+    # its floor a smaller cross-section too, at the same solid fraction
     if full.dim == 2:
-        ny = int(max(8, min(full.n[1], per_step_budget / 1.2e-6 / full.n[0])))
-        sample = W.scaled_riser2d(nx=full.n[0], ny=ny, n_particles=int(round(
-            full.n_particles * ny / full.n[1])), storage=W.STORE_F64)
+        cells = per_step_budget / 1.2e-6
+        ny = int(max(8, min(full.n[1], cells / full.n[0])))
+        nx = int(max(16, min(full.n[0], cells / ny)))
+        sample = W.scaled_riser2d(nx=nx, ny=ny, n_particles=int(round(
+            full.n_particles * nx * ny / full.ncell)), storage=W.STORE_F64)
     else:
+        cells = per_step_budget / 3.0e-6
         plane = full.n[0] * full.n[1]
-        nz = int(max(4, min(full.n[2], per_step_budget / 3.0e-6 / plane)))
-        sample = W.scaled_riser3d(nx=full.n[0], ny=full.n[1], nz=nz, n_particles=int(round(
-            full.n_particles * nz / full.n[2])), storage=W.STORE_F64)
+        nz = int(max(4, min(full.n[2], cells / plane)))
+        side = min(1.0, math.sqrt(cells / (nz * plane)))
+        nx = int(max(16, round(full.n[0] * side)))
+        ny = int(max(16, round(full.n[1] * side)))
+        sample = W.scaled_riser3d(nx=nx, ny=ny, nz=nz, n_particles=int(round(
+            full.n_particles * nx * ny * nz / full.ncell)), storage=W.STORE_F64)
     bed = O.OracleBed(sample)
     bed.step(args.warmup)
     t0 = time.perf_counter()
