@@ -90,3 +90,32 @@ def test_drag_step_bytes_and_kernel_roofline():
     r = bench.kernel_roofline(2e9, 1.0, 4000.0)     # 2 GB in 1 ms: 2,000 GB/s
     assert r["achieved"] == pytest.approx(2000.0) and r["frac"] == pytest.approx(0.5)
     assert bench.kernel_roofline(2e9, 0.0, 4000.0) is None
+
+
+def test_step_byte_models_match_the_planned_figures():
+    # B_ideal = N_cells (2 Q s_f + c_cell) + N_p 4 s_p, c_cell = the 4-byte
+    # cell-list offset + rho, u and F_p->g read by the drag; the planned
+    # figures per configuration: 1.80 MB (bubbling 64 x 128, FP64, 2,000
+    # particles), 69.5 MB (riser 256 x 2048, 200,000), 50.7 MB (the same in
+    # 16-bit storage), 12.92 GB (3D riser 256 x 256 x 1024, 4,000,000)
+    import types
+    import bench
+
+    def shape(dim, n, n_particles):
+        ncell = 1
+        for v in n:
+            ncell *= v
+        return types.SimpleNamespace(dim=dim, n=n, ncell=ncell, n_particles=n_particles)
+
+    bubbling = shape(2, (64, 128), 2000)
+    riser = shape(2, (256, 2048), 200000)
+    riser3d = shape(3, (256, 256, 1024), 4000000)
+    assert bench.whole_step_bytes(bubbling, "f64") == pytest.approx(1.80e6, abs=0.005e6)
+    assert bench.whole_step_bytes(riser, "f32") == pytest.approx(69.5e6, abs=0.05e6)
+    assert bench.whole_step_bytes(riser, "f16") == pytest.approx(50.7e6, abs=0.05e6)
+    assert bench.whole_step_bytes(riser3d, "f32") == pytest.approx(12.92e9, abs=0.005e9)
+    # collide_stream alone: populations twice, the offset, rho, u_act, F_p->g,
+    # beta and 1 - eps per cell, a velocity per particle
+    assert bench.collide_stream_bytes(riser, "f32")[1:] == (104, 8)
+    assert bench.collide_stream_bytes(riser3d, "f32")[1:] == (192, 12)
+    assert bench.collide_stream_bytes(riser3d, "f16")[1:] == (116, 12)
